@@ -1,0 +1,239 @@
+"""Seeded synthetic inputs for the GPFC fold + score path.
+
+This module only draws random inputs with the shapes of Kepler long-cadence light
+curves (paper Sec. 2.2 and Sec. 3: 29.4-min cadence, 30k-70k epochs; Table 2
+ranges). It holds none of the method's arithmetic (no phase, no binning, no
+scoring): both the FP64 oracle and the CUDA path receive the arrays it returns.
+
+Every generator takes an explicit integer seed and uses NumPy's PCG64, so the
+same call gives the same arrays on every machine.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+# Kepler long cadence, 29.4 minutes, in days (the workload's stated cadence).
+CADENCE_D = 29.4 / 1440.0
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def freq_grid(n_periods: int, p_min: float = 0.2, p_max: float = 1.0) -> np.ndarray:
+    """Trial periods uniform in frequency over [1/p_max, 1/p_min], endpoints included.
+
+    Returns float64 periods P_k = 1/f_k with f_k = f_lo + k (f_hi - f_lo)/(n-1).
+    """
+    f_lo, f_hi = 1.0 / p_max, 1.0 / p_min
+    if n_periods == 1:
+        return np.array([1.0 / f_lo])
+    k = np.arange(n_periods, dtype=np.float64)
+    f = f_lo + k * (f_hi - f_lo) / (n_periods - 1)
+    return 1.0 / f
+
+
+def period_grid(n_periods: int, p_min: float = 0.2, p_max: float = 1.0) -> np.ndarray:
+    """Trial periods uniform in period (the paper's own grid form, Sec. 2.1)."""
+    return np.linspace(p_min, p_max, n_periods, dtype=np.float64)
+
+
+def box_mask(t: np.ndarray, period: float, epoch: float, duration: float) -> np.ndarray:
+    """True where t lies within duration/2 of a mid-transit time epoch + j*period."""
+    d = np.mod(t - epoch + 0.5 * period, period) - 0.5 * period
+    return np.abs(d) < 0.5 * duration
+
+
+@dataclasses.dataclass
+class LightCurve:
+    times: np.ndarray      # float64 [N], days
+    flux: np.ndarray       # float32 [N], relative flux
+    t0: float              # phase origin used by the workload
+    truth: dict            # injected parameters (empty dict if none)
+
+
+def _gaps(rng: np.random.Generator, n_cad: int, frac: float, lo_d: float, hi_d: float) -> np.ndarray:
+    """Keep-mask after dropping seeded gaps of U[lo_d, hi_d] days until >= frac removed."""
+    keep = np.ones(n_cad, dtype=bool)
+    span = n_cad * CADENCE_D
+    while (~keep).mean() < frac:
+        start = rng.uniform(0.0, span)
+        length = rng.uniform(lo_d, hi_d)
+        a = int(start / CADENCE_D)
+        b = min(n_cad, int((start + length) / CADENCE_D) + 1)
+        keep[a:b] = False
+    return keep
+
+
+def light_curve_tiny(seed: int = 20231204) -> LightCurve:
+    """4,096 cadences from t0 = 0, no gaps, white noise 1e-4, one box at P = 0.7 d.
+
+    Box: depth 3e-4, duration 1 h, epoch uniform in [0, P).
+    """
+    rng = _rng(seed)
+    n = 4096
+    t = np.arange(n, dtype=np.float64) * CADENCE_D
+    period, depth, dur = 0.7, 3e-4, 1.0 / 24.0
+    epoch = rng.uniform(0.0, period)
+    flux = 1.0 + rng.normal(0.0, 1e-4, n)
+    flux = flux * np.where(box_mask(t, period, epoch, dur), 1.0 - depth, 1.0)
+    return LightCurve(t, flux.astype(np.float32), 0.0,
+                      dict(period=period, depth=depth, duration=dur, epoch=epoch))
+
+
+def light_curve_kepler(seed: int = 20232204, n_cad: int = 65536, sigma_white: float = 2e-4,
+                       ar_phi: float = 0.9, ar_sigma: float = 5e-5, gap_frac: float = 0.04,
+                       inject: bool = True, depth_ppm=(50.0, 500.0), dur_h=(0.5, 2.0),
+                       p_range=(0.2, 1.0)) -> LightCurve:
+    """Full-length Kepler-like light curve.
+
+    n_cad cadences at 29.4 min (65,536 -> ~1,338 d); ~gap_frac of cadences dropped in
+    seeded 1-5 d gaps; white noise plus AR(1) red noise (ar_sigma is the marginal std,
+    so the innovation std is ar_sigma*sqrt(1-phi^2)); one box transit with depth
+    log-uniform in depth_ppm, duration uniform in dur_h hours, period uniform in
+    p_range days, epoch uniform in [0, P). t0 = times[0] = 0.
+    """
+    rng = _rng(seed)
+    t_all = np.arange(n_cad, dtype=np.float64) * CADENCE_D
+    keep = _gaps(rng, n_cad, gap_frac, 1.0, 5.0)
+    white = rng.normal(0.0, sigma_white, n_cad)
+    innov = rng.normal(0.0, ar_sigma * np.sqrt(1.0 - ar_phi ** 2), n_cad)
+    red = np.empty(n_cad)
+    red[0] = rng.normal(0.0, ar_sigma)
+    for i in range(1, n_cad):
+        red[i] = ar_phi * red[i - 1] + innov[i]
+    flux = 1.0 + white + red
+    truth = {}
+    if inject:
+        depth = 1e-6 * np.exp(rng.uniform(np.log(depth_ppm[0]), np.log(depth_ppm[1])))
+        dur = rng.uniform(dur_h[0], dur_h[1]) / 24.0
+        period = rng.uniform(p_range[0], p_range[1])
+        epoch = rng.uniform(0.0, period)
+        flux = flux * np.where(box_mask(t_all, period, epoch, dur), 1.0 - depth, 1.0)
+        truth = dict(period=period, depth=depth, duration=dur, epoch=epoch)
+    return LightCurve(t_all[keep].copy(), flux[keep].astype(np.float32), 0.0, truth)
+
+
+@dataclasses.dataclass
+class StarBatch:
+    """Many stars of uneven length, concatenated (CSR offsets)."""
+    lc_offsets: np.ndarray    # int64 [S+1]
+    times: np.ndarray         # float64 [sum N]
+    flux: np.ndarray          # float32 [sum N]
+    grid_offsets: np.ndarray  # int64 [S+1]
+    periods: np.ndarray       # float64 [sum P]
+    t0s: np.ndarray           # float64 [S]
+    truths: list
+
+
+def star_batch(n_stars: int = 1024, seed: int = 20235204, n_range=(8192, 70000),
+               p_count_range=(20000, 250000), transit_frac: float = 0.3,
+               sigma_range=(1e-4, 1e-3)) -> StarBatch:
+    """Batch of stars with uneven lengths and grids (one frequency grid per star)."""
+    rng = _rng(seed)
+    lc_off = [0]
+    g_off = [0]
+    ts, fs, ps, t0s, truths = [], [], [], [], []
+    for s in range(n_stars):
+        n_cad = int(rng.integers(n_range[0], n_range[1] + 1))
+        keep = _gaps(rng, n_cad, 0.04, 1.0, 5.0)
+        t = np.arange(n_cad, dtype=np.float64) * CADENCE_D
+        sig = np.exp(rng.uniform(np.log(sigma_range[0]), np.log(sigma_range[1])))
+        flux = 1.0 + rng.normal(0.0, sig, n_cad)
+        truth = dict(sigma=sig)
+        if rng.uniform() < transit_frac:
+            depth = 1e-6 * np.exp(rng.uniform(np.log(30.0), np.log(2000.0)))
+            dur = rng.uniform(0.5, 3.0) / 24.0
+            period = rng.uniform(0.2, 1.0)
+            epoch = rng.uniform(0.0, period)
+            flux = flux * np.where(box_mask(t, period, epoch, dur), 1.0 - depth, 1.0)
+            truth.update(period=period, depth=depth, duration=dur, epoch=epoch)
+        t, flux = t[keep], flux[keep]
+        n_p = int(rng.integers(p_count_range[0], p_count_range[1] + 1))
+        ts.append(t)
+        fs.append(flux.astype(np.float32))
+        ps.append(freq_grid(n_p))
+        t0s.append(0.0)
+        truths.append(truth)
+        lc_off.append(lc_off[-1] + len(t))
+        g_off.append(g_off[-1] + n_p)
+    return StarBatch(np.array(lc_off, np.int64), np.concatenate(ts), np.concatenate(fs),
+                     np.array(g_off, np.int64), np.concatenate(ps), np.array(t0s), truths)
+
+
+def profiles_mixed(n: int, nbins: int = 256, seed: int = 20233204):
+    """Folded-profile-like vectors: half boxes, half noise-only or sinusoids.
+
+    Boxes: depth log-uniform 30-2,000 ppm, target SNR uniform 3-30 (Eq. 2 form,
+    alpha = d*sqrt(w)/sigma_bin over the w in-box bins), width w = round(q*nbins) bins
+    with q = duration/period, duration U[0.5, 3] h, period U[0.2, 1] d; the per-bin
+    noise sigma_bin is set by the SNR target. Negatives: noise-only (sigma_bin
+    log-uniform 1e-5..1e-3) or a sinusoid (amplitude 1e-4..1e-3, 1-5 cycles per
+    profile, random phase) plus noise. Returns (profiles float32 [n][nbins], labels
+    uint8 [n]).
+    """
+    rng = _rng(seed)
+    out = np.empty((n, nbins), dtype=np.float32)
+    lab = np.zeros(n, dtype=np.uint8)
+    x = np.arange(nbins, dtype=np.float64)
+    for j in range(n):
+        if j % 2 == 0:
+            depth = 1e-6 * np.exp(rng.uniform(np.log(30.0), np.log(2000.0)))
+            snr = rng.uniform(3.0, 30.0)
+            q = (rng.uniform(0.5, 3.0) / 24.0) / rng.uniform(0.2, 1.0)
+            w = int(min(max(1, round(q * nbins)), nbins // 2))
+            sig = depth * np.sqrt(w) / snr
+            start = int(rng.integers(0, nbins))
+            prof = 1.0 + rng.normal(0.0, sig, nbins)
+            idx = (start + np.arange(w)) % nbins
+            prof[idx] -= depth
+            lab[j] = 1
+        elif rng.uniform() < 0.5:
+            sig = np.exp(rng.uniform(np.log(1e-5), np.log(1e-3)))
+            prof = 1.0 + rng.normal(0.0, sig, nbins)
+        else:
+            amp = rng.uniform(1e-4, 1e-3)
+            cyc = rng.uniform(1.0, 5.0)
+            ph = rng.uniform(0.0, 2 * np.pi)
+            sig = np.exp(rng.uniform(np.log(1e-5), np.log(1e-4)))
+            prof = 1.0 + amp * np.sin(2 * np.pi * cyc * x / nbins + ph) + rng.normal(0.0, sig, nbins)
+        out[j] = prof
+    return out, lab
+
+
+def round_to_bf16(a: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even); returns float32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).reshape(a.shape)
+
+
+# Layer shapes of the scorer CNN, PyTorch layout: (name, shape, fan_in)
+CNN_SHAPES = [
+    ("conv1.w", (16, 1, 5), 5), ("conv1.b", (16,), None),
+    ("conv2.w", (32, 16, 5), 80), ("conv2.b", (32,), None),
+    ("conv3.w", (64, 32, 5), 160), ("conv3.b", (64,), None),
+    ("fc1.w", (256, 2048), 2048), ("fc1.b", (256,), None),
+    ("fc2.w", (1, 256), 256), ("fc2.b", (1,), None),
+]
+
+
+def cnn_init(seed: int = 20232304, bias_scale: float = 0.0) -> dict:
+    """He-uniform weights U(+-sqrt(6/fan_in)), biases zero (or U(+-bias_scale)).
+
+    Values are rounded to bfloat16-representable float32 so that every consumer sees
+    the same numbers whatever precision it computes in.
+    """
+    rng = _rng(seed)
+    out = {}
+    for name, shape, fan_in in CNN_SHAPES:
+        if fan_in is None:
+            v = rng.uniform(-bias_scale, bias_scale, shape) if bias_scale > 0 else np.zeros(shape)
+        else:
+            lim = np.sqrt(6.0 / fan_in)
+            v = rng.uniform(-lim, lim, shape)
+        out[name] = round_to_bf16(v.astype(np.float32))
+    return out
