@@ -1,0 +1,309 @@
+"""Benchmark of the GPFC hot path on one GB300 (or N independent replicas).
+
+A step is one full search of one Kepler-length light curve (65,536 cadences with ~4%
+gapped, N ~ 62,900 samples) over 250,000 trial periods uniform in frequency in
+[1, 5] c/d, 256 bins, box widths 1..108: quantise, fold, box-SNR score every period,
+best period. The metric is sample*period folds per second (periods scored per second is
+reported beside it).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the FP64 CPU oracle (the only reference this path has) on a
+bounded sample of the same workload. For N > 1 (torchrun) every rank runs its own
+replica (no data-path communication); value counts the work of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("sample·period folds/s and periods scored/s on 1 GB300, CNN vs box-SNR at fixed TPR/FPR")
+UNIT = "sample·period folds/s"
+NBINS = 256
+N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
+W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
+SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, per SM
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_name(n):
+    return f"kepler-like light curve, {n} samples (65,536 cadences, 4% gaps), {N_PERIODS} periods, " \
+           f"{NBINS} bins, fold + box-SNR (w 1..{W_MAX}) + best period"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_inputs():
+    import lcsynth
+    lc = lcsynth.light_curve_kepler()
+    periods = lcsynth.freq_grid(N_PERIODS)
+    return lc, periods
+
+
+def cpu_oracle_rate(lc, periods, n_periods, seed=0):
+    """Time the FP64 oracle (fold + box-SNR) on n_periods periods; returns (folds/s, seconds)."""
+    import oracle
+    idx = np.random.default_rng(seed).choice(len(periods), n_periods, replace=False)
+    sub = np.ascontiguousarray(periods[np.sort(idx)])
+    sigma = float(np.std(lc.flux.astype(np.float64)))
+    t = time.perf_counter()
+    _, cnt, sums = oracle.fold(lc.times, lc.flux, sub, NBINS, lc.t0)
+    oracle.box_snr(sums, cnt, 1, W_MAX, sigma)
+    dt = time.perf_counter() - t
+    return lc.times.shape[0] * n_periods / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    lc, periods = make_inputs()
+    n = lc.times.shape[0]
+    per_step = 800
+    for _ in range(args.warmup):
+        cpu_oracle_rate(lc, periods, per_step // 4)
+    rates, secs = [], []
+    for s in range(args.steps):
+        r, dt = cpu_oracle_rate(lc, periods, per_step, seed=s + 1)
+        rates.append(r)
+        secs.append(dt)
+    value = n * per_step * len(secs) / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(n), "n_samples": n, "n_periods": N_PERIODS, "nbins": NBINS,
+                   "w_max": W_MAX, "step_sample": f"{per_step} random periods of the {N_PERIODS}-period grid"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} periods per step, full light curve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2312_02063_gb300 as g
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = g.Context(local_rank)
+    lc, periods = make_inputs()
+    n = lc.times.shape[0]
+    t_d = torch.from_numpy(lc.times).to(dev)
+    f_d = torch.from_numpy(lc.flux).to(dev)
+    p_d = torch.from_numpy(periods).to(dev)
+    score = torch.empty(N_PERIODS, dtype=torch.float32, device=dev)
+    bi = torch.empty(1, dtype=torch.int64, device=dev)
+    bs = torch.empty(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        g.gpfc_search(ctx, t_d, f_d, p_d, NBINS, lc.t0, g.SCORER_BOX, 1, W_MAX, 0.0, score, bi, bs)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.sync()
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps, outside the events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        kernel_ms.append(ctx.kernel_time_ms())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * n * N_PERIODS / (ms_per_step * 1e-3)
+
+    # end to end through host buffers: H2D of the step's inputs, the C-ABI call, D2H of
+    # the periodogram and the best period
+    th = torch.from_numpy(lc.times).pin_memory()
+    fh = torch.from_numpy(lc.flux).pin_memory()
+    ph = torch.from_numpy(periods).pin_memory()
+    sh = torch.empty(N_PERIODS, dtype=torch.float32).pin_memory()
+    bih = torch.empty(1, dtype=torch.int64).pin_memory()
+    bsh = torch.empty(1, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps + 2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t_d.copy_(th, non_blocking=True)
+        f_d.copy_(fh, non_blocking=True)
+        p_d.copy_(ph, non_blocking=True)
+        step()
+        sh.copy_(score, non_blocking=True)
+        bih.copy_(bi, non_blocking=True)
+        bsh.copy_(bs, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            e2e_ms.append(a.elapsed_time(b))
+    ctx.sync()
+    e2e_value = world * n * N_PERIODS / (statistics.mean(e2e_ms) * 1e-3)
+    h2d = th.numel() * 8 + fh.numel() * 4 + ph.numel() * 8
+    d2h = sh.numel() * 4 + 8 + 4
+
+    result = None
+    if rank == 0:
+        peaks, src = measured_peaks()
+        smax = float(peaks.get("sm_max_mhz", 2070.0))
+        sms = ctx.num_sms
+        peak_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
+        kmean = statistics.mean(kernel_ms)
+        achieved = n * N_PERIODS / (kmean * 1e-3) / 1e9
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, dt = cpu_oracle_rate(lc, periods, args.cpu_periods)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_periods} random periods of the grid, full light curve, "
+                             f"fold + box-SNR, {dt:.1f} s"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/f32", "data": "synthetic",
+            "config": {"workload": workload_name(n), "n_samples": n, "n_periods": N_PERIODS,
+                       "nbins": NBINS, "w_min": 1, "w_max": W_MAX,
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
+            "roofline": {"bound": "alu", "kernel": "fold_kernel<box>", "achieved": achieved,
+                         "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
+                         "traffic": None, "kernel_ms": kmean,
+                         "peak_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} bin updates/clk "
+                                       f"(shared-memory pipe) x {smax:.0f} MHz ({src} sm_max_mhz)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpfc", choices=["gpfc", "reference"])
+    ap.add_argument("--cpu-periods", type=int, default=6000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-periods", type=int, default=N_PERIODS)
+    args = ap.parse_args()
+    globals()["N_PERIODS"] = args.n_periods
+    rank, world, local_rank = env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * gpfc.h -- C ABI of the GPFC fold + score library (libgpfc.so, sm_103a).
+ *
+ * The library folds a detrended light curve at every trial period of a grid into
+ * phase-binned profiles and scores each profile (paper Sec. 2.1, Fig. 1: fold, noise
+ * normalisation, CNN score per trial period; Sec. 3.1: box-fitting statistic as the
+ * plain detector).
+ *
+ * Conventions for every call:
+ *  - Array arguments are DEVICE pointers owned by the caller (unless a comment says
+ *    "host"). The library never frees them and never keeps them after the call.
+ *  - Work is enqueued on the context's CUDA stream and runs asynchronously. A call
+ *    returns GPFC_OK once its work is enqueued; argument errors found on the host are
+ *    returned at once. Errors found on the device (an invalid period, a time outside
+ *    the fixed-point range, a wait that timed out) are latched in the context and
+ *    returned by gpfc_sync() and by the next call on the context.
+ *  - Status codes are the negative gpfc_status values; GPFC_OK is 0. No call throws.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef GPFC_H
+#define GPFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPFC_OK = 0,
+    GPFC_EINVAL = -1,   /* bad argument: NULL pointer, size out of range */
+    GPFC_ENOMEM = -2,   /* device workspace allocation failed */
+    GPFC_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    GPFC_ERANGE = -4,   /* a period is not finite and > 0, or |tau| / F overflow */
+    GPFC_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+    GPFC_ENOTSUP = -6   /* valid but unsupported configuration (e.g. CNN with nbins != 256) */
+} gpfc_status;
+
+typedef struct gpfc_ctx gpfc_ctx;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int gpfc_version(void);
+
+/* Static message for a status code. */
+const char *gpfc_strerror(int status);
+
+/* Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream). The stream is borrowed, not owned. The context
+ * owns a device workspace that grows on demand; *out is set to NULL on failure. */
+int gpfc_create(gpfc_ctx **out, int device, void *stream);
+
+/* Release the context and its workspace (synchronises its stream first). */
+void gpfc_destroy(gpfc_ctx *ctx);
+
+/* Change the stream later calls enqueue on (synchronises the old stream first). */
+int gpfc_set_stream(gpfc_ctx *ctx, void *stream);
+
+/* Detail text for the last failing call on this context (empty if none). */
+const char *gpfc_last_error(const gpfc_ctx *ctx);
+
+/* Wait for the context's stream, then return (and clear) any latched device error. */
+int gpfc_sync(gpfc_ctx *ctx);
+
+/* Number of multiprocessors of the context's device. */
+int gpfc_num_sms(const gpfc_ctx *ctx);
+
+/* Kernel timing. With timing enabled, each call records CUDA events on the context's
+ * stream around its main kernel (the fold kernel for gpfc_fold / gpfc_search, the
+ * scoring kernel for gpfc_score_*). gpfc_kernel_time_ms synchronises on the stop event
+ * of the last recorded launch and writes its duration in milliseconds to *ms (host).
+ * Returns GPFC_EINVAL if timing is off or nothing was recorded yet. */
+int gpfc_set_timing(gpfc_ctx *ctx, int enable);
+int gpfc_kernel_time_ms(gpfc_ctx *ctx, float *ms);
+
+/* ------------------------------------------------------------------ fold
+ * Phase fold (Sec. 2.3: modular residual of each timestamp by the trial period, map to
+ * a bin, per-bin count and flux sum, mean = sum / count), with equal-width bins and the
+ * phase exact in 64-bit fixed point:
+ *     tau_i = rint((times_i - t0) * 2^24)            (int64, round-to-nearest-even)
+ *     F_k   = rint(2^40 / periods_k)                 (uint64)
+ *     bin   = floor(((tau_i * F_k) mod 2^64) * nbins / 2^64)
+ * so the bin index equals floor(frac((t - t0)/P) * nbins) up to the 2^-25 d time and
+ * 2^-41 c/d frequency quanta, and is bit-identical on every run and machine.
+ *
+ * times   [n]            float64, days, any order
+ * flux    [n]            float32
+ * periods [n_periods]    float64, days, finite and > 0 (else GPFC_ERANGE, latched)
+ * nbins                  2..1024
+ * t0                     phase origin in days; NaN means t0 = times[0]
+ * folded  [n_periods][nbins] float32 row-major, per-bin mean flux, NaN for an empty bin;
+ *                        may be NULL (not written)
+ * counts  [n_periods][nbins] int32 row-major, samples per bin; may be NULL
+ * Sums are accumulated as (flux - mean flux) in FP32 with Kahan compensation (chunk
+ * partials in shared memory, compensated across chunks); counts are exact integers.
+ * Limits: 1 <= n <= 2^24, 1 <= n_periods <= 2^31 - 1, |tau| < 2^62, F < 2^63. */
+int gpfc_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
+              const double *periods, int64_t n_periods, int32_t nbins, double t0,
+              float *folded, int32_t *counts);
+
+/* ------------------------------------------------------------------ box-SNR
+ * Box statistic per folded profile (the box-fitting idea of Sec. 3.1, BLS). For every
+ * width w in [w_min, w_max] and start bin s, the box is bins s..s+w-1 (mod nbins); with
+ * n_in, n_out the samples inside/outside and mu_in, mu_out their mean flux,
+ *     snr = (mu_out - mu_in) * sqrt(n_in * n_out / N) / sigma
+ * over boxes with n_in >= 1 and n_out >= 1. The score is the largest snr (ties: smaller
+ * w, then smaller s); -inf with best_s = best_w = -1 when no box is valid. */
+typedef struct {
+    int32_t w_min;  /* >= 1 */
+    int32_t w_max;  /* w_min..nbins */
+    double sigma;   /* noise scale; <= 0 means 1 (standalone scoring) or the
+                       population std of the light curve's flux (gpfc_search) */
+} gpfc_box_params;
+
+/* folded [n_periods][nbins] float32 means (NaN or count 0 marks an empty bin);
+ * counts [n_periods][nbins] int32 (required); score [n_periods] float32;
+ * best_s / best_w [n_periods] int32, may be NULL. Limits: nbins 2..1024,
+ * per-profile sample count N <= 2^24. */
+int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts,
+                   int64_t n_periods, int32_t nbins, const gpfc_box_params *params,
+                   float *score, int32_t *best_s, int32_t *best_w);
+
+/* ------------------------------------------------------------------ best period
+ * argmax over score[n_periods] (NaN never wins; ties go to the smaller index), Sec. 2.1:
+ * the trial period with the strongest score. best_index [1] int64 (-1 if every score is
+ * NaN), best_score [1] float32; device pointers. */
+int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods,
+                     int64_t *best_index, float *best_score);
+
+/* ------------------------------------------------------------------ search
+ * Fold + score in one pass (Fig. 1): the profiles stay on chip and are not written.
+ * scorer GPFC_SCORER_BOX takes a gpfc_box_params* in scorer_params.
+ * score [n_periods] float32; best_index [1] int64 and best_score [1] float32 (device,
+ * may be NULL). Limits as for gpfc_fold. */
+typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;
+
+int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
+                const double *periods, int64_t n_periods, int32_t nbins, double t0,
+                int scorer, const void *scorer_params, float *score,
+                int64_t *best_index, float *best_score);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPFC_H */

@@ -1,0 +1,240 @@
+"""Python binding of libgpfc.so: the GPFC fold + score path on one GB300 (sm_103a).
+
+Thin ctypes marshalling over the C ABI in include/gpfc.h, with the same names
+(gpfc_fold, gpfc_score_box, gpfc_best_period, gpfc_search, ...). PyTorch provides the
+device buffers and the stream; every step of the path runs in the library's kernels.
+There is no CPU fallback: importing works anywhere, but every call needs the compiled
+library and a CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "GpfcError", "Context", "load_library", "library_path",
+    "gpfc_fold", "gpfc_score_box", "gpfc_best_period", "gpfc_search",
+    "SCORER_BOX", "SCORER_CNN",
+]
+
+SCORER_BOX = 0
+SCORER_CNN = 1
+
+STATUS = {0: "GPFC_OK", -1: "GPFC_EINVAL", -2: "GPFC_ENOMEM", -3: "GPFC_ECUDA", -4: "GPFC_ERANGE",
+          -5: "GPFC_ETIMEOUT", -6: "GPFC_ENOTSUP"}
+
+
+class GpfcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class BoxParams(ctypes.Structure):
+    _fields_ = [("w_min", ctypes.c_int32), ("w_max", ctypes.c_int32), ("sigma", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libgpfc.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise GpfcError(-3, f"libgpfc.so not found at {_build.LIB}; run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        L.gpfc_version.restype = ctypes.c_int
+        L.gpfc_strerror.restype = ctypes.c_char_p
+        L.gpfc_strerror.argtypes = [ctypes.c_int]
+        L.gpfc_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp]
+        L.gpfc_destroy.argtypes = [_vp]
+        L.gpfc_destroy.restype = None
+        L.gpfc_set_stream.argtypes = [_vp, _vp]
+        L.gpfc_last_error.argtypes = [_vp]
+        L.gpfc_last_error.restype = ctypes.c_char_p
+        L.gpfc_sync.argtypes = [_vp]
+        L.gpfc_num_sms.argtypes = [_vp]
+        L.gpfc_set_timing.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_kernel_time_ms.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
+        L.gpfc_fold.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_double, _vp, _vp]
+        L.gpfc_score_box.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.POINTER(BoxParams), _vp, _vp, _vp]
+        L.gpfc_best_period.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.gpfc_search.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, device, name, numel=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t
+
+
+class Context:
+    """A gpfc_ctx bound to one CUDA device and a stream (torch's current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        if not torch.cuda.is_available():
+            raise GpfcError(-3, "no CUDA device: the GPFC path runs only on the GPU")
+        self.lib = load_library()
+        self.device = torch.device("cuda", device if isinstance(device, int) else torch.device(device).index or 0)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        h = _vp()
+        with torch.cuda.device(self.device):
+            rc = self.lib.gpfc_create(ctypes.byref(h), self.device.index, _vp(s.cuda_stream))
+        if rc != 0:
+            raise GpfcError(rc, self.lib.gpfc_strerror(rc).decode())
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gpfc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise GpfcError(rc, self.lib.gpfc_last_error(self.handle).decode() or
+                            self.lib.gpfc_strerror(rc).decode())
+
+    def set_stream(self, stream):
+        self._check(self.lib.gpfc_set_stream(self.handle, _vp(stream.cuda_stream)))
+        self.stream = stream
+
+    def sync(self):
+        self._check(self.lib.gpfc_sync(self.handle))
+
+    def set_timing(self, enable: bool):
+        self._check(self.lib.gpfc_set_timing(self.handle, int(bool(enable))))
+
+    def kernel_time_ms(self) -> float:
+        v = ctypes.c_float()
+        self._check(self.lib.gpfc_kernel_time_ms(self.handle, ctypes.byref(v)))
+        return float(v.value)
+
+    @property
+    def num_sms(self):
+        return self.lib.gpfc_num_sms(self.handle)
+
+
+def gpfc_fold(ctx: Context, times, flux, periods, nbins: int, t0: float = math.nan, folded=None,
+              counts=None, want_folded=True, want_counts=True):
+    """Fold (times f64, flux f32) at every period (f64) into nbins equal-width bins.
+
+    Returns (folded f32 [P][nbins] or None, counts i32 [P][nbins] or None); outputs are
+    allocated on the context's device unless given.
+    """
+    dev = ctx.device
+    n, npd = times.numel(), periods.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    _need(periods, torch.float64, dev, "periods")
+    if folded is None and want_folded:
+        folded = torch.empty((npd, nbins), dtype=torch.float32, device=dev)
+    if counts is None and want_counts:
+        counts = torch.empty((npd, nbins), dtype=torch.int32, device=dev)
+    if folded is not None:
+        _need(folded, torch.float32, dev, "folded", npd * nbins)
+    if counts is not None:
+        _need(counts, torch.int32, dev, "counts", npd * nbins)
+    ctx._check(ctx.lib.gpfc_fold(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), npd, int(nbins),
+                                 float(t0), _ptr(folded), _ptr(counts)))
+    return folded, counts
+
+
+def gpfc_score_box(ctx: Context, folded, counts, w_min: int, w_max: int, sigma: float = 0.0,
+                   score=None, best_s=None, best_w=None, want_best=True):
+    """Box-SNR of each profile ([P][nbins] means + counts). Returns (score, best_s, best_w)."""
+    dev = ctx.device
+    npd, nbins = folded.shape
+    _need(folded, torch.float32, dev, "folded")
+    _need(counts, torch.int32, dev, "counts", folded.numel())
+    if score is None:
+        score = torch.empty(npd, dtype=torch.float32, device=dev)
+    if want_best and best_s is None:
+        best_s = torch.empty(npd, dtype=torch.int32, device=dev)
+    if want_best and best_w is None:
+        best_w = torch.empty(npd, dtype=torch.int32, device=dev)
+    bp = BoxParams(int(w_min), int(w_max), float(sigma))
+    ctx._check(ctx.lib.gpfc_score_box(ctx.handle, _ptr(folded), _ptr(counts), npd, int(nbins),
+                                      ctypes.byref(bp), _ptr(score), _ptr(best_s), _ptr(best_w)))
+    return score, best_s, best_w
+
+
+def gpfc_best_period(ctx: Context, score, best_index=None, best_score=None):
+    """argmax of score (ties -> smaller index, NaN never wins). Returns (index i64[1], score f32[1])."""
+    dev = ctx.device
+    _need(score, torch.float32, dev, "score")
+    if best_index is None:
+        best_index = torch.empty(1, dtype=torch.int64, device=dev)
+    if best_score is None:
+        best_score = torch.empty(1, dtype=torch.float32, device=dev)
+    ctx._check(ctx.lib.gpfc_best_period(ctx.handle, _ptr(score), score.numel(), _ptr(best_index),
+                                        _ptr(best_score)))
+    return best_index, best_score
+
+
+def gpfc_search(ctx: Context, times, flux, periods, nbins: int, t0: float = math.nan, scorer: int = SCORER_BOX,
+                w_min: int = 1, w_max: int | None = None, sigma: float = 0.0, score=None, best_index=None,
+                best_score=None):
+    """Fold + score without materialising profiles. Returns (score [P], best_index [1], best_score [1])."""
+    dev = ctx.device
+    n, npd = times.numel(), periods.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    _need(periods, torch.float64, dev, "periods")
+    if score is None:
+        score = torch.empty(npd, dtype=torch.float32, device=dev)
+    if best_index is None:
+        best_index = torch.empty(1, dtype=torch.int64, device=dev)
+    if best_score is None:
+        best_score = torch.empty(1, dtype=torch.float32, device=dev)
+    if scorer == SCORER_BOX:
+        if w_max is None:
+            w_max = int(math.ceil(0.125 * nbins))
+        params = BoxParams(int(w_min), int(w_max), float(sigma))
+        pp = ctypes.cast(ctypes.pointer(params), _vp)
+    else:
+        raise GpfcError(-6, f"scorer {scorer} is not available through this call yet")
+    ctx._check(ctx.lib.gpfc_search(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), npd, int(nbins),
+                                   float(t0), int(scorer), pp, _ptr(score), _ptr(best_index),
+                                   _ptr(best_score)))
+    return score, best_index, best_score

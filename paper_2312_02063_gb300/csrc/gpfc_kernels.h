@@ -1,0 +1,91 @@
+// gpfc_kernels.h -- launch parameters shared between the host API and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpfc {
+
+// Device error bits, OR-ed into the context's status word (host-mapped memory).
+enum : uint32_t {
+    kErrRange = 1u,    // period not finite/positive, or tau / F outside the fixed point
+    kErrTimeout = 2u,  // a bounded wait on an mbarrier gave up
+};
+
+constexpr int kTile = 1024;            // light-curve samples per bulk-copy tile
+constexpr int kMaxFoldWarps = 16;      // warps per fold block (32 periods each)
+constexpr int kMaxNbinsLane = 1024;    // largest nbins of the lane-private fold
+constexpr size_t kSmemLimit = 232448;  // opt-in dynamic shared memory per block (227 KB)
+
+// Per-star statistics written by the prep kernels.
+struct StarStats {
+    double f_ref;   // mean flux (FP64)
+    float f_hi;     // f_ref rounded to FP32
+    float f_lo;     // f_ref - f_hi rounded to FP32
+    float sigma;    // population std of the flux (FP64 reduction, rounded)
+    int32_t n;      // samples of the star
+};
+
+// Samples of all stars, quantised, at 16-byte aligned per-star offsets.
+struct SampleScratch {
+    uint32_t *tau_lo;   // low 32 bits of tau
+    int32_t *tau_hi;    // high 32 bits of tau
+    float *x;           // flux - f_ref (FP32)
+};
+
+enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeCnnPrep = 2 };
+
+struct FoldParams {
+    SampleScratch smp;
+    const int64_t *lc_off;     // [S+1] sample offsets, or NULL (one star of n samples)
+    int64_t n;
+    const double *periods;
+    const int64_t *grid_off;   // [S+1] period offsets, or NULL (one grid of np periods)
+    int64_t np;
+    const int64_t *task_off;   // [S+1] first fold task of each star, or NULL
+    int64_t ntasks;
+    int nstars;
+    const StarStats *stats;
+    int nbins;
+    int shift;                 // 32 - log2(nbins) if nbins is a power of two, else -1
+    int warps;                 // warps per block; periods per block = 32 * warps
+    int chunk_tiles;           // tiles per shared-memory chunk (<= 63)
+    float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
+    uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
+    // kModeFold outputs ([global period][nbins])
+    float *folded;
+    int32_t *counts;
+    // kModeBox outputs
+    float *score;              // [global period]
+    int32_t *best_s;
+    int32_t *best_w;
+    unsigned long long *best_key;  // [S] argmax keys (may be NULL)
+    int w_min, w_max;
+    float sigma_user;          // > 0: use it; else the star's flux std (1 if that is 0)
+    // kModeCnnPrep output: normalised profiles, bf16 [global period][256]
+    uint16_t *cnn_in;
+    uint32_t *status;
+};
+
+size_t fold_smem_bytes(int nbins, int warps);
+int fold_max_warps(int nbins);
+int fold_register_kernels();
+
+cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
+                        int nstars, int64_t max_len, const double *t0s, double t0, SampleScratch smp,
+                        double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st);
+cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st);
+cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, int64_t np, int nbins,
+                                  int w_min, int w_max, float sigma, float *score, int32_t *best_s,
+                                  int32_t *best_w, cudaStream_t st);
+cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *key, cudaStream_t st);
+cudaError_t launch_argmax_finalize(const unsigned long long *key, int nstars, int64_t *best_index,
+                                   float *best_score, cudaStream_t st);
+
+inline int64_t scratch_elems(int64_t total_samples, int nstars)
+{
+    return 4 * ((total_samples + 3) / 4 + nstars) + 4 * kTile;
+}
+
+}  // namespace gpfc

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every
+function that include/*.h declares (no compute calls: there is no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(gpfc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gpfc_create", "gpfc_destroy", "gpfc_fold", "gpfc_score_box", "gpfc_search",
+                     "gpfc_best_period", "gpfc_sync", "gpfc_strerror"):
+        assert required in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    assert lib.gpfc_strerror(0) == b"ok"
+    assert lib.gpfc_strerror(-4) == b"value outside the fixed-point range"
+    assert lib.gpfc_version() >= 100
+
+
+def test_null_context_is_rejected_without_gpu():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    assert lib.gpfc_sync(None) == -1
+    assert lib.gpfc_fold(None, None, None, 0, None, 0, 64, 0.0, None, None) == -1
+
+
+def test_product_path_has_no_cpu_fallback():
+    import torch
+    import paper_2312_02063_gb300 as g
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(g.GpfcError):
+        g.Context(0)
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2312_02063_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(f).read()
+            assert "import oracle" not in text and "from oracle" not in text, f
+            assert "gpfc_oracle" not in text, f
+
+
+def test_sm103a_binary_is_built():
+    import paper_2312_02063_gb300 as g
+    g.load_library()
+    logs = glob.glob(os.path.join(ROOT, "paper_2312_02063_gb300", "_build", "*.ptxas.txt"))
+    assert logs and any("sm_103a" in open(l).read() for l in logs)

@@ -1,0 +1,245 @@
+"""GPU parity of the fold, box-SNR and best-period kernels against the FP64 oracle.
+
+Tolerances: bin counts bit-exact; bin means within 1e-6 relative; box-SNR within 1e-5
+relative (with the score's own scale as floor when |score| < 1).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import lcsynth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+MEAN_RTOL = 1e-6
+BOX_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2312_02063_gb300 as g
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(ctx, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(ctx.device)
+
+
+def gpu_fold(ctx, times, flux, periods, nbins, t0):
+    import paper_2312_02063_gb300 as g
+    folded, counts = g.gpfc_fold(ctx, _dev(ctx, times), _dev(ctx, flux.astype(np.float32)),
+                                 _dev(ctx, periods), nbins, t0)
+    ctx.sync()
+    return folded.cpu().numpy(), counts.cpu().numpy()
+
+
+def check_fold(fo, co, mean_o, cnt_o):
+    np.testing.assert_array_equal(co, cnt_o)
+    nz = cnt_o > 0
+    err = np.abs(fo[nz].astype(np.float64) - mean_o[nz])
+    assert np.all(err <= MEAN_RTOL * np.abs(mean_o[nz])), float(np.max(err / np.abs(mean_o[nz])))
+    assert np.all(np.isnan(fo[~nz]))
+
+
+def check_box(sc, sc_o):
+    sc = sc.astype(np.float64)
+    fin = np.isfinite(sc_o)
+    np.testing.assert_array_equal(np.isfinite(sc), fin)
+    err = np.abs(sc[fin] - sc_o[fin])
+    assert np.all(err <= BOX_RTOL * np.maximum(np.abs(sc_o[fin]), 1.0)), float(np.max(err))
+
+
+def test_fold_tiny_config_matches_oracle(ctx):
+    lc = lcsynth.light_curve_tiny()
+    periods = lcsynth.freq_grid(2000)
+    fo, co = gpu_fold(ctx, lc.times, lc.flux, periods, 64, lc.t0)
+    mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods, 64, lc.t0)
+    check_fold(fo, co, mean_o, cnt_o)
+
+
+@pytest.mark.parametrize("n,npd,nbins", [(1, 1, 2), (5, 3, 7), (1023, 37, 64), (1025, 33, 100),
+                                         (3001, 65, 256), (4096 * 5 + 17, 129, 128), (2500, 40, 1024),
+                                         (70001, 31, 256)])
+def test_fold_ragged_sizes(ctx, n, npd, nbins):
+    rng = np.random.default_rng(n + npd + nbins)
+    times = np.sort(rng.uniform(0.0, 400.0, n))
+    flux = (1.0 + rng.normal(0, 3e-4, n)).astype(np.float32)
+    periods = rng.uniform(0.2, 1.0, npd)
+    t0 = float(rng.uniform(-5, 5))
+    fo, co = gpu_fold(ctx, times, flux, periods, nbins, t0)
+    mean_o, cnt_o, _ = oracle.fold(times, flux, periods, nbins, t0)
+    check_fold(fo, co, mean_o, cnt_o)
+
+
+def test_fold_adversarial_edges_multiples_and_negative_tau(ctx):
+    # t on a 2^-24 grid and power-of-two periods: many samples exactly on bin edges;
+    # periods equal to multiples of the cadence leave most bins empty; t < t0.
+    n = 5000
+    dt = 2.0 ** -6
+    times = np.arange(n) * dt - 20.0
+    flux = (1.0 + 1e-4 * np.sin(np.arange(n))).astype(np.float32)
+    periods = np.array([0.25, 0.5, 1.0, 2.0, 8 * dt, 13 * dt, 0.7, 1e-3, 123.0])
+    for nbins in (64, 256, 100):
+        fo, co = gpu_fold(ctx, times, flux, periods, nbins, 0.0)
+        mean_o, cnt_o, _ = oracle.fold(times, flux, periods, nbins, 0.0)
+        check_fold(fo, co, mean_o, cnt_o)
+
+
+def test_fold_constant_flux_and_all_in_one_bin(ctx):
+    n = 70000  # > 65535: one bin receives every sample (period far above the span)
+    times = np.arange(n) * lcsynth.CADENCE_D
+    flux = np.full(n, 0.99931, np.float32)
+    periods = np.array([1e7, 0.5, 0.6123])
+    fo, co = gpu_fold(ctx, times, flux, periods, 64, 0.0)
+    mean_o, cnt_o, _ = oracle.fold(times, flux, periods, 64, 0.0)
+    check_fold(fo, co, mean_o, cnt_o)
+    assert co[0, 0] == n
+
+
+def test_fold_is_deterministic(ctx):
+    lc = lcsynth.light_curve_tiny(3)
+    periods = lcsynth.freq_grid(777)
+    a = gpu_fold(ctx, lc.times, lc.flux, periods, 64, lc.t0)
+    b = gpu_fold(ctx, lc.times, lc.flux, periods, 64, lc.t0)
+    assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32))
+    assert np.array_equal(a[1], b[1])
+
+
+@pytest.fixture(scope="module")
+def kepler():
+    lc = lcsynth.light_curve_kepler()
+    periods = lcsynth.freq_grid(250_000)
+    return lc, periods
+
+
+def test_fold_full_length_sampled_periods_and_invariants(ctx, kepler):
+    lc, periods = kepler
+    fo, co = gpu_fold(ctx, lc.times, lc.flux, periods, 256, lc.t0)
+    n = lc.times.shape[0]
+    assert np.all(co.sum(axis=1) == n)
+    # sum of (mean * count) over bins equals the flux total for every period
+    tot = float(np.sum(lc.flux.astype(np.float64)))
+    s = np.where(co > 0, fo.astype(np.float64) * co, 0.0).sum(axis=1)
+    assert np.max(np.abs(s - tot)) <= 1e-6 * tot
+    idx = np.random.default_rng(0).choice(len(periods), 96, replace=False)
+    idx = np.concatenate([idx, [0, len(periods) - 1]])
+    mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods[idx], 256, lc.t0)
+    check_fold(fo[idx], co[idx], mean_o, cnt_o)
+
+
+def test_search_box_tiny_config(ctx):
+    import paper_2312_02063_gb300 as g
+    lc = lcsynth.light_curve_tiny()
+    periods = lcsynth.freq_grid(2000)
+    sig = 1e-4
+    score, bi, bs = g.gpfc_search(ctx, _dev(ctx, lc.times), _dev(ctx, lc.flux), _dev(ctx, periods), 64,
+                                  lc.t0, g.SCORER_BOX, 1, 8, sig)
+    ctx.sync()
+    _, cnt_o, sum_o = oracle.fold(lc.times, lc.flux, periods, 64, lc.t0)
+    sc_o, s_o, w_o = oracle.box_snr(sum_o, cnt_o, 1, 8, sig)
+    sc = score.cpu().numpy()
+    check_box(sc, sc_o)
+    k = int(bi.item())
+    assert k == oracle.argmax(sc)
+    assert float(bs.item()) == sc[k]
+    # the injected 0.7 d signal (or a harmonic) wins
+    P = periods[k]
+    assert min(abs(P - 0.7 * m) for m in (0.5, 1.0, 2.0)) < 2e-3
+
+
+def test_search_box_full_length_sampled(ctx, kepler):
+    import paper_2312_02063_gb300 as g
+    lc, periods = kepler
+    w_max = int(math.ceil(0.42 * 256))
+    score, bi, bs = g.gpfc_search(ctx, _dev(ctx, lc.times), _dev(ctx, lc.flux), _dev(ctx, periods), 256,
+                                  lc.t0, g.SCORER_BOX, 1, w_max, 0.0)
+    ctx.sync()
+    sc = score.cpu().numpy()
+    sigma = float(np.std(lc.flux.astype(np.float64)))
+    k = int(bi.item())
+    idx = np.random.default_rng(1).choice(len(periods), 24, replace=False)
+    idx = np.unique(np.concatenate([idx, [k]]))
+    _, cnt_o, sum_o = oracle.fold(lc.times, lc.flux, periods[idx], 256, lc.t0)
+    sc_o, _, _ = oracle.box_snr(sum_o, cnt_o, 1, w_max, sigma)
+    # sigma: GPU uses its own FP64 population std, rounded to FP32
+    check_box(sc[idx] * 1.0, sc_o * (sigma / np.float64(np.float32(sigma))))
+    assert k == oracle.argmax(sc)
+
+
+def test_score_box_standalone_matches_oracle(ctx):
+    import paper_2312_02063_gb300 as g
+    prof, _ = lcsynth.profiles_mixed(1500, seed=4)
+    rng = np.random.default_rng(4)
+    counts = rng.integers(0, 400, prof.shape).astype(np.int32)
+    counts[:, ::17] = 0
+    prof = np.where(counts > 0, prof, np.nan).astype(np.float32)
+    sc, bs, bw = g.gpfc_score_box(ctx, _dev(ctx, prof), _dev(ctx, counts), 1, 32, 2e-4)
+    ctx.sync()
+    sc_o, _, _ = oracle.box_snr_from_means(prof, counts, 1, 32, 2e-4)
+    check_box(sc.cpu().numpy(), sc_o)
+    # the reported box must reach the score (several boxes may tie within rounding)
+    bs, bw = bs.cpu().numpy(), bw.cpu().numpy()
+    sums = np.where(counts > 0, prof.astype(np.float64) * counts, 0.0)
+    for k in range(0, 1500, 97):
+        v = oracle.box_snr_at(sums[k], counts[k], int(bs[k]), int(bw[k]), 2e-4)
+        assert abs(v - sc_o[k]) <= BOX_RTOL * max(abs(sc_o[k]), 1.0)
+
+
+def test_score_box_degenerate_profiles(ctx):
+    import paper_2312_02063_gb300 as g
+    nb = 64
+    prof = np.ones((3, nb), np.float32)
+    counts = np.full((3, nb), 5, np.int32)
+    counts[1] = 0
+    counts[1, 9] = 70000  # one bin holds everything: no valid box, count > 65535
+    prof[2] = 0.9995
+    sc, bs, bw = g.gpfc_score_box(ctx, _dev(ctx, prof), _dev(ctx, counts), 3, 8, 1.0)
+    ctx.sync()
+    sc, bs, bw = sc.cpu().numpy(), bs.cpu().numpy(), bw.cpu().numpy()
+    assert sc[0] == 0.0 and (bs[0], bw[0]) == (0, 3)
+    assert sc[1] == -np.inf and (bs[1], bw[1]) == (-1, -1)
+    assert sc[2] == 0.0
+
+
+def test_best_period_ties_and_nan(ctx):
+    import paper_2312_02063_gb300 as g
+    s = np.full(100003, -1.0, np.float32)
+    s[5] = 3.0
+    s[77777] = 3.0
+    s[9] = np.nan
+    bi, bs = g.gpfc_best_period(ctx, _dev(ctx, s))
+    ctx.sync()
+    assert int(bi.item()) == 5 and float(bs.item()) == 3.0
+    bi, bs = g.gpfc_best_period(ctx, _dev(ctx, np.full(7, np.nan, np.float32)))
+    ctx.sync()
+    assert int(bi.item()) == -1
+
+
+def test_invalid_period_is_reported_at_sync(ctx):
+    import paper_2312_02063_gb300 as g
+    times = np.arange(100) * 0.02
+    flux = np.ones(100, np.float32)
+    periods = np.array([0.5, -1.0, 0.3])
+    g.gpfc_fold(ctx, _dev(ctx, times), _dev(ctx, flux), _dev(ctx, periods), 64, 0.0)
+    with pytest.raises(g.GpfcError) as ei:
+        ctx.sync()
+    assert ei.value.code == -4
+    ctx.sync()  # cleared
+
+
+def test_argument_errors_are_synchronous(ctx):
+    import paper_2312_02063_gb300 as g
+    times = _dev(ctx, np.arange(10) * 0.1)
+    flux = _dev(ctx, np.ones(10, np.float32))
+    per = _dev(ctx, np.array([0.5]))
+    with pytest.raises(g.GpfcError) as ei:
+        g.gpfc_fold(ctx, times, flux, per, 1, 0.0)
+    assert ei.value.code == -1
+    with pytest.raises(g.GpfcError) as ei:
+        g.gpfc_fold(ctx, times, flux, per, 2048, 0.0)
+    assert ei.value.code == -6
