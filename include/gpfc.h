@@ -56,7 +56,8 @@ void gpfc_destroy(gpfc_ctx *ctx);
 /* Change the stream later calls enqueue on (synchronises the old stream first). */
 int gpfc_set_stream(gpfc_ctx *ctx, void *stream);
 
-/* Detail text for the last failing call on this context (empty if none). */
+/* Detail text for the last failing call on this context (empty if none). With
+ * ctx == NULL: the detail of the calling thread's last failed gpfc_create. */
 const char *gpfc_last_error(const gpfc_ctx *ctx);
 
 /* Wait for the context's stream, then return (and clear) any latched device error. */

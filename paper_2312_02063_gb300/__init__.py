@@ -116,7 +116,7 @@ class Context:
         with torch.cuda.device(self.device):
             rc = self.lib.gpfc_create(ctypes.byref(h), self.device.index, _vp(s.cuda_stream))
         if rc != 0:
-            raise GpfcError(rc, self.lib.gpfc_strerror(rc).decode())
+            raise GpfcError(rc, self.lib.gpfc_last_error(None).decode() or self.lib.gpfc_strerror(rc).decode())
         self.handle = h
 
     def close(self):

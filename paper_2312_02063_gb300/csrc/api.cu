@@ -31,6 +31,9 @@ struct gpfc_ctx {
 
 namespace {
 
+// Message of the last failure that had no context to hold it (gpfc_create).
+thread_local char g_create_error[512] = {0};
+
 // Bracket the main kernel of a call with events when timing is enabled.
 struct KernelTimer {
     gpfc_ctx *ctx;
@@ -202,7 +205,9 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     p.nbins = nbins;
     p.shift = shift_of(nbins);
     p.warps = pl.warps;
-    p.chunk_tiles = 4;
+    // ~64 samples per bin per chunk keeps the plain FP32 partials short; the chunk
+    // partials are then added with Kahan compensation
+    p.chunk = (int)std::min<int64_t>(65532, std::max<int64_t>(256, (int64_t)64 * nbins)) & ~3;
     p.ws_sc = fb.ws_sc;
     p.ws_cnt = fb.ws_cnt;
     p.status = ctx->status_dev;
@@ -259,6 +264,8 @@ int gpfc_create(gpfc_ctx **out, int device, void *stream)
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_stop);
     if (e != cudaSuccess) {
+        snprintf(g_create_error, sizeof(g_create_error), "gpfc_create on device %d: %s", device,
+                 cudaGetErrorString(e));
         cudaGetLastError();
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
         delete ctx;
@@ -307,7 +314,7 @@ int gpfc_set_stream(gpfc_ctx *ctx, void *stream)
     return GPFC_OK;
 }
 
-const char *gpfc_last_error(const gpfc_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+const char *gpfc_last_error(const gpfc_ctx *ctx) { return ctx ? ctx->last_error : g_create_error; }
 
 int gpfc_num_sms(const gpfc_ctx *ctx) { return ctx ? ctx->num_sms : 0; }
 
@@ -341,7 +348,7 @@ int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts, in
     if (!folded || !counts || !score || !params) return set_err(ctx, GPFC_EINVAL, "NULL argument");
     if (n_periods < 1 || n_periods > (int64_t)INT32_MAX) return set_err(ctx, GPFC_EINVAL, "bad n_periods");
     if (nbins < 2 || nbins > kMaxNbinsLane) return set_err(ctx, GPFC_EINVAL, "nbins outside [2, 1024]");
-    if ((size_t)4 * nbins * 33 * 6 > kSmemLimit) return set_err(ctx, GPFC_ENOTSUP, "nbins too large for the box kernel");
+    if ((size_t)nbins * 33 * 6 > kSmemLimit - 1024) return set_err(ctx, GPFC_ENOTSUP, "nbins too large for the box kernel");
     if (params->w_min < 1 || params->w_max < params->w_min || params->w_max > nbins)
         return set_err(ctx, GPFC_EINVAL, "box widths must satisfy 1 <= w_min <= w_max <= nbins");
     cudaSetDevice(ctx->device);

@@ -186,7 +186,34 @@ __device__ __forceinline__ uint32_t phase_bin(uint32_t tl, uint32_t th, uint32_t
     return (uint32_t)(t >> 32);
 }
 
-// Fold nvalid samples of a staged tile into this lane's bins (accw[b*32], cntw[b*32]).
+// Lane-private bins. The FP32 partial sum of bin b is at accw[b * 32] (bank = lane).
+// 16-bit counts are paired per lane: word (b / 2) * 32 + lane holds bins 2j and 2j+1,
+// so a warp's count accesses also hit 32 distinct banks whatever the bins.
+__device__ __forceinline__ uint32_t cidx(uint32_t b) { return ((b >> 1) << 6) | (b & 1u); }
+
+template <bool POW2>
+__device__ __forceinline__ void bins4(const uint32_t *__restrict__ stl, const uint32_t *__restrict__ sth,
+                                      int i, uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift,
+                                      uint32_t (&b)[4])
+{
+    const uint4 a = *reinterpret_cast<const uint4 *>(stl + i);
+    const uint4 h = *reinterpret_cast<const uint4 *>(sth + i);
+    b[0] = phase_bin<POW2>(a.x, h.x, Fl, Fh, nbins, shift);
+    b[1] = phase_bin<POW2>(a.y, h.y, Fl, Fh, nbins, shift);
+    b[2] = phase_bin<POW2>(a.z, h.z, Fl, Fh, nbins, shift);
+    b[3] = phase_bin<POW2>(a.w, h.w, Fl, Fh, nbins, shift);
+}
+
+__device__ __forceinline__ bool hazard4(const uint32_t (&b)[4])
+{
+    return (b[0] == b[1]) | (b[0] == b[2]) | (b[0] == b[3]) | (b[1] == b[2]) | (b[1] == b[3]) |
+           (b[2] == b[3]);
+}
+
+// Fold nvalid samples of a staged tile into this lane's bins. Groups of 4 samples are
+// software-pipelined: the bin reads of group g are issued, then the phases and bins of
+// group g+1 are computed while they are in flight, then group g is written back. If two
+// samples of a group share a bin the group is applied one sample at a time.
 template <bool POW2>
 __device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
                                           const uint32_t *__restrict__ sth,
@@ -194,145 +221,264 @@ __device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
                                           uint16_t *cntw, uint32_t Fl, uint32_t Fh,
                                           uint32_t nbins, int shift)
 {
-    int i = 0;
+    const int ng = nvalid >> 2;
+    if (ng > 0) {
+        uint32_t b[4];
+        bins4<POW2>(stl, sth, 0, Fl, Fh, nbins, shift, b);
+        float4 x = *reinterpret_cast<const float4 *>(sx);
+        bool haz = hazard4(b);
 #pragma unroll 1
-    for (; i + 4 <= nvalid; i += 4) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(stl + i);
-        const uint4 h = *reinterpret_cast<const uint4 *>(sth + i);
-        const float4 f = *reinterpret_cast<const float4 *>(sx + i);
-        const uint32_t b0 = phase_bin<POW2>(a.x, h.x, Fl, Fh, nbins, shift) << 5;
-        const uint32_t b1 = phase_bin<POW2>(a.y, h.y, Fl, Fh, nbins, shift) << 5;
-        const uint32_t b2 = phase_bin<POW2>(a.z, h.z, Fl, Fh, nbins, shift) << 5;
-        const uint32_t b3 = phase_bin<POW2>(a.w, h.w, Fl, Fh, nbins, shift) << 5;
-        const bool haz = (b0 == b1) | (b0 == b2) | (b0 == b3) | (b1 == b2) | (b1 == b3) | (b2 == b3);
-        if (!haz) {
-            const float s0 = accw[b0], s1 = accw[b1], s2 = accw[b2], s3 = accw[b3];
-            const uint32_t c0 = cntw[b0], c1 = cntw[b1], c2 = cntw[b2], c3 = cntw[b3];
-            accw[b0] = s0 + f.x;
-            accw[b1] = s1 + f.y;
-            accw[b2] = s2 + f.z;
-            accw[b3] = s3 + f.w;
-            cntw[b0] = (uint16_t)(c0 + 1u);
-            cntw[b1] = (uint16_t)(c1 + 1u);
-            cntw[b2] = (uint16_t)(c2 + 1u);
-            cntw[b3] = (uint16_t)(c3 + 1u);
-        } else {
-            accw[b0] += f.x;
-            cntw[b0] = (uint16_t)(cntw[b0] + 1u);
-            accw[b1] += f.y;
-            cntw[b1] = (uint16_t)(cntw[b1] + 1u);
-            accw[b2] += f.z;
-            cntw[b2] = (uint16_t)(cntw[b2] + 1u);
-            accw[b3] += f.w;
-            cntw[b3] = (uint16_t)(cntw[b3] + 1u);
+        for (int g = 0; g < ng; ++g) {
+            float s[4];
+            uint32_t c[4];
+            if (!haz) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    s[u] = accw[b[u] << 5];
+                    c[u] = cntw[cidx(b[u])];
+                }
+            }
+            const int in = (g + 1 < ng) ? 4 * g + 4 : 4 * g;
+            uint32_t nb[4];
+            bins4<POW2>(stl, sth, in, Fl, Fh, nbins, shift, nb);
+            const float4 nx = *reinterpret_cast<const float4 *>(sx + in);
+            const bool nhaz = hazard4(nb);
+            if (!haz) {
+                accw[b[0] << 5] = s[0] + x.x;
+                accw[b[1] << 5] = s[1] + x.y;
+                accw[b[2] << 5] = s[2] + x.z;
+                accw[b[3] << 5] = s[3] + x.w;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cntw[cidx(b[u])] = (uint16_t)(c[u] + 1u);
+            } else {
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    accw[b[u] << 5] += xs[u];
+                    cntw[cidx(b[u])] = (uint16_t)(cntw[cidx(b[u])] + 1u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = nb[u];
+            x = nx;
+            haz = nhaz;
         }
     }
-    for (; i < nvalid; ++i) {
-        const uint32_t b = phase_bin<POW2>(stl[i], sth[i], Fl, Fh, nbins, shift) << 5;
-        accw[b] += sx[i];
-        cntw[b] = (uint16_t)(cntw[b] + 1u);
+    for (int i = 4 * ng; i < nvalid; ++i) {
+        const uint32_t bb = phase_bin<POW2>(stl[i], sth[i], Fl, Fh, nbins, shift);
+        accw[bb << 5] += sx[i];
+        cntw[cidx(bb)] = (uint16_t)(cntw[cidx(bb)] + 1u);
     }
 }
 
-// Fold this lane's chunk partials into the Kahan workspace. On the last chunk the
-// finished sums (sum - compensation) go back into accw and the counts into cntw
-// (saturated at 65535; the exact totals stay in the workspace). Returns true if a
-// count saturated.
+// Fold this lane's chunk partials into the Kahan workspace (sum, compensation) and the
+// exact 32-bit counts. On the last chunk the finished sums (sum - compensation) go back
+// into accw and the counts into cntw, saturated at 65535 (the exact totals stay in the
+// workspace). Workspace reads are batched 16 bins at a time to overlap their latency.
+// Returns true if a count saturated.
+__device__ __forceinline__ void flush_one(float *accw, uint16_t *cntw, float2 *wsc, uint32_t *wcn,
+                                          int b, size_t idx, bool first, bool last, float2 sc,
+                                          uint32_t cc, bool &over)
+{
+    const float p = accw[b << 5];
+    const uint32_t c = cntw[cidx(b)];
+    if (first) {
+        sc = make_float2(p, 0.f);
+        cc = c;
+    } else {
+        cc += c;
+        const float y = p - sc.y;
+        const float t = sc.x + y;
+        sc.y = (t - sc.x) - y;
+        sc.x = t;
+    }
+    if (last) {
+        accw[b << 5] = sc.x - sc.y;
+        cntw[cidx(b)] = (uint16_t)min(cc, 65535u);
+        over |= cc > 65535u;
+        if (!first) wcn[idx] = cc;
+    } else {
+        wsc[idx] = sc;
+        wcn[idx] = cc;
+        accw[b << 5] = 0.f;
+        cntw[cidx(b)] = 0;
+    }
+}
+
 __device__ __forceinline__ bool flush_chunk(float *accw, uint16_t *cntw, float2 *wsc, uint32_t *wcn,
                                             int nbins, int ppc, bool first, bool last)
 {
     bool over = false;
-#pragma unroll 4
-    for (int b = 0; b < nbins; ++b) {
-        const float p = accw[b << 5];
-        const uint32_t c = cntw[b << 5];
-        const size_t idx = (size_t)b * ppc;
-        float2 sc;
-        uint32_t cc;
-        if (first) {
-            sc = make_float2(p, 0.f);
-            cc = c;
-        } else {
+    int b0 = 0;
+    for (; b0 + 16 <= nbins; b0 += 16) {
+        float2 sc[16];
+        uint32_t cc[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            sc[u] = make_float2(0.f, 0.f);
+            cc[u] = 0u;
+            if (!first) {
+                sc[u] = wsc[(size_t)(b0 + u) * ppc];
+                cc[u] = wcn[(size_t)(b0 + u) * ppc];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            flush_one(accw, cntw, wsc, wcn, b0 + u, (size_t)(b0 + u) * ppc, first, last, sc[u], cc[u], over);
+    }
+    for (; b0 < nbins; ++b0) {
+        const size_t idx = (size_t)b0 * ppc;
+        float2 sc = make_float2(0.f, 0.f);
+        uint32_t cc = 0u;
+        if (!first) {
             sc = wsc[idx];
-            cc = wcn[idx] + c;
-            const float y = p - sc.y;
-            const float t = sc.x + y;
-            sc.y = (t - sc.x) - y;
-            sc.x = t;
+            cc = wcn[idx];
         }
-        if (last) {
-            accw[b << 5] = sc.x - sc.y;
-            cntw[b << 5] = (uint16_t)min(cc, 65535u);
-            over |= cc > 65535u;
-            wcn[idx] = cc;
-        } else {
-            wsc[idx] = sc;
-            wcn[idx] = cc;
-            accw[b << 5] = 0.f;
-            cntw[b << 5] = 0;
-        }
+        flush_one(accw, cntw, wsc, wcn, b0, idx, first, last, sc, cc, over);
     }
     return over;
 }
 
-// Box-SNR search over one profile held by this lane: bin b's centred flux sum at
-// S[b*cs], its count at C[b*cs] (or Cbig[b*cbs] when `big`). See gpfc_score_box.
-// The search runs in FP32 with running in-box sums; the winning box is then
-// re-evaluated in FP64 from the same bin sums.
-__device__ __forceinline__ void box_search(const float *S, const uint16_t *C, const uint32_t *Cbig,
-                                           size_t cbs, bool big, int cs, int nbins, int w_min,
-                                           int w_max, float sigma, float &score, int &best_s,
-                                           int &best_w)
+// Bins of one profile as seen by one lane: the fold's lane-private layout.
+struct LaneBins {
+    const float *S;        // accw
+    const uint16_t *C;     // cntw
+    const uint32_t *Cbig;  // exact counts (workspace) when a count saturated
+    size_t cbs;
+    bool big;
+    __device__ __forceinline__ float s(int b) const { return S[b << 5]; }
+    __device__ __forceinline__ float c(int b) const
+    {
+        return big ? (float)Cbig[(size_t)b * cbs] : (float)C[cidx((uint32_t)b)];
+    }
+};
+
+// Bins of one profile staged transposed for the standalone scorer ([bin][33]).
+struct StagedBins {
+    const float *S;
+    const uint16_t *C;
+    const int32_t *Cbig;   // the caller's counts row when a count exceeds 65535
+    bool big;
+    __device__ __forceinline__ float s(int b) const { return S[b * 33]; }
+    __device__ __forceinline__ float c(int b) const
+    {
+        return big ? (float)max(Cbig[b], 0) : (float)C[b * 33];
+    }
+};
+
+// Box-SNR search over one profile held by this lane (bin sums centred on a reference,
+// counts). For start s and width w the in-box sums come from running totals: starts
+// s0..s0+7 are scored in one walk over bins s0..s0+6+w_max, so every bin read serves 8
+// boxes and the 8 evaluations are independent. The search maximises
+//     v = (S n_in - S_in N) / sqrt(n_in n_out)      (= snr * sigma * sqrt(N))
+// in FP32; ties keep the smaller w, then the smaller s. The winning box is re-evaluated
+// in FP64 from the same bin sums.
+template <class Bins>
+__device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
+                                           float &score, int &best_s, int &best_w)
 {
+    constexpr int R = 8;
     float Stot = 0.f, Ntot = 0.f;
     for (int b = 0; b < nbins; ++b) {
-        Stot += S[b * cs];
-        Ntot += (float)(big ? Cbig[(size_t)b * cbs] : (uint32_t)C[b * cs]);
+        Stot += B.s(b);
+        Ntot += B.c(b);
     }
     float bv = -INFINITY;
-    int bs = -1, bw = -1;
-    for (int s = 0; s < nbins; ++s) {
-        float sin_ = 0.f, nin = 0.f;
-        int j = s;
-        for (int w = 1; w <= w_max; ++w) {
-            sin_ += S[j * cs];
-            nin += (float)(big ? Cbig[(size_t)j * cbs] : (uint32_t)C[j * cs]);
+    int bkey = 0x7fffffff;
+    auto eval = [&](float sin_, float nin, int key, bool ok) {
+        const float nout = Ntot - nin;
+        const float q = nin * nout;
+        const float D = fmaf(Stot, nin, -(sin_ * Ntot));
+        const float v = D * rsqrtf(q);
+        const bool take = ok & (q >= 1.f) & ((v > bv) | ((v == bv) & (key < bkey)));
+        bv = take ? v : bv;
+        bkey = take ? key : bkey;
+    };
+    for (int s0 = 0; s0 < nbins; s0 += R) {
+        const bool full = s0 + R <= nbins;
+        float bS[R], bN[R];
+        int cr[R];  // key = (w << 12) | s = ((t + 1) << 12) + cr[r]
+#pragma unroll
+        for (int r = 0; r < R; ++r) cr[r] = s0 + r - (r << 12);
+        float runS = 0.f, runN = 0.f;
+        int j = s0;
+        // head: t = 0..R-1; start r is entered at t = r
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            bS[t] = runS;
+            bN[t] = runN;
+            runS += B.s(j);
+            runN += B.c(j);
             j = (j + 1 == nbins) ? 0 : j + 1;
-            if (w >= w_min) {
-                const float nout = Ntot - nin;
-                const float q = nin * nout;
-                const float D = fmaf(Stot, nin, -(sin_ * Ntot));
-                const float v = D * rsqrtf(q);
-                const bool take = (q >= 1.f) & ((v > bv) | ((v == bv) & (w < bw)));
-                if (take) {
-                    bv = v;
-                    bs = s;
-                    bw = w;
-                }
+            const int T = (t + 1) << 12;
+#pragma unroll
+            for (int r = 0; r <= t; ++r) {
+                const int w = t - r + 1;
+                eval(runS - bS[r], runN - bN[r], T + cr[r],
+                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
+            }
+        }
+        const int tend = R - 1 + w_max;  // exclusive
+        int ta = max(R, w_min + R - 2);
+        int tb = max(ta, min(w_max, tend));
+        if (!full) {
+            ta = R;
+            tb = R;
+        }
+        for (int t = R; t < min(ta, tend); ++t) {
+            runS += B.s(j);
+            runN += B.c(j);
+            j = (j + 1 == nbins) ? 0 : j + 1;
+            const int T = (t + 1) << 12;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int w = t - r + 1;
+                eval(runS - bS[r], runN - bN[r], T + cr[r],
+                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
+            }
+        }
+        for (int t = ta; t < tb; ++t) {  // every (r, w) valid here
+            runS += B.s(j);
+            runN += B.c(j);
+            j = (j + 1 == nbins) ? 0 : j + 1;
+            const int T = (t + 1) << 12;
+#pragma unroll
+            for (int r = 0; r < R; ++r) eval(runS - bS[r], runN - bN[r], T + cr[r], true);
+        }
+        for (int t = max(tb, R); t < tend; ++t) {
+            runS += B.s(j);
+            runN += B.c(j);
+            j = (j + 1 == nbins) ? 0 : j + 1;
+            const int T = (t + 1) << 12;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int w = t - r + 1;
+                eval(runS - bS[r], runN - bN[r], T + cr[r],
+                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
             }
         }
     }
-    if (bs < 0) {
+    if (bkey == 0x7fffffff) {
         score = -INFINITY;
         best_s = -1;
         best_w = -1;
         return;
     }
-    // FP64 re-evaluation of the winning box: snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out))
+    const int bw = bkey >> 12, bs = bkey & 4095;
+    // FP64 re-evaluation: snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out))
     double St = 0.0, Nt = 0.0, Si = 0.0, Ni = 0.0;
     for (int b = 0; b < nbins; ++b) {
-        St += (double)S[b * cs];
-        Nt += (double)(big ? Cbig[(size_t)b * cbs] : (uint32_t)C[b * cs]);
+        St += (double)B.s(b);
+        Nt += (double)B.c(b);
     }
     int j = bs;
     for (int w = 0; w < bw; ++w) {
-        Si += (double)S[j * cs];
-        Ni += (double)(big ? Cbig[(size_t)j * cbs] : (uint32_t)C[j * cs]);
+        Si += (double)B.s(j);
+        Ni += (double)B.c(j);
         j = (j + 1 == nbins) ? 0 : j + 1;
     }
     const double No = Nt - Ni;
-    const double snr = (St * Ni - Si * Nt) / ((double)sigma * sqrt(Nt * Ni * No));
-    score = (float)snr;
+    score = (float)((St * Ni - Si * Nt) / ((double)sigma * sqrt(Nt * Ni * No)));
     best_s = bs;
     best_w = bw;
 }
@@ -361,9 +507,10 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
     uint32_t *th_buf = tl_buf + 2 * kTile;
     float *x_buf = reinterpret_cast<float *>(th_buf + 2 * kTile);
     float *acc = x_buf + 2 * kTile;
+    const int nb2 = (nbins + 1) & ~1;
     uint16_t *cnt = reinterpret_cast<uint16_t *>(acc + (size_t)p.warps * nbins * 32);
     float *accw = acc + (size_t)warp * nbins * 32 + lane;
-    uint16_t *cntw = cnt + (size_t)warp * nbins * 32 + lane;
+    uint16_t *cntw = cnt + (size_t)warp * nb2 * 32 + 2 * lane;
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -412,7 +559,7 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
         }
         for (int b = 0; b < nbins; ++b) {
             accw[b << 5] = 0.f;
-            cntw[b << 5] = 0;
+            cntw[cidx(b)] = 0;
         }
         const int ntiles = (int)((nsamp + kTile - 1) / kTile);
         auto issue = [&](int t, int buf) {
@@ -430,6 +577,8 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
             if (ntiles > 1) issue(1, 1);
         }
         bool over = false;
+        bool first_flush = true;
+        int chunk_left = p.chunk;
         for (int t = 0; t < ntiles; ++t) {
             const int buf = t & 1;
             const bool ok = mbar_wait_bounded(&bars[buf], (parity_bits >> buf) & 1u);
@@ -439,12 +588,23 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
                 report_error(p.status, kErrTimeout);
             } else {
                 const int nv = (int)min((int64_t)kTile, nsamp - (int64_t)t * kTile);
-                fold_tile<POW2>(tl_buf + buf * kTile, th_buf + buf * kTile, x_buf + buf * kTile, nv,
-                                accw, cntw, Fl, Fh, (uint32_t)nbins, p.shift);
-                const bool last = (t == ntiles - 1);
-                if (last || ((t + 1) % p.chunk_tiles) == 0) {
-                    over = flush_chunk(accw, cntw, wsc_cta, wcn_cta, nbins, ppc,
-                                       t + 1 <= p.chunk_tiles, last);
+                const uint32_t *stl = tl_buf + buf * kTile;
+                const uint32_t *sth = th_buf + buf * kTile;
+                const float *sx = x_buf + buf * kTile;
+                int i = 0;
+                while (i < nv) {
+                    // segments end at chunk boundaries (multiples of 4 samples) or the tile end
+                    const int seg = min(nv - i, chunk_left);
+                    fold_tile<POW2>(stl + i, sth + i, sx + i, seg, accw, cntw, Fl, Fh, (uint32_t)nbins,
+                                    p.shift);
+                    i += seg;
+                    chunk_left -= seg;
+                    const bool last = (t == ntiles - 1) && (i == nv);
+                    if (chunk_left == 0 || last) {
+                        over = flush_chunk(accw, cntw, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
+                        first_flush = false;
+                        chunk_left = p.chunk;
+                    }
                 }
             }
             __syncthreads();
@@ -457,7 +617,7 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
             if (kvalid) {
                 const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
                 for (int b = 0; b < nbins; ++b) {
-                    const uint32_t c = over ? wcn_cta[(size_t)b * ppc] : (uint32_t)cntw[b << 5];
+                    const uint32_t c = over ? wcn_cta[(size_t)b * ppc] : (uint32_t)cntw[cidx(b)];
                     const float S = accw[b << 5];
                     const float mean = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
                     if (p.folded) p.folded[(size_t)k * nbins + b] = mean;
@@ -471,8 +631,8 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
                 float sig = p.sigma_user;
                 if (!(sig > 0.f)) sig = p.stats[s].sigma;
                 if (!(sig > 0.f)) sig = 1.f;
-                box_search(accw, cntw, wcn_cta, (size_t)ppc, over, 32, nbins, p.w_min, p.w_max, sig,
-                           sc, bs, bw);
+                const LaneBins B{accw, cntw, wcn_cta, (size_t)ppc, over};
+                box_search(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
                 p.score[k] = sc;
                 if (p.best_s) p.best_s[k] = bs;
                 if (p.best_w) p.best_w[k] = bw;
@@ -490,7 +650,7 @@ template <int MODE, bool POW2>
 static cudaError_t set_smem_attr()
 {
     return cudaFuncSetAttribute(fold_kernel<MODE, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmemLimit);
+                                (int)(kSmemLimit - 1024));
 }
 
 int fold_register_kernels()
@@ -505,7 +665,8 @@ int fold_register_kernels()
 
 size_t fold_smem_bytes(int nbins, int warps)
 {
-    return 128 + (size_t)2 * kTile * 12 + (size_t)warps * nbins * 32 * 6;
+    const size_t nb2 = (size_t)((nbins + 1) & ~1);
+    return 128 + (size_t)2 * kTile * 12 + (size_t)warps * 32 * (nbins * 4 + nb2 * 2);
 }
 
 int fold_max_warps(int nbins)
@@ -548,13 +709,14 @@ __global__ void __launch_bounds__(kBoxWarps * 32) box_kernel(const float *__rest
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     float *Sw = reinterpret_cast<float *>(smem) + (size_t)warp * nbins * 33;
     uint16_t *Cw = reinterpret_cast<uint16_t *>(reinterpret_cast<float *>(smem) +
-                                                 (size_t)kBoxWarps * nbins * 33) +
+                                                 (size_t)nwarps * nbins * 33) +
                    (size_t)warp * nbins * 33;
     const int64_t nblocks = (np + 31) / 32;
-    for (int64_t blk = (int64_t)blockIdx.x * kBoxWarps + warp; blk < nblocks;
-         blk += (int64_t)gridDim.x * kBoxWarps) {
+    for (int64_t blk = (int64_t)blockIdx.x * nwarps + warp; blk < nblocks;
+         blk += (int64_t)gridDim.x * nwarps) {
         const int64_t k0 = blk * 32;
         const int nk = (int)min((int64_t)32, np - k0);
         bool big_lane = false;
@@ -597,8 +759,8 @@ __global__ void __launch_bounds__(kBoxWarps * 32) box_kernel(const float *__rest
             const int64_t k = k0 + lane;
             float sc;
             int bs, bw;
-            box_search(Sw + lane, Cw + lane, reinterpret_cast<const uint32_t *>(counts + (size_t)k * nbins),
-                       1, big_lane, 33, nbins, w_min, w_max, sigma, sc, bs, bw);
+            const StagedBins B{Sw + lane, Cw + lane, counts + (size_t)k * nbins, big_lane};
+            box_search(B, nbins, w_min, w_max, sigma, sc, bs, bw);
             score[k] = sc;
             if (best_s) best_s[k] = bs;
             if (best_w) best_w[k] = bw;
@@ -612,21 +774,23 @@ cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, in
                                   int32_t *best_w, cudaStream_t st)
 {
     static bool attr = false;
-    const size_t smem = (size_t)kBoxWarps * nbins * 33 * 6;
+    int warps = kBoxWarps;
+    while (warps > 1 && (size_t)warps * nbins * 33 * 6 > kSmemLimit - 1024) --warps;
+    const size_t smem = (size_t)warps * nbins * 33 * 6;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemLimit);
+                                             (int)(kSmemLimit - 1024));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (smem > kSmemLimit) return cudaErrorInvalidValue;
+    if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t nblocks = (np + 31) / 32;
-    const int64_t want = (nblocks + kBoxWarps - 1) / kBoxWarps;
+    const int64_t want = (nblocks + warps - 1) / warps;
     const int grid = (int)(want < (int64_t)sms * 2 ? want : (int64_t)sms * 2);
-    box_kernel<<<grid, kBoxWarps * 32, smem, st>>>(folded, counts, np, nbins, w_min, w_max, sigma,
+    box_kernel<<<grid, warps * 32, smem, st>>>(folded, counts, np, nbins, w_min, w_max, sigma,
                                                    score, best_s, best_w);
     return cudaGetLastError();
 }

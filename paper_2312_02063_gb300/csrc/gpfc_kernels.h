@@ -16,7 +16,8 @@ enum : uint32_t {
 constexpr int kTile = 1024;            // light-curve samples per bulk-copy tile
 constexpr int kMaxFoldWarps = 16;      // warps per fold block (32 periods each)
 constexpr int kMaxNbinsLane = 1024;    // largest nbins of the lane-private fold
-constexpr size_t kSmemLimit = 232448;  // opt-in dynamic shared memory per block (227 KB)
+constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block (227 KB); kernels ask
+                                       // for at most kSmemLimit - 1024 dynamic bytes
 
 // Per-star statistics written by the prep kernels.
 struct StarStats {
@@ -50,7 +51,7 @@ struct FoldParams {
     int nbins;
     int shift;                 // 32 - log2(nbins) if nbins is a power of two, else -1
     int warps;                 // warps per block; periods per block = 32 * warps
-    int chunk_tiles;           // tiles per shared-memory chunk (<= 63)
+    int chunk;                 // samples per shared-memory chunk: multiple of 4, <= 65532
     float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
     // kModeFold outputs ([global period][nbins])

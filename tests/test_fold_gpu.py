@@ -190,6 +190,45 @@ def test_score_box_standalone_matches_oracle(ctx):
         assert abs(v - sc_o[k]) <= BOX_RTOL * max(abs(sc_o[k]), 1.0)
 
 
+@pytest.mark.parametrize("nbins,w_min,w_max", [(64, 1, 8), (100, 3, 17), (37, 2, 37), (256, 5, 108),
+                                               (8, 1, 8), (13, 4, 4), (1024, 1, 40)])
+def test_score_box_width_ranges_and_odd_bins(ctx, nbins, w_min, w_max):
+    import paper_2312_02063_gb300 as g
+    rng = np.random.default_rng(nbins * 1000 + w_min * 10 + w_max)
+    n = 203
+    counts = rng.integers(0, 30, (n, nbins)).astype(np.int32)
+    counts[rng.random((n, nbins)) < 0.1] = 0
+    prof = (1.0 + rng.normal(0, 1e-3, (n, nbins))).astype(np.float32)
+    for k in range(0, n, 3):  # some boxes
+        st, w = rng.integers(0, nbins), rng.integers(1, max(2, nbins // 3))
+        prof[k, (st + np.arange(w)) % nbins] -= 3e-3
+    prof = np.where(counts > 0, prof, np.nan).astype(np.float32)
+    sc, bs, bw = g.gpfc_score_box(ctx, _dev(ctx, prof), _dev(ctx, counts), w_min, w_max, 1e-3)
+    ctx.sync()
+    sc_o, _, _ = oracle.box_snr_from_means(prof, counts, w_min, w_max, 1e-3)
+    check_box(sc.cpu().numpy(), sc_o)
+    bs, bw = bs.cpu().numpy(), bw.cpu().numpy()
+    sums = np.where(counts > 0, prof.astype(np.float64) * counts, 0.0)
+    for k in range(n):
+        if np.isfinite(sc_o[k]):
+            assert w_min <= bw[k] <= w_max and 0 <= bs[k] < nbins
+            v = oracle.box_snr_at(sums[k], counts[k], int(bs[k]), int(bw[k]), 1e-3)
+            assert abs(v - sc_o[k]) <= BOX_RTOL * max(abs(sc_o[k]), 1.0)
+
+
+def test_search_box_odd_bins_and_width_range(ctx):
+    import paper_2312_02063_gb300 as g
+    lc = lcsynth.light_curve_tiny(5)
+    periods = lcsynth.freq_grid(333)
+    for nbins, w_min, w_max in ((100, 3, 17), (64, 2, 64), (7, 1, 6)):
+        score, _, _ = g.gpfc_search(ctx, _dev(ctx, lc.times), _dev(ctx, lc.flux), _dev(ctx, periods), nbins,
+                                    lc.t0, g.SCORER_BOX, w_min, w_max, 2e-4)
+        ctx.sync()
+        _, cnt_o, sum_o = oracle.fold(lc.times, lc.flux, periods, nbins, lc.t0)
+        sc_o, _, _ = oracle.box_snr(sum_o, cnt_o, w_min, w_max, 2e-4)
+        check_box(score.cpu().numpy(), sc_o)
+
+
 def test_score_box_degenerate_profiles(ctx):
     import paper_2312_02063_gb300 as g
     nb = 64
