@@ -74,6 +74,25 @@ int gpfc_num_sms(const gpfc_ctx *ctx);
 int gpfc_set_timing(gpfc_ctx *ctx, int enable);
 int gpfc_kernel_time_ms(gpfc_ctx *ctx, float *ms);
 
+/* Launch configuration of the fold kernel (gpfc_fold, gpfc_search). Every field 0
+ * means "automatic". The results do not depend on it except for the FP32 rounding of
+ * the per-chunk partial sums (chunk).
+ *   warps   warps per block, 32 trial periods per warp (1..16, capped by shared memory)
+ *   layout  shared-memory bins: 1 = FP32 sum + 16-bit count (6 B per bin),
+ *           2 = FP32 sum + 32-bit count in one 64-bit word (8 B per bin)
+ *   chunk   samples per compensated chunk (rounded down to a multiple of 16, 256..65520) */
+typedef struct {
+    int32_t warps;
+    int32_t layout;
+    int32_t chunk;
+} gpfc_fold_config;
+
+/* Set (cfg != NULL) or reset to automatic (cfg == NULL) the context's fold config. */
+int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg);
+
+/* Largest `warps` the fold kernel fits in shared memory for nbins and layout (0 if none). */
+int gpfc_fold_max_warps(int32_t nbins, int32_t layout);
+
 /* ------------------------------------------------------------------ fold
  * Phase fold (Sec. 2.3: modular residual of each timestamp by the trial period, map to
  * a bin, per-bin count and flux sum, mean = sum / count), with equal-width bins and the

@@ -36,6 +36,14 @@ class GpfcError(RuntimeError):
         self.code = code
 
 
+class FoldConfig(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int32), ("layout", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
+LAYOUT_PAIRED16 = 1
+LAYOUT_PACKED64 = 2
+
+
 class BoxParams(ctypes.Structure):
     _fields_ = [("w_min", ctypes.c_int32), ("w_max", ctypes.c_int32), ("sigma", ctypes.c_double)]
 
@@ -71,6 +79,8 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_last_error.restype = ctypes.c_char_p
         L.gpfc_sync.argtypes = [_vp]
         L.gpfc_num_sms.argtypes = [_vp]
+        L.gpfc_set_fold_config.argtypes = [_vp, ctypes.POINTER(FoldConfig)]
+        L.gpfc_fold_max_warps.argtypes = [ctypes.c_int32, ctypes.c_int32]
         L.gpfc_set_timing.argtypes = [_vp, ctypes.c_int]
         L.gpfc_kernel_time_ms.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
         L.gpfc_fold.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
@@ -141,6 +151,17 @@ class Context:
 
     def sync(self):
         self._check(self.lib.gpfc_sync(self.handle))
+
+    def set_fold_config(self, warps=0, layout=0, chunk=0):
+        """Fold launch configuration; 0 means automatic for each field."""
+        cfg = FoldConfig(int(warps), int(layout), int(chunk))
+        self._check(self.lib.gpfc_set_fold_config(self.handle, ctypes.byref(cfg)))
+
+    def reset_fold_config(self):
+        self._check(self.lib.gpfc_set_fold_config(self.handle, None))
+
+    def fold_max_warps(self, nbins, layout):
+        return int(self.lib.gpfc_fold_max_warps(int(nbins), int(layout)))
 
     def set_timing(self, enable: bool):
         self._check(self.lib.gpfc_set_timing(self.handle, int(bool(enable))))

@@ -23,6 +23,7 @@ struct gpfc_ctx {
     size_t ws_bytes = 0;
     uint32_t *status_host = nullptr;  // mapped pinned memory
     uint32_t *status_dev = nullptr;
+    gpfc_fold_config fold_cfg{0, 0, 0};
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
@@ -112,17 +113,31 @@ int ensure_ws(gpfc_ctx *ctx, size_t bytes)
 }
 
 struct FoldPlan {
-    int warps, ppc, grid, G;
+    int warps, ppc, grid, G, layout, chunk;
     int64_t ntasks;
 };
+
+int default_layout(int nbins)
+{
+    (void)nbins;
+    return kLayoutPaired16;
+}
 
 FoldPlan plan_fold(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins)
 {
     FoldPlan pl{};
-    const int maxw = fold_max_warps(nbins);
+    const gpfc_fold_config &cfg = ctx->fold_cfg;
+    pl.layout = cfg.layout ? cfg.layout : default_layout(nbins);
+    if (fold_max_warps(nbins, pl.layout) < 1) pl.layout = kLayoutPaired16;
+    const int maxw = fold_max_warps(nbins, pl.layout);
     // enough blocks to cover the SMs when the grid is short, else the widest block
     int64_t per_sm = (np + (int64_t)32 * ctx->num_sms - 1) / ((int64_t)32 * ctx->num_sms);
     int w = (int)std::min<int64_t>(maxw, std::max<int64_t>(1, per_sm));
+    if (cfg.warps > 0) w = std::min(cfg.warps, maxw);
+    // ~64 samples per bin per chunk keeps the plain FP32 partials short; the chunk
+    // partials are then added with Kahan compensation
+    int64_t chunk = cfg.chunk > 0 ? cfg.chunk : (int64_t)64 * nbins;
+    pl.chunk = (int)std::min<int64_t>(65520, std::max<int64_t>(256, chunk)) & ~15;
     pl.warps = w;
     pl.ppc = 32 * w;
     pl.ntasks = (np + pl.ppc - 1) / pl.ppc;
@@ -144,12 +159,13 @@ size_t carve_fold(void *base, const FoldPlan &pl, int64_t n_total, int nstars, i
                   FoldBuffers &fb)
 {
     Carver c(base);
-    fb.partial = c.take<double>((size_t)2 * nstars * pl.G);
+    fb.partial = c.take<double>((size_t)3 * nstars * pl.G);  // sums, squares, min steps
     fb.stats = c.take<StarStats>(nstars);
     const int64_t se = scratch_elems(n_total, nstars);
     fb.smp.tau_lo = c.take<uint32_t>(se);
     fb.smp.tau_hi = c.take<int32_t>(se);
     fb.smp.x = c.take<float>(se);
+    fb.smp.flags = c.take<uint8_t>(se / 16 + 64);
     fb.ws_sc = c.take<float2>((size_t)pl.grid * nbins * pl.ppc);
     fb.ws_cnt = c.take<uint32_t>((size_t)pl.grid * nbins * pl.ppc);
     fb.key = c.take<unsigned long long>(nstars);
@@ -165,7 +181,7 @@ int check_fold_args(gpfc_ctx *ctx, const double *times, const float *flux, int64
     if (np < 1 || np > (int64_t)INT32_MAX)
         return set_err(ctx, GPFC_EINVAL, "n_periods = %lld outside [1, 2^31-1]", (long long)np);
     if (nbins < 2) return set_err(ctx, GPFC_EINVAL, "nbins = %d < 2", nbins);
-    if (nbins > kMaxNbinsLane || fold_max_warps(nbins) < 1)
+    if (nbins > kMaxNbinsLane || fold_max_warps(nbins, kLayoutPaired16) < 1)
         return set_err(ctx, GPFC_ENOTSUP, "nbins = %d > %d", nbins, kMaxNbinsLane);
     return GPFC_OK;
 }
@@ -205,9 +221,8 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     p.nbins = nbins;
     p.shift = shift_of(nbins);
     p.warps = pl.warps;
-    // ~64 samples per bin per chunk keeps the plain FP32 partials short; the chunk
-    // partials are then added with Kahan compensation
-    p.chunk = (int)std::min<int64_t>(65532, std::max<int64_t>(256, (int64_t)64 * nbins)) & ~3;
+    p.chunk = pl.chunk;
+    p.layout = pl.layout;
     p.ws_sc = fb.ws_sc;
     p.ws_cnt = fb.ws_cnt;
     p.status = ctx->status_dev;
@@ -285,6 +300,26 @@ void gpfc_destroy(gpfc_ctx *ctx)
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
     delete ctx;
+}
+
+int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!cfg) {
+        ctx->fold_cfg = gpfc_fold_config{0, 0, 0};
+        return GPFC_OK;
+    }
+    if (cfg->warps < 0 || cfg->warps > kMaxFoldWarps || cfg->layout < 0 || cfg->layout > 2 ||
+        cfg->chunk < 0 || cfg->chunk > 65520)
+        return set_err(ctx, GPFC_EINVAL, "fold config out of range");
+    ctx->fold_cfg = *cfg;
+    return GPFC_OK;
+}
+
+int gpfc_fold_max_warps(int32_t nbins, int32_t layout)
+{
+    if (nbins < 2 || nbins > kMaxNbinsLane || layout < 1 || layout > 2) return 0;
+    return fold_max_warps(nbins, layout);
 }
 
 int gpfc_set_timing(gpfc_ctx *ctx, int enable)

@@ -21,8 +21,10 @@
 // Epilogues, same kernel: write means + counts (gpfc_fold), or run the box-SNR search
 // over the finished profile of each lane's period (gpfc_search, box scorer).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "gpfc_common.cuh"
 #include "gpfc_kernels.h"
@@ -46,11 +48,12 @@ __device__ __forceinline__ void star_range(const int64_t *off, int64_t n, int s,
     }
 }
 
-// First element of star s in the sample scratch: a multiple of 4 (16 bytes), with room
-// for the star's samples rounded up to a multiple of 4.
+// First element of star s in the sample scratch: a multiple of 256 (so its per-16-sample
+// flags start on a 16-byte boundary), with room for the star's samples rounded up to a
+// multiple of 256.
 __device__ __forceinline__ int64_t scratch_start(int64_t lc_begin, int s)
 {
-    return 4 * ((lc_begin + 3) / 4 + s);
+    return 256 * ((lc_begin + 255) / 256 + s);
 }
 
 // ------------------------------------------------------------------ prep
@@ -88,11 +91,20 @@ __global__ void prep_sum_kernel(const float *flux, const int64_t *lc_off, int64_
 }
 
 // Pass 2: f_ref = mean flux; quantise times; centre flux; partial sums of squares.
+__device__ __forceinline__ long long quantise_time(double t, double t0, bool &bad)
+{
+    const double v = (t - t0) * kTwo24;
+    if (fabs(v) < kTwo62) return __double2ll_rn(v);
+    bad = true;
+    return 0;
+}
+
 __global__ void prep_quant_kernel(const double *times, const float *flux, const int64_t *lc_off,
                                   int64_t n, const double *t0s, double t0_scalar, double *partial,
-                                  SampleScratch smp, StarStats *stats, uint32_t *status)
+                                  long long *pmin, SampleScratch smp, StarStats *stats, uint32_t *status)
 {
     __shared__ double red[32];
+    __shared__ long long redm[32];
     __shared__ double s_fref;
     const int s = blockIdx.y;
     const int G = gridDim.x;
@@ -114,11 +126,13 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
     const int64_t j1 = min(len, j0 + per);
     double acc = 0.0;
     bool bad = false;
+    long long dmin = LLONG_MAX;  // smallest positive step tau_j - tau_{j-1}
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const double v = (times[b + j] - t0) * kTwo24;
-        long long tau = 0;
-        if (fabs(v) < kTwo62) tau = __double2ll_rn(v);
-        else bad = true;
+        const long long tau = quantise_time(times[b + j], t0, bad);
+        if (j > 0) {
+            const long long d = tau - quantise_time(times[b + j - 1], t0, bad);
+            if (d > 0 && d < dmin) dmin = d;
+        }
         smp.tau_lo[base + j] = (uint32_t)(unsigned long long)tau;
         smp.tau_hi[base + j] = (int32_t)(tau >> 32);
         const double d = (double)flux[b + j] - f_ref;
@@ -126,18 +140,28 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
         acc += d * d;
     }
     if (bad) report_error(status, kErrRange);
-    // zero the (at most 3) padding elements after the star so tile copies read defined data
-    if (blockIdx.x == 0 && threadIdx.x < 4) {
-        const int64_t j = len + threadIdx.x;
-        if (j < ((len + 3) & ~(int64_t)3)) {
+    // zero the padding after the star (up to the next multiple of 256) so tile copies read
+    // defined data
+    if (blockIdx.x == 0) {
+        for (int64_t j = len + threadIdx.x; j < ((len + 255) & ~(int64_t)255); j += blockDim.x) {
             smp.tau_lo[base + j] = 0u;
             smp.tau_hi[base + j] = 0;
             smp.x[base + j] = 0.f;
         }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long u = __shfl_down_sync(0xffffffffu, dmin, o);
+        dmin = u < dmin ? u : dmin;
+    }
+    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = dmin;
     double t = block_sum_f64(acc, red);
     __syncthreads();
-    if (threadIdx.x == 0) partial[(size_t)gridDim.y * G + (size_t)s * G + blockIdx.x] = t;
+    if (threadIdx.x == 0) {
+        partial[(size_t)gridDim.y * G + (size_t)s * G + blockIdx.x] = t;
+        long long m = LLONG_MAX;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = redm[w] < m ? redm[w] : m;
+        pmin[(size_t)s * G + blockIdx.x] = m;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[s].f_ref = f_ref;
         const float hi = (float)f_ref;
@@ -147,14 +171,53 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
     }
 }
 
-// Pass 3: sigma = sqrt(sum (flux - f_ref)^2 / n) per star. grid = stars, 32 threads.
-__global__ void prep_sigma_kernel(const double *partial, int G, int nstars, StarStats *stats)
+// Pass 3: sigma = sqrt(sum (flux - f_ref)^2 / n) and the smallest positive time step
+// per star. grid = stars, 32 threads.
+__global__ void prep_sigma_kernel(const double *partial, const long long *pmin, int G, int nstars,
+                                  StarStats *stats)
 {
     const int s = blockIdx.x;
     if (threadIdx.x != 0) return;
     double t = 0.0;
-    for (int g = 0; g < G; ++g) t += partial[(size_t)nstars * G + (size_t)s * G + g];
+    long long m = LLONG_MAX;
+    for (int g = 0; g < G; ++g) {
+        t += partial[(size_t)nstars * G + (size_t)s * G + g];
+        const long long v = pmin[(size_t)s * G + g];
+        m = v < m ? v : m;
+    }
     stats[s].sigma = (float)sqrt(t / (double)stats[s].n);
+    stats[s].dtau0 = m == LLONG_MAX ? 0 : m;
+}
+
+// Pass 4: one flag byte per group of 16 samples: 1 if every step inside the group lies in
+// [dtau0, dtau0 + 2] (a regular cadence up to the 2^-24 d rounding of tau). The fold
+// skips its per-group bin-collision check on flagged groups when the period allows it.
+// grid = (G, stars).
+__global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratch smp,
+                                  const StarStats *stats)
+{
+    const int s = blockIdx.y;
+    int64_t b, e;
+    star_range(lc_off, n, s, b, e);
+    const int64_t len = e - b;
+    const int64_t base = scratch_start(b, s);
+    const long long d0 = stats[s].dtau0;
+    const int64_t ngroups = (len + 255) / 256 * 16;  // every flag byte of the star's region
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ngroups;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j0 = q * 16;
+        bool reg = d0 > 0 && j0 + 16 <= len;
+        if (reg) {
+            long long prev = ((long long)smp.tau_hi[base + j0] << 32) | smp.tau_lo[base + j0];
+            for (int k = 1; k < 16; ++k) {
+                const long long cur = ((long long)smp.tau_hi[base + j0 + k] << 32) | smp.tau_lo[base + j0 + k];
+                const long long d = cur - prev;
+                reg &= (d >= d0) & (d <= d0 + 2);
+                prev = cur;
+            }
+        }
+        smp.flags[base / 16 + q] = reg ? 1 : 0;
+    }
 }
 
 cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
@@ -163,10 +226,12 @@ cudaError_t launch_prep(const double *times, const float *flux, const int64_t *l
 {
     (void)max_len;
     dim3 grid(G, nstars);
+    long long *pmin = reinterpret_cast<long long *>(partial + (size_t)2 * nstars * G);
     prep_sum_kernel<<<grid, 256, 0, st>>>(flux, lc_off, n, partial);
-    prep_quant_kernel<<<grid, 256, 0, st>>>(times, flux, lc_off, n, t0s, t0, partial, smp, stats,
+    prep_quant_kernel<<<grid, 256, 0, st>>>(times, flux, lc_off, n, t0s, t0, partial, pmin, smp, stats,
                                             status);
-    prep_sigma_kernel<<<nstars, 32, 0, st>>>(partial, G, nstars, stats);
+    prep_sigma_kernel<<<nstars, 32, 0, st>>>(partial, pmin, G, nstars, stats);
+    prep_flags_kernel<<<grid, 256, 0, st>>>(lc_off, n, smp, stats);
     return cudaGetLastError();
 }
 
@@ -186,102 +251,252 @@ __device__ __forceinline__ uint32_t phase_bin(uint32_t tl, uint32_t th, uint32_t
     return (uint32_t)(t >> 32);
 }
 
-// Lane-private bins. The FP32 partial sum of bin b is at accw[b * 32] (bank = lane).
-// 16-bit counts are paired per lane: word (b / 2) * 32 + lane holds bins 2j and 2j+1,
-// so a warp's count accesses also hit 32 distinct banks whatever the bins.
+// Lane-private bin stores. Element (b, lane) sits at index b * 32 + lane, so the 32
+// lanes of a warp touch 32 distinct banks whatever bins they hit.
 __device__ __forceinline__ uint32_t cidx(uint32_t b) { return ((b >> 1) << 6) | (b & 1u); }
 
-template <bool POW2>
-__device__ __forceinline__ void bins4(const uint32_t *__restrict__ stl, const uint32_t *__restrict__ sth,
-                                      int i, uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift,
-                                      uint32_t (&b)[4])
+// FP32 partial sums plus 16-bit counts (6 bytes per bin): counts are paired per lane,
+// word (b / 2) * 32 + lane holds bins 2j and 2j+1, which keeps count accesses
+// conflict-free too. Counts of one chunk stay below 65536.
+struct StorePaired16 {
+    float *acc;     // sums, lane offset applied
+    uint16_t *cnt;  // counts, 2 * lane offset applied
+    static constexpr bool kSaturates = true;
+    __device__ __forceinline__ void load(uint32_t b, float &s, uint32_t &c) const
+    {
+        s = acc[b << 5];
+        c = cnt[cidx(b)];
+    }
+    __device__ __forceinline__ void put(uint32_t b, float s, uint32_t c) const
+    {
+        acc[b << 5] = s;
+        cnt[cidx(b)] = (uint16_t)c;
+    }
+    __device__ __forceinline__ float sum(uint32_t b) const { return acc[b << 5]; }
+    __device__ __forceinline__ uint32_t count(uint32_t b) const { return cnt[cidx(b)]; }
+};
+
+// FP32 sum and 32-bit count packed in one 64-bit word (8 bytes per bin): one shared
+// load and one store per update.
+struct StorePacked64 {
+    uint2 *v;  // lane offset applied
+    static constexpr bool kSaturates = false;
+    __device__ __forceinline__ void load(uint32_t b, float &s, uint32_t &c) const
+    {
+        const uint2 t = v[b << 5];
+        s = __uint_as_float(t.x);
+        c = t.y;
+    }
+    __device__ __forceinline__ void put(uint32_t b, float s, uint32_t c) const
+    {
+        v[b << 5] = make_uint2(__float_as_uint(s), c);
+    }
+    __device__ __forceinline__ float sum(uint32_t b) const { return __uint_as_float(v[b << 5].x); }
+    __device__ __forceinline__ uint32_t count(uint32_t b) const { return v[b << 5].y; }
+};
+
+// Tile data of U consecutive samples, held in registers.
+template <int U>
+struct TileRegs {
+    uint4 a[U / 4];   // tau low words
+    uint4 h[U / 4];   // tau high words
+    float4 f[U / 4];  // flux - f_ref
+};
+
+template <int U>
+__device__ __forceinline__ void load_tile_regs(const uint32_t *__restrict__ stl,
+                                               const uint32_t *__restrict__ sth,
+                                               const float *__restrict__ sx, int i, TileRegs<U> &T)
 {
-    const uint4 a = *reinterpret_cast<const uint4 *>(stl + i);
-    const uint4 h = *reinterpret_cast<const uint4 *>(sth + i);
-    b[0] = phase_bin<POW2>(a.x, h.x, Fl, Fh, nbins, shift);
-    b[1] = phase_bin<POW2>(a.y, h.y, Fl, Fh, nbins, shift);
-    b[2] = phase_bin<POW2>(a.z, h.z, Fl, Fh, nbins, shift);
-    b[3] = phase_bin<POW2>(a.w, h.w, Fl, Fh, nbins, shift);
+#pragma unroll
+    for (int q = 0; q < U / 4; ++q) {
+        T.a[q] = *reinterpret_cast<const uint4 *>(stl + i + 4 * q);
+        T.h[q] = *reinterpret_cast<const uint4 *>(sth + i + 4 * q);
+        T.f[q] = *reinterpret_cast<const float4 *>(sx + i + 4 * q);
+    }
 }
 
-__device__ __forceinline__ bool hazard4(const uint32_t (&b)[4])
+template <bool POW2, int U>
+__device__ __forceinline__ void bins_from_regs(const TileRegs<U> &T, uint32_t Fl, uint32_t Fh, uint32_t nbins,
+                                               int shift, uint32_t (&b)[U], float (&x)[U])
 {
-    return (b[0] == b[1]) | (b[0] == b[2]) | (b[0] == b[3]) | (b[1] == b[2]) | (b[1] == b[3]) |
-           (b[2] == b[3]);
+#pragma unroll
+    for (int q = 0; q < U / 4; ++q) {
+        b[4 * q + 0] = phase_bin<POW2>(T.a[q].x, T.h[q].x, Fl, Fh, nbins, shift);
+        b[4 * q + 1] = phase_bin<POW2>(T.a[q].y, T.h[q].y, Fl, Fh, nbins, shift);
+        b[4 * q + 2] = phase_bin<POW2>(T.a[q].z, T.h[q].z, Fl, Fh, nbins, shift);
+        b[4 * q + 3] = phase_bin<POW2>(T.a[q].w, T.h[q].w, Fl, Fh, nbins, shift);
+        x[4 * q + 0] = T.f[q].x;
+        x[4 * q + 1] = T.f[q].y;
+        x[4 * q + 2] = T.f[q].z;
+        x[4 * q + 3] = T.f[q].w;
+    }
 }
 
-// Fold nvalid samples of a staged tile into this lane's bins. Groups of 4 samples are
-// software-pipelined: the bin reads of group g are issued, then the phases and bins of
-// group g+1 are computed while they are in flight, then group g is written back. If two
-// samples of a group share a bin the group is applied one sample at a time.
-template <bool POW2>
+template <int U>
+__device__ __forceinline__ bool hazard_u(const uint32_t (&b)[U])
+{
+    bool h = false;
+#pragma unroll
+    for (int u = 1; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < u; ++v) h |= (b[u] == b[v]);
+    return h;
+}
+
+// Fold nvalid samples of a staged tile into this lane's bins, U samples per group, as a
+// three-stage software pipeline: while the bin reads of group g are in flight, the tile
+// data of group g+2 is fetched and the bins of group g+1 are computed from registers;
+// then group g is written back. A group in which two samples share a bin is applied
+// one sample at a time.
+template <bool POW2, class St, int U>
 __device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
                                           const uint32_t *__restrict__ sth,
-                                          const float *__restrict__ sx, int nvalid, float *accw,
-                                          uint16_t *cntw, uint32_t Fl, uint32_t Fh,
-                                          uint32_t nbins, int shift)
+                                          const float *__restrict__ sx, int nvalid, const St &st,
+                                          uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift)
 {
-    const int ng = nvalid >> 2;
+    const int ng = nvalid / U;
     if (ng > 0) {
-        uint32_t b[4];
-        bins4<POW2>(stl, sth, 0, Fl, Fh, nbins, shift, b);
-        float4 x = *reinterpret_cast<const float4 *>(sx);
-        bool haz = hazard4(b);
+        uint32_t b[U];
+        float x[U];
+        TileRegs<U> T1;
+        load_tile_regs<U>(stl, sth, sx, 0, T1);
+        bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, b, x);
+        bool haz = hazard_u<U>(b);
+        load_tile_regs<U>(stl, sth, sx, ng > 1 ? U : 0, T1);
 #pragma unroll 1
         for (int g = 0; g < ng; ++g) {
-            float s[4];
-            uint32_t c[4];
+            float s[U];
+            uint32_t c[U];
             if (!haz) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    s[u] = accw[b[u] << 5];
-                    c[u] = cntw[cidx(b[u])];
-                }
+                for (int u = 0; u < U; ++u) st.load(b[u], s[u], c[u]);
             }
-            const int in = (g + 1 < ng) ? 4 * g + 4 : 4 * g;
-            uint32_t nb[4];
-            bins4<POW2>(stl, sth, in, Fl, Fh, nbins, shift, nb);
-            const float4 nx = *reinterpret_cast<const float4 *>(sx + in);
-            const bool nhaz = hazard4(nb);
+            TileRegs<U> T2;
+            load_tile_regs<U>(stl, sth, sx, U * min(g + 2, ng - 1), T2);
+            uint32_t nb[U];
+            float nx[U];
+            bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, nb, nx);
+            const bool nhaz = hazard_u<U>(nb);
             if (!haz) {
-                accw[b[0] << 5] = s[0] + x.x;
-                accw[b[1] << 5] = s[1] + x.y;
-                accw[b[2] << 5] = s[2] + x.z;
-                accw[b[3] << 5] = s[3] + x.w;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) cntw[cidx(b[u])] = (uint16_t)(c[u] + 1u);
+                for (int u = 0; u < U; ++u) st.put(b[u], s[u] + x[u], c[u] + 1u);
             } else {
-                const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    accw[b[u] << 5] += xs[u];
-                    cntw[cidx(b[u])] = (uint16_t)(cntw[cidx(b[u])] + 1u);
+                for (int u = 0; u < U; ++u) {
+                    float s1;
+                    uint32_t c1;
+                    st.load(b[u], s1, c1);
+                    st.put(b[u], s1 + x[u], c1 + 1u);
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = nb[u];
-            x = nx;
+            for (int u = 0; u < U; ++u) {
+                b[u] = nb[u];
+                x[u] = nx[u];
+            }
             haz = nhaz;
+            T1 = T2;
         }
     }
-    for (int i = 4 * ng; i < nvalid; ++i) {
+    for (int i = U * ng; i < nvalid; ++i) {
         const uint32_t bb = phase_bin<POW2>(stl[i], sth[i], Fl, Fh, nbins, shift);
-        accw[bb << 5] += sx[i];
-        cntw[cidx(bb)] = (uint16_t)(cntw[cidx(bb)] + 1u);
+        float s1;
+        uint32_t c1;
+        st.load(bb, s1, c1);
+        st.put(bb, s1 + sx[i], c1 + 1u);
     }
+}
+
+// Fold nvalid samples (a segment starting on a 16-sample boundary of the tile) in groups
+// of 16. A group flagged regular by the prep pass, folded at a period for which 15
+// regular steps can never bring two samples into one bin (`safe`), needs no collision
+// check: its 16 bin reads are all issued before its 16 writes. Other groups, and the
+// tail, go through the checked path.
+template <bool POW2, class St>
+__device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
+                                             const uint32_t *__restrict__ sth,
+                                             const float *__restrict__ sx, unsigned long long fmask,
+                                             int nvalid, const St &st, uint32_t Fl, uint32_t Fh,
+                                             uint32_t nbins, int shift, bool safe)
+{
+    const int ng = nvalid >> 4;
+    if (!safe) fmask = 0ull;
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+        const int i = g << 4;
+        if ((fmask >> g) & 1ull) {
+            TileRegs<16> T;
+            load_tile_regs<16>(stl, sth, sx, i, T);
+            uint32_t b[16];
+            float x[16];
+            bins_from_regs<POW2, 16>(T, Fl, Fh, nbins, shift, b, x);
+            float sm[16];
+            uint32_t c[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) st.load(b[u], sm[u], c[u]);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) st.put(b[u], sm[u] + x[u], c[u] + 1u);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < 16; q += 4) {
+                TileRegs<4> T;
+                load_tile_regs<4>(stl, sth, sx, i + q, T);
+                uint32_t b[4];
+                float x[4];
+                bins_from_regs<POW2, 4>(T, Fl, Fh, nbins, shift, b, x);
+                if (!hazard_u<4>(b)) {
+                    float sm[4];
+                    uint32_t c[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) st.load(b[u], sm[u], c[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) st.put(b[u], sm[u] + x[u], c[u] + 1u);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float s1;
+                        uint32_t c1;
+                        st.load(b[u], s1, c1);
+                        st.put(b[u], s1 + x[u], c1 + 1u);
+                    }
+                }
+            }
+        }
+    }
+    if (nvalid & 15)
+        fold_tile<POW2, St, 4>(stl + 16 * ng, sth + 16 * ng, sx + 16 * ng, nvalid & 15, st, Fl, Fh,
+                               nbins, shift);
+}
+
+// True if, for this lane's frequency F, samples 1..15 regular steps apart (each step in
+// [d0, d0 + 2] tau units) are always at least one bin width apart in phase, so they can
+// never share a bin.
+__device__ __forceinline__ bool regular_steps_safe(unsigned long long F, long long d0, uint32_t nbins)
+{
+    if (d0 <= 0 || F == 0ull || F > 0xFFFFFFFFFFFFFFFFull / 32ull) return false;
+    for (int k = 1; k < 16; ++k) {
+        const unsigned long long ph = (unsigned long long)k * (unsigned long long)d0 * F;  // mod 2^64
+        const unsigned long long dist = ph < (0ull - ph) ? ph : (0ull - ph);  // circular distance
+        const unsigned long long jitter = (unsigned long long)(2 * k) * F;
+        if (dist <= jitter) return false;
+        if (__umul64hi(dist - jitter, (unsigned long long)nbins) == 0ull) return false;  // < 1 bin
+    }
+    return true;
 }
 
 // Fold this lane's chunk partials into the Kahan workspace (sum, compensation) and the
 // exact 32-bit counts. On the last chunk the finished sums (sum - compensation) go back
-// into accw and the counts into cntw, saturated at 65535 (the exact totals stay in the
-// workspace). Workspace reads are batched 16 bins at a time to overlap their latency.
-// Returns true if a count saturated.
-__device__ __forceinline__ void flush_one(float *accw, uint16_t *cntw, float2 *wsc, uint32_t *wcn,
-                                          int b, size_t idx, bool first, bool last, float2 sc,
-                                          uint32_t cc, bool &over)
+// into the store with the counts (16-bit stores saturate at 65535; the exact totals stay
+// in the workspace). Workspace reads are batched 16 bins at a time to overlap their
+// latency. Returns true if a count saturated.
+template <class St>
+__device__ __forceinline__ void flush_one(const St &st, float2 *wsc, uint32_t *wcn, int b, size_t idx,
+                                          bool first, bool last, float2 sc, uint32_t cc, bool &over)
 {
-    const float p = accw[b << 5];
-    const uint32_t c = cntw[cidx(b)];
+    float p;
+    uint32_t c;
+    st.load((uint32_t)b, p, c);
     if (first) {
         sc = make_float2(p, 0.f);
         cc = c;
@@ -293,20 +508,23 @@ __device__ __forceinline__ void flush_one(float *accw, uint16_t *cntw, float2 *w
         sc.x = t;
     }
     if (last) {
-        accw[b << 5] = sc.x - sc.y;
-        cntw[cidx(b)] = (uint16_t)min(cc, 65535u);
-        over |= cc > 65535u;
-        if (!first) wcn[idx] = cc;
+        if (St::kSaturates) {
+            st.put((uint32_t)b, sc.x - sc.y, min(cc, 65535u));
+            over |= cc > 65535u;
+            if (!first) wcn[idx] = cc;
+        } else {
+            st.put((uint32_t)b, sc.x - sc.y, cc);
+        }
     } else {
         wsc[idx] = sc;
         wcn[idx] = cc;
-        accw[b << 5] = 0.f;
-        cntw[cidx(b)] = 0;
+        st.put((uint32_t)b, 0.f, 0u);
     }
 }
 
-__device__ __forceinline__ bool flush_chunk(float *accw, uint16_t *cntw, float2 *wsc, uint32_t *wcn,
-                                            int nbins, int ppc, bool first, bool last)
+template <class St>
+__device__ __forceinline__ bool flush_chunk(const St &st, float2 *wsc, uint32_t *wcn, int nbins, int ppc,
+                                            bool first, bool last)
 {
     bool over = false;
     int b0 = 0;
@@ -324,7 +542,7 @@ __device__ __forceinline__ bool flush_chunk(float *accw, uint16_t *cntw, float2 
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-            flush_one(accw, cntw, wsc, wcn, b0 + u, (size_t)(b0 + u) * ppc, first, last, sc[u], cc[u], over);
+            flush_one(st, wsc, wcn, b0 + u, (size_t)(b0 + u) * ppc, first, last, sc[u], cc[u], over);
     }
     for (; b0 < nbins; ++b0) {
         const size_t idx = (size_t)b0 * ppc;
@@ -334,22 +552,22 @@ __device__ __forceinline__ bool flush_chunk(float *accw, uint16_t *cntw, float2 
             sc = wsc[idx];
             cc = wcn[idx];
         }
-        flush_one(accw, cntw, wsc, wcn, b0, idx, first, last, sc, cc, over);
+        flush_one(st, wsc, wcn, b0, idx, first, last, sc, cc, over);
     }
     return over;
 }
 
-// Bins of one profile as seen by one lane: the fold's lane-private layout.
+// Bins of one profile as seen by one lane: the fold's lane-private store.
+template <class St>
 struct LaneBins {
-    const float *S;        // accw
-    const uint16_t *C;     // cntw
-    const uint32_t *Cbig;  // exact counts (workspace) when a count saturated
+    St st;
+    const uint32_t *Cbig;  // exact counts (workspace) when a 16-bit count saturated
     size_t cbs;
     bool big;
-    __device__ __forceinline__ float s(int b) const { return S[b << 5]; }
+    __device__ __forceinline__ float s(int b) const { return st.sum((uint32_t)b); }
     __device__ __forceinline__ float c(int b) const
     {
-        return big ? (float)Cbig[(size_t)b * cbs] : (float)C[cidx((uint32_t)b)];
+        return big ? (float)Cbig[(size_t)b * cbs] : (float)st.count((uint32_t)b);
     }
 };
 
@@ -492,8 +710,8 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-template <int MODE, bool POW2>
-__global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldParams p)
+template <int MODE, bool POW2, int LAYOUT, int MAXW>
+__global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort;
@@ -506,11 +724,19 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
     uint32_t *tl_buf = reinterpret_cast<uint32_t *>(smem + 128);
     uint32_t *th_buf = tl_buf + 2 * kTile;
     float *x_buf = reinterpret_cast<float *>(th_buf + 2 * kTile);
-    float *acc = x_buf + 2 * kTile;
-    const int nb2 = (nbins + 1) & ~1;
-    uint16_t *cnt = reinterpret_cast<uint16_t *>(acc + (size_t)p.warps * nbins * 32);
-    float *accw = acc + (size_t)warp * nbins * 32 + lane;
-    uint16_t *cntw = cnt + (size_t)warp * nb2 * 32 + 2 * lane;
+    uint8_t *f_buf = reinterpret_cast<uint8_t *>(x_buf + 2 * kTile);  // [2][kTile / 16]
+    using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64, StorePaired16>::type;
+    St st;
+    if constexpr (LAYOUT == kLayoutPacked64) {
+        uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (kTile / 16));
+        st.v = v + (size_t)warp * nbins * 32 + lane;
+    } else {
+        float *acc = reinterpret_cast<float *>(f_buf + 2 * (kTile / 16));
+        const int nb2 = (nbins + 1) & ~1;
+        uint16_t *cnt = reinterpret_cast<uint16_t *>(acc + (size_t)p.warps * nbins * 32);
+        st.acc = acc + (size_t)warp * nbins * 32 + lane;
+        st.cnt = cnt + (size_t)warp * nb2 * 32 + 2 * lane;
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -546,6 +772,7 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
         const bool kvalid = k < ge;
 
         uint32_t Fl = 0u, Fh = 0u;
+        bool safe = false;
         if (kvalid) {
             const double P = p.periods[k];
             const double q = kTwo40 / P;
@@ -553,23 +780,23 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
                 const unsigned long long F = (unsigned long long)__double2ll_rn(q);
                 Fl = (uint32_t)F;
                 Fh = (uint32_t)(F >> 32);
+                safe = regular_steps_safe(F, p.stats[s].dtau0, (uint32_t)nbins);
             } else {
                 report_error(p.status, kErrRange);
             }
         }
-        for (int b = 0; b < nbins; ++b) {
-            accw[b << 5] = 0.f;
-            cntw[cidx(b)] = 0;
-        }
+        for (int b = 0; b < nbins; ++b) st.put((uint32_t)b, 0.f, 0u);
         const int ntiles = (int)((nsamp + kTile - 1) / kTile);
         auto issue = [&](int t, int buf) {
             const int64_t i0 = (int64_t)t * kTile;
             const int nv = (int)min((int64_t)kTile, nsamp - i0);
             const uint32_t bytes = (uint32_t)(((nv + 3) & ~3) * 4);
-            mbar_arrive_expect_tx(&bars[buf], 3u * bytes);
+            const uint32_t fbytes = (uint32_t)((((nv + 15) >> 4) + 15) & ~15);
+            mbar_arrive_expect_tx(&bars[buf], 3u * bytes + fbytes);
             bulk_g2s(tl_buf + buf * kTile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(th_buf + buf * kTile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(x_buf + buf * kTile, p.smp.x + sbase + i0, bytes, &bars[buf]);
+            bulk_g2s(f_buf + buf * (kTile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
         __syncthreads();  // previous task's readers are done with both buffers
         if (threadIdx.x == 0) {
@@ -591,17 +818,33 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
                 const uint32_t *stl = tl_buf + buf * kTile;
                 const uint32_t *sth = th_buf + buf * kTile;
                 const float *sx = x_buf + buf * kTile;
+                // the tile's 64 regular-group flag bytes, packed into a register bit mask
+                unsigned long long fmask = 0ull;
+                {
+                    const uint4 *fw = reinterpret_cast<const uint4 *>(f_buf + buf * (kTile / 16));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 w = fw[q];
+                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            // bytes (0 or 1) j = 0..3 of a word -> bits j of a nibble
+                            const unsigned long long nib = ((ww[r] * 0x01020408u) >> 24) & 0xFu;
+                            fmask |= nib << (16 * q + 4 * r);
+                        }
+                    }
+                }
                 int i = 0;
                 while (i < nv) {
                     // segments end at chunk boundaries (multiples of 4 samples) or the tile end
                     const int seg = min(nv - i, chunk_left);
-                    fold_tile<POW2>(stl + i, sth + i, sx + i, seg, accw, cntw, Fl, Fh, (uint32_t)nbins,
-                                    p.shift);
+                    fold_segment<POW2, St>(stl + i, sth + i, sx + i, fmask >> (i >> 4), seg, st, Fl, Fh,
+                                           (uint32_t)nbins, p.shift, safe);
                     i += seg;
                     chunk_left -= seg;
                     const bool last = (t == ntiles - 1) && (i == nv);
                     if (chunk_left == 0 || last) {
-                        over = flush_chunk(accw, cntw, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
+                        over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
                         first_flush = false;
                         chunk_left = p.chunk;
                     }
@@ -617,8 +860,8 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
             if (kvalid) {
                 const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
                 for (int b = 0; b < nbins; ++b) {
-                    const uint32_t c = over ? wcn_cta[(size_t)b * ppc] : (uint32_t)cntw[cidx(b)];
-                    const float S = accw[b << 5];
+                    const uint32_t c = over ? wcn_cta[(size_t)b * ppc] : st.count((uint32_t)b);
+                    const float S = st.sum((uint32_t)b);
                     const float mean = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
                     if (p.folded) p.folded[(size_t)k * nbins + b] = mean;
                     if (p.counts) p.counts[(size_t)k * nbins + b] = (int32_t)c;
@@ -631,7 +874,7 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
                 float sig = p.sigma_user;
                 if (!(sig > 0.f)) sig = p.stats[s].sigma;
                 if (!(sig > 0.f)) sig = 1.f;
-                const LaneBins B{accw, cntw, wcn_cta, (size_t)ppc, over};
+                const LaneBins<St> B{st, wcn_cta, (size_t)ppc, over};
                 box_search(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
                 p.score[k] = sc;
                 if (p.best_s) p.best_s[k] = bs;
@@ -646,47 +889,72 @@ __global__ void __launch_bounds__(kMaxFoldWarps * 32, 1) fold_kernel(const FoldP
     }
 }
 
-template <int MODE, bool POW2>
+template <int MODE, bool POW2, int LAYOUT, int MAXW>
 static cudaError_t set_smem_attr()
 {
-    return cudaFuncSetAttribute(fold_kernel<MODE, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(kSmemLimit - 1024));
+    return cudaFuncSetAttribute(fold_kernel<MODE, POW2, LAYOUT, MAXW>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemLimit - 1024));
+}
+
+template <int MODE, bool POW2>
+static cudaError_t set_smem_attr_all()
+{
+    cudaError_t e = set_smem_attr<MODE, POW2, kLayoutPaired16, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPaired16, kMaxFoldWarps>();
+    if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPacked64, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPacked64, kMaxFoldWarps>();
+    return e;
 }
 
 int fold_register_kernels()
 {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = set_smem_attr<kModeFold, true>();
-    if (e == cudaSuccess) e = set_smem_attr<kModeFold, false>();
-    if (e == cudaSuccess) e = set_smem_attr<kModeBox, true>();
-    if (e == cudaSuccess) e = set_smem_attr<kModeBox, false>();
+    cudaError_t e = set_smem_attr_all<kModeFold, true>();
+    if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, false>();
+    if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, true>();
+    if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, false>();
     return (int)e;
 }
 
-size_t fold_smem_bytes(int nbins, int warps)
+size_t fold_smem_bytes(int nbins, int warps, int layout)
 {
     const size_t nb2 = (size_t)((nbins + 1) & ~1);
-    return 128 + (size_t)2 * kTile * 12 + (size_t)warps * 32 * (nbins * 4 + nb2 * 2);
+    const size_t per_warp = layout == kLayoutPacked64 ? (size_t)32 * nbins * 8
+                                                      : (size_t)32 * (nbins * 4 + nb2 * 2);
+    return 128 + (size_t)2 * kTile * 12 + 2 * (kTile / 16) + (size_t)warps * per_warp;
 }
 
-int fold_max_warps(int nbins)
+int fold_max_warps(int nbins, int layout)
 {
     int w = kMaxFoldWarps;
-    while (w > 1 && fold_smem_bytes(nbins, w) > kSmemLimit - 1024) --w;
-    return fold_smem_bytes(nbins, w) <= kSmemLimit - 1024 ? w : 0;
+    while (w > 1 && fold_smem_bytes(nbins, w, layout) > kSmemLimit - 1024) --w;
+    return fold_smem_bytes(nbins, w, layout) <= kSmemLimit - 1024 ? w : 0;
+}
+
+// Blocks of up to 4 warps use the instantiation with a 255-register budget (the 16-sample
+// groups keep many values live); wider blocks the one capped at 128 registers.
+template <int MODE, bool POW2>
+static void launch_variant(const FoldParams &p, int grid, int threads, size_t smem, cudaStream_t st)
+{
+    if (p.layout == kLayoutPacked64) {
+        if (p.warps <= 4) fold_kernel<MODE, POW2, kLayoutPacked64, 4><<<grid, threads, smem, st>>>(p);
+        else fold_kernel<MODE, POW2, kLayoutPacked64, kMaxFoldWarps><<<grid, threads, smem, st>>>(p);
+    } else {
+        if (p.warps <= 4) fold_kernel<MODE, POW2, kLayoutPaired16, 4><<<grid, threads, smem, st>>>(p);
+        else fold_kernel<MODE, POW2, kLayoutPaired16, kMaxFoldWarps><<<grid, threads, smem, st>>>(p);
+    }
 }
 
 cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st)
 {
-    const size_t smem = fold_smem_bytes(p.nbins, p.warps);
+    const size_t smem = fold_smem_bytes(p.nbins, p.warps, p.layout);
     const int threads = 32 * p.warps;
     const bool pow2 = p.shift >= 0;
     if (mode == kModeFold) {
-        if (pow2) fold_kernel<kModeFold, true><<<grid, threads, smem, st>>>(p);
-        else fold_kernel<kModeFold, false><<<grid, threads, smem, st>>>(p);
+        if (pow2) launch_variant<kModeFold, true>(p, grid, threads, smem, st);
+        else launch_variant<kModeFold, false>(p, grid, threads, smem, st);
     } else if (mode == kModeBox) {
-        if (pow2) fold_kernel<kModeBox, true><<<grid, threads, smem, st>>>(p);
-        else fold_kernel<kModeBox, false><<<grid, threads, smem, st>>>(p);
+        if (pow2) launch_variant<kModeBox, true>(p, grid, threads, smem, st);
+        else launch_variant<kModeBox, false>(p, grid, threads, smem, st);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -26,6 +26,7 @@ struct StarStats {
     float f_lo;     // f_ref - f_hi rounded to FP32
     float sigma;    // population std of the flux (FP64 reduction, rounded)
     int32_t n;      // samples of the star
+    long long dtau0;  // smallest positive step between consecutive quantised times (0: none)
 };
 
 // Samples of all stars, quantised, at 16-byte aligned per-star offsets.
@@ -33,9 +34,13 @@ struct SampleScratch {
     uint32_t *tau_lo;   // low 32 bits of tau
     int32_t *tau_hi;    // high 32 bits of tau
     float *x;           // flux - f_ref (FP32)
+    uint8_t *flags;     // one byte per 16 samples: regular-cadence group (see prep)
 };
 
 enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeCnnPrep = 2 };
+
+// Shared-memory layout of the lane-private bins (see fold.cu).
+enum FoldLayout : int { kLayoutPaired16 = 1, kLayoutPacked64 = 2 };
 
 struct FoldParams {
     SampleScratch smp;
@@ -51,7 +56,8 @@ struct FoldParams {
     int nbins;
     int shift;                 // 32 - log2(nbins) if nbins is a power of two, else -1
     int warps;                 // warps per block; periods per block = 32 * warps
-    int chunk;                 // samples per shared-memory chunk: multiple of 4, <= 65532
+    int chunk;                 // samples per shared-memory chunk: multiple of 16, <= 65520
+    int layout;                // FoldLayout
     float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
     // kModeFold outputs ([global period][nbins])
@@ -69,8 +75,8 @@ struct FoldParams {
     uint32_t *status;
 };
 
-size_t fold_smem_bytes(int nbins, int warps);
-int fold_max_warps(int nbins);
+size_t fold_smem_bytes(int nbins, int warps, int layout);
+int fold_max_warps(int nbins, int layout);
 int fold_register_kernels();
 
 cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
@@ -86,7 +92,7 @@ cudaError_t launch_argmax_finalize(const unsigned long long *key, int nstars, in
 
 inline int64_t scratch_elems(int64_t total_samples, int nstars)
 {
-    return 4 * ((total_samples + 3) / 4 + nstars) + 4 * kTile;
+    return 256 * ((total_samples + 255) / 256 + nstars) + 4 * kTile;
 }
 
 }  // namespace gpfc

@@ -282,3 +282,28 @@ def test_argument_errors_are_synchronous(ctx):
     with pytest.raises(g.GpfcError) as ei:
         g.gpfc_fold(ctx, times, flux, per, 2048, 0.0)
     assert ei.value.code == -6
+
+
+@pytest.mark.parametrize("layout,chunk", [(1, 1000), (2, 1000), (1, 0), (2, 0)])
+def test_fold_and_search_every_kernel_variant(ctx, layout, chunk):
+    import paper_2312_02063_gb300 as g
+    rng = np.random.default_rng(layout * 10 + chunk)
+    n = 9001
+    times = np.sort(rng.uniform(0.0, 300.0, n))
+    times[100:107] = times[100]  # repeated timestamps: hazards inside a group
+    flux = (1.0 + rng.normal(0, 2e-4, n)).astype(np.float32)
+    periods = np.concatenate([rng.uniform(0.2, 1.0, 70), [1e6, 0.25]])
+    try:
+        for nbins in (256, 100):
+            for warps in (1, ctx.fold_max_warps(nbins, layout)):
+                ctx.set_fold_config(warps=warps, layout=layout, chunk=chunk)
+                fo, co = gpu_fold(ctx, times, flux, periods, nbins, 0.0)
+                mean_o, cnt_o, sum_o = oracle.fold(times, flux, periods, nbins, 0.0)
+                check_fold(fo, co, mean_o, cnt_o)
+                score, _, _ = g.gpfc_search(ctx, _dev(ctx, times), _dev(ctx, flux), _dev(ctx, periods), nbins,
+                                            0.0, g.SCORER_BOX, 1, 20, 2e-4)
+                ctx.sync()
+                sc_o, _, _ = oracle.box_snr(sum_o, cnt_o, 1, 20, 2e-4)
+                check_box(score.cpu().numpy(), sc_o)
+    finally:
+        ctx.reset_fold_config()
