@@ -140,6 +140,33 @@ int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts,
                    int64_t n_periods, int32_t nbins, const gpfc_box_params *params,
                    float *score, int32_t *best_s, int32_t *best_w);
 
+/* ------------------------------------------------------------------ CNN scorer
+ * Score of each folded profile by a 1-D CNN (Sec. 2.5; the noise normalisation of
+ * Sec. 2.1 first scales each profile to unit standard deviation while keeping its mean):
+ *   conv(1->16,k5) ReLU maxpool2, conv(16->32,k5) ReLU maxpool2, conv(32->64,k5) ReLU
+ *   maxpool2, flatten (channel-major, 2048), fc(2048->256) ReLU, fc(256->1), sigmoid.
+ * Convolutions are circular with padding 2. Normalisation over the non-empty bins:
+ * m = their mean, s = their population std, x_b = m + (v_b - m) / s, empty bins -> m,
+ * s = 0 -> every x_b = m. Computation: BF16 inputs, weights and activations, FP32
+ * accumulation on the tensor cores.
+ * Parameters are FP32 device tensors in PyTorch layout: conv1_w [16][1][5],
+ * conv2_w [32][16][5], conv3_w [64][32][5], fc1_w [256][2048], fc2_w [1][256] and their
+ * biases; they are rounded to BF16 on every call. */
+typedef struct {
+    const float *conv1_w, *conv1_b, *conv2_w, *conv2_b, *conv3_w, *conv3_b;
+    const float *fc1_w, *fc1_b, *fc2_w, *fc2_b;
+} gpfc_cnn_weights;
+
+/* folded [n_periods][256] float32 means; counts [n_periods][256] int32 or NULL (then a
+ * NaN mean marks an empty bin); nbins must be 256 (else GPFC_ENOTSUP);
+ * score [n_periods] float32 in (0, 1). */
+int gpfc_score_cnn(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
+                   int32_t nbins, const gpfc_cnn_weights *weights, float *score);
+
+/* As gpfc_score_cnn, writing the pre-sigmoid logits z (score = 1 / (1 + exp(-z))). */
+int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
+                    int32_t nbins, const gpfc_cnn_weights *weights, float *logit);
+
 /* ------------------------------------------------------------------ best period
  * argmax over score[n_periods] (NaN never wins; ties go to the smaller index), Sec. 2.1:
  * the trial period with the strongest score. best_index [1] int64 (-1 if every score is

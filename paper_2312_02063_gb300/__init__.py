@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
-    "gpfc_fold", "gpfc_score_box", "gpfc_best_period", "gpfc_search",
+    "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -42,6 +42,18 @@ class FoldConfig(ctypes.Structure):
 
 LAYOUT_PAIRED16 = 1
 LAYOUT_PACKED64 = 2
+
+
+class CnnWeights(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("conv1_w", "conv1_b", "conv2_w", "conv2_b", "conv3_w",
+                                               "conv3_b", "fc1_w", "fc1_b", "fc2_w", "fc2_b")]
+
+
+CNN_PARAM_NAMES = ["conv1.w", "conv1.b", "conv2.w", "conv2.b", "conv3.w", "conv3.b",
+                   "fc1.w", "fc1.b", "fc2.w", "fc2.b"]
+CNN_PARAM_SHAPES = {"conv1.w": (16, 1, 5), "conv1.b": (16,), "conv2.w": (32, 16, 5), "conv2.b": (32,),
+                    "conv3.w": (64, 32, 5), "conv3.b": (64,), "fc1.w": (256, 2048), "fc1.b": (256,),
+                    "fc2.w": (1, 256), "fc2.b": (1,)}
 
 
 class BoxParams(ctypes.Structure):
@@ -88,6 +100,8 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_score_box.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.POINTER(BoxParams), _vp, _vp, _vp]
         L.gpfc_best_period.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.gpfc_score_cnn.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights), _vp]
+        L.gpfc_cnn_logits.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights), _vp]
         L.gpfc_search.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]
         _lib = L
@@ -218,6 +232,45 @@ def gpfc_score_box(ctx: Context, folded, counts, w_min: int, w_max: int, sigma: 
     ctx._check(ctx.lib.gpfc_score_box(ctx.handle, _ptr(folded), _ptr(counts), npd, int(nbins),
                                       ctypes.byref(bp), _ptr(score), _ptr(best_s), _ptr(best_w)))
     return score, best_s, best_w
+
+
+def _cnn_weights(ctx, weights):
+    ptrs = []
+    for n in CNN_PARAM_NAMES:
+        t = weights[n]
+        _need(t, torch.float32, ctx.device, n, int(torch.Size(CNN_PARAM_SHAPES[n]).numel()))
+        ptrs.append(ctypes.c_void_p(t.data_ptr()))
+    return CnnWeights(*ptrs)
+
+
+def gpfc_score_cnn(ctx: Context, folded, weights, counts=None, score=None):
+    """CNN score of each 256-bin profile. weights: dict name -> FP32 CUDA tensor (PyTorch layout)."""
+    dev = ctx.device
+    _need(folded, torch.float32, dev, "folded")
+    npd = folded.shape[0]
+    if counts is not None:
+        _need(counts, torch.int32, dev, "counts", folded.numel())
+    if score is None:
+        score = torch.empty(npd, dtype=torch.float32, device=dev)
+    w = _cnn_weights(ctx, weights)
+    ctx._check(ctx.lib.gpfc_score_cnn(ctx.handle, _ptr(folded), _ptr(counts), npd, int(folded.shape[1]),
+                                      ctypes.byref(w), _ptr(score)))
+    return score
+
+
+def gpfc_cnn_logits(ctx: Context, folded, weights, counts=None, logit=None):
+    """Pre-sigmoid CNN outputs of each 256-bin profile."""
+    dev = ctx.device
+    _need(folded, torch.float32, dev, "folded")
+    npd = folded.shape[0]
+    if counts is not None:
+        _need(counts, torch.int32, dev, "counts", folded.numel())
+    if logit is None:
+        logit = torch.empty(npd, dtype=torch.float32, device=dev)
+    w = _cnn_weights(ctx, weights)
+    ctx._check(ctx.lib.gpfc_cnn_logits(ctx.handle, _ptr(folded), _ptr(counts), npd, int(folded.shape[1]),
+                                       ctypes.byref(w), _ptr(logit)))
+    return logit
 
 
 def gpfc_best_period(ctx: Context, score, best_index=None, best_score=None):

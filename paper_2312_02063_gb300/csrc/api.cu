@@ -11,6 +11,7 @@
 #include <new>
 
 #include "gpfc.h"
+#include "gpfc_cnn.h"
 #include "gpfc_kernels.h"
 
 using namespace gpfc;
@@ -31,6 +32,9 @@ struct gpfc_ctx {
 };
 
 namespace {
+
+// Profiles scored per CNN launch pair: their fc1 operand tiles (64 MB) stay in L2.
+constexpr int64_t kCnnChunk = 16384;
 
 // Message of the last failure that had no context to hold it (gpfc_create).
 thread_local char g_create_error[512] = {0};
@@ -396,6 +400,73 @@ int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts, in
     if (e != cudaSuccess) return cuda_err(ctx, e, "box kernel");
     timer.stop();
     return GPFC_OK;
+}
+
+static int cnn_forward(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
+                       int32_t nbins, const gpfc_cnn_weights *wt, float *score, float *logit)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!folded || (!score && !logit) || !wt) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (nbins != 256) return set_err(ctx, GPFC_ENOTSUP, "the CNN scorer takes 256-bin profiles, got %d", nbins);
+    if (n_periods < 1 || n_periods > (int64_t)INT32_MAX) return set_err(ctx, GPFC_EINVAL, "bad n_periods");
+    const float *ptrs[10] = {wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                             wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+    for (const float *q : ptrs)
+        if (!q) return set_err(ctx, GPFC_EINVAL, "NULL CNN parameter");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    const int64_t chunk = std::min<int64_t>(n_periods, kCnnChunk);
+    Carver c(nullptr);
+    c.take<uint8_t>(cnn_dev_bytes());
+    c.take<uint8_t>((size_t)((chunk + 127) / 128) * 32 * 128 * 64 * 2);
+    rc = ensure_ws(ctx, c.off + 256);
+    if (rc) return rc;
+    Carver c2(ctx->ws);
+    const CnnDev dev = cnn_dev_carve(c2.take<uint8_t>(cnn_dev_bytes()));
+    uint8_t *h3t = c2.take<uint8_t>((size_t)((chunk + 127) / 128) * 32 * 128 * 64 * 2);
+    const CnnSrc src{wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                     wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+    cudaError_t e = launch_cnn_prep(src, dev, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "CNN weight preparation");
+    KernelTimer timer(ctx);
+    for (int64_t k0 = 0; k0 < n_periods; k0 += chunk) {
+        const int64_t nk = std::min<int64_t>(chunk, n_periods - k0);
+        CnnConvParams cp{};
+        cp.folded = folded;
+        cp.counts = counts;
+        cp.k_begin = k0;
+        cp.np = nk;
+        cp.w = dev;
+        cp.h3t = h3t;
+        cp.status = ctx->status_dev;
+        e = launch_cnn_conv(cp, ctx->num_sms, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "CNN conv kernel");
+        CnnFcParams fp{};
+        fp.h3t = h3t;
+        fp.k_begin = k0;
+        fp.np = nk;
+        fp.w = dev;
+        fp.score = score;
+        fp.logit = logit;
+        fp.status = ctx->status_dev;
+        e = launch_cnn_fc(fp, ctx->num_sms, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "CNN fc kernel");
+    }
+    timer.stop();
+    return GPFC_OK;
+}
+
+int gpfc_score_cnn(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
+                   int32_t nbins, const gpfc_cnn_weights *wt, float *score)
+{
+    return cnn_forward(ctx, folded, counts, n_periods, nbins, wt, score, nullptr);
+}
+
+int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
+                    int32_t nbins, const gpfc_cnn_weights *wt, float *logit)
+{
+    return cnn_forward(ctx, folded, counts, n_periods, nbins, wt, nullptr, logit);
 }
 
 int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods, int64_t *best_index,

@@ -1,0 +1,74 @@
+// gpfc_cnn.h -- launch parameters of the CNN scorer kernels (cnn.cu, cnn_train.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gpfc_kernels.h"
+
+namespace gpfc {
+
+// FP32 parameters in PyTorch layout (device pointers):
+// w1 [16][1][5], w2 [32][16][5], w3 [64][32][5], wf1 [256][2048], wf2 [1][256], biases.
+struct CnnSrc {
+    const float *w1, *b1, *w2, *b2, *w3, *b3, *wf1, *bf1, *wf2, *bf2;
+};
+
+// Device copies in the layouts the kernels read (weights rounded to BF16).
+struct CnnDev {
+    float *w1, *b1, *b2, *b3, *bf1, *wf2, *bf2;
+    uint8_t *B2;   // conv2 weights, tensor-core operand layout (32 x 80 BF16)
+    uint8_t *B3;   // conv3 weights (64 x 160 BF16)
+    uint8_t *W1t;  // fc1 weights, 32 K chunks of 256 x 64 BF16
+};
+
+struct CnnDevLayout {
+    static constexpr size_t w1 = 0;
+    static constexpr size_t b1 = 512;
+    static constexpr size_t b2 = 1024;
+    static constexpr size_t b3 = 1536;
+    static constexpr size_t bf1 = 2048;
+    static constexpr size_t wf2 = 3072;
+    static constexpr size_t bf2 = 4096;
+    static constexpr size_t B2 = 8192;
+    static constexpr size_t B3 = B2 + 32 * 80 * 2;
+    static constexpr size_t W1t = 65536;
+    static constexpr size_t total() { return W1t + (size_t)256 * 2048 * 2; }
+};
+
+struct CnnConvParams {
+    const float *folded;     // [*][256] means (global profile index)
+    const int32_t *counts;   // [*][256] or NULL (then NaN marks an empty bin)
+    int64_t k_begin;         // first profile of this launch
+    int64_t np;              // profiles in this launch
+    CnnDev w;
+    uint8_t *h3t;            // [ceil(np/128)][32][128 x 64 BF16 tile] (local profile index)
+    // activations kept for the backward pass (NULL at inference), local profile index
+    float *xsave;            // [np][256] normalised input (BF16 values)
+    uint16_t *h1save;        // [np][16][128] BF16
+    uint16_t *a2save;        // [np][32][128] BF16 conv2 pre-activation
+    uint16_t *h2save;        // [np][32][64] BF16
+    uint16_t *a3save;        // [np][64][64] BF16 conv3 pre-activation
+    uint32_t *status;
+};
+
+struct CnnFcParams {
+    const uint8_t *h3t;
+    int64_t k_begin;
+    int64_t np;
+    CnnDev w;
+    float *score;            // [global] sigmoid(logit), or NULL
+    float *logit;            // [global] or NULL
+    float *z1save;           // [np][256] fc1 pre-activation (NULL at inference)
+    uint32_t *status;
+};
+
+size_t cnn_dev_bytes();
+CnnDev cnn_dev_carve(void *base);
+cudaError_t cnn_register_kernels();
+cudaError_t launch_cnn_prep(const CnnSrc &src, const CnnDev &dst, cudaStream_t st);
+cudaError_t launch_cnn_conv(const CnnConvParams &p, int num_sms, cudaStream_t st);
+cudaError_t launch_cnn_fc(const CnnFcParams &p, int num_sms, cudaStream_t st);
+
+}  // namespace gpfc

@@ -1,0 +1,81 @@
+"""GPU parity of the CNN scorer (tcgen05 forward) against the FP64 oracle.
+
+Tolerance: scores within 2e-2 absolute and >= 99.9% agreement of the above/below 0.5
+decisions; the logits are also checked against a BF16-scale bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lcsynth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SCORE_ATOL = 2e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2312_02063_gb300 as g
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+def dev_weights(ctx, w):
+    return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(ctx.device) for k, v in w.items()}
+
+
+def scaled_weights(seed, fc2_scale):
+    w = lcsynth.cnn_init(seed, bias_scale=0.05)
+    w["fc2.w"] = lcsynth.round_to_bf16(w["fc2.w"] * fc2_scale)
+    return w
+
+
+def run(ctx, prof, w, counts=None):
+    import paper_2312_02063_gb300 as g
+    f = torch.from_numpy(prof).to(ctx.device)
+    c = None if counts is None else torch.from_numpy(counts).to(ctx.device)
+    wd = dev_weights(ctx, w)
+    z = g.gpfc_cnn_logits(ctx, f, wd, c)
+    s = g.gpfc_score_cnn(ctx, f, wd, c)
+    ctx.sync()
+    return z.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,seed,scale", [(4096, 1, 0.25), (1001, 2, 1.0), (3, 3, 0.25), (1, 4, 0.25)])
+def test_cnn_scores_match_oracle(ctx, n, seed, scale):
+    prof, _ = lcsynth.profiles_mixed(n, seed=seed)
+    w = scaled_weights(seed, scale)
+    z, s = run(ctx, prof, w)
+    zo, so = oracle.cnn_score(w, prof)
+    assert np.max(np.abs(s - so)) <= SCORE_ATOL, np.max(np.abs(s - so))
+    agree = np.mean((s > 0.5) == (so > 0.5))
+    assert agree >= 0.999 or n < 1000 and np.all(np.abs(so[(s > 0.5) != (so > 0.5)] - 0.5) < SCORE_ATOL)
+    np.testing.assert_allclose(1 / (1 + np.exp(-z)), s, atol=1e-6)
+    assert np.max(np.abs(z - zo)) <= 0.05 * (1 + np.max(np.abs(zo)))
+
+
+def test_cnn_empty_bins_by_counts_and_nan(ctx):
+    prof, _ = lcsynth.profiles_mixed(300, seed=9)
+    rng = np.random.default_rng(9)
+    counts = rng.integers(0, 5, prof.shape).astype(np.int32)
+    w = scaled_weights(9, 0.25)
+    _, s = run(ctx, prof, w, counts)
+    _, so = oracle.cnn_score(w, prof, counts)
+    assert np.max(np.abs(s - so)) <= SCORE_ATOL
+    pn = np.where(counts > 0, prof, np.nan).astype(np.float32)
+    _, s2 = run(ctx, pn, w)
+    assert np.max(np.abs(s2 - so)) <= SCORE_ATOL
+
+
+def test_cnn_degenerate_profiles(ctx):
+    w = scaled_weights(11, 0.25)
+    prof = np.ones((4, 256), np.float32)
+    prof[1] = np.nan            # every bin empty: input 0
+    prof[2, ::2] = np.nan       # constant over the non-empty bins: input m
+    prof[3] = 0.9993
+    _, s = run(ctx, prof, w)
+    _, so = oracle.cnn_score(w, prof)
+    assert np.max(np.abs(s - so)) <= SCORE_ATOL
