@@ -174,6 +174,27 @@ int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, i
 int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods,
                      int64_t *best_index, float *best_score);
 
+/* Allocation-free best period. The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate memory at the point of the call (a region where
+ * cudaMalloc is not allowed, a pre-planned memory budget, a hot loop kept off the
+ * allocator). They cannot call gpfc_create either, since it allocates, so this call
+ * takes a cudaStream_t (NULL = legacy default stream) instead of a context and runs on
+ * the current CUDA device. It computes what gpfc_best_period computes, with its only
+ * scratch, one 8-byte argmax key, in a static device array that every GPU using the
+ * library holds until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  - score [n_periods] float32, best_index [1] int64, best_score [1] float32: device
+ *    pointers; either output may be NULL, not both.
+ *  - n_periods must be 1..2^31-1 (the key stores a 32-bit index); else GPFC_EINVAL.
+ *  - The first call on a device looks up the scratch address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - All calls share the one key: calls that overlap on the GPU (different streams, or
+ *    different host threads without ordering) race and may return each other's result.
+ *    The key is cleared at the start of every call.
+ * Returns GPFC_OK, GPFC_EINVAL or GPFC_ECUDA (enqueue failure). */
+int gpfc_best_period_noalloc(const float *score, int64_t n_periods, int64_t *best_index,
+                             float *best_score, void *stream);
+
 /* ------------------------------------------------------------------ search
  * Fold + score in one pass (Fig. 1): the profiles stay on chip and are not written.
  * scorer GPFC_SCORER_BOX takes a gpfc_box_params* in scorer_params.

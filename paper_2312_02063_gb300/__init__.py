@@ -20,6 +20,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
+    "gpfc_best_period_noalloc",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -100,6 +101,7 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_score_box.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.POINTER(BoxParams), _vp, _vp, _vp]
         L.gpfc_best_period.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.gpfc_best_period_noalloc.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
         L.gpfc_score_cnn.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights), _vp]
         L.gpfc_cnn_logits.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights), _vp]
         L.gpfc_search.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
@@ -283,6 +285,26 @@ def gpfc_best_period(ctx: Context, score, best_index=None, best_score=None):
         best_score = torch.empty(1, dtype=torch.float32, device=dev)
     ctx._check(ctx.lib.gpfc_best_period(ctx.handle, _ptr(score), score.numel(), _ptr(best_index),
                                         _ptr(best_score)))
+    return best_index, best_score
+
+
+def gpfc_best_period_noalloc(score, best_index, best_score, stream=None):
+    """Allocation-free argmax of score (see include/gpfc.h). No context: runs on the current
+    device and the given torch stream (default: torch's current stream). The outputs must be
+    preallocated device tensors (int64 [1], float32 [1]); this call allocates nothing."""
+    lib = load_library()
+    if not (isinstance(score, torch.Tensor) and score.is_cuda and score.dtype == torch.float32
+            and score.is_contiguous()):
+        raise TypeError("score must be a contiguous float32 CUDA tensor")
+    dev = score.device
+    _need(best_index, torch.int64, dev, "best_index", 1)
+    _need(best_score, torch.float32, dev, "best_score", 1)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = lib.gpfc_best_period_noalloc(_ptr(score), score.numel(), _ptr(best_index), _ptr(best_score),
+                                          _vp(s.cuda_stream))
+    if rc != 0:
+        raise GpfcError(rc, lib.gpfc_strerror(rc).decode())
     return best_index, best_score
 
 
