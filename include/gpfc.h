@@ -167,6 +167,45 @@ int gpfc_score_cnn(gpfc_ctx *ctx, const float *folded, const int32_t *counts, in
 int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
                     int32_t nbins, const gpfc_cnn_weights *weights, float *logit);
 
+/* ------------------------------------------------------------------ CNN training
+ * The training loop of the scorer (Sec. 2.5: Adam minimising binary cross-entropy; the
+ * paper trains in TensorFlow): a forward pass that keeps its activations, the loss, the
+ * backward pass and the Adam update, all on the device.
+ *
+ * Bytes of the activation buffer gpfc_cnn_forward_train fills for `batch` profiles. */
+size_t gpfc_cnn_saved_bytes(int64_t batch);
+
+/* Forward pass (as gpfc_cnn_logits) that also stores, in `saved` (a caller-owned device
+ * buffer of gpfc_cnn_saved_bytes(batch) bytes), what the backward pass needs: the BF16
+ * normalised input, pre-activations and pooled outputs, the fc1 operand and fc1's FP32
+ * pre-activations. logit [batch] float32. */
+int gpfc_cnn_forward_train(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t batch,
+                           int32_t nbins, const gpfc_cnn_weights *weights, float *logit, void *saved);
+
+/* Gradients of the CNN parameters, FP32 device tensors in PyTorch layout (overwritten). */
+typedef struct {
+    float *conv1_w, *conv1_b, *conv2_w, *conv2_b, *conv3_w, *conv3_b;
+    float *fc1_w, *fc1_b, *fc2_w, *fc2_b;
+} gpfc_cnn_grads;
+
+/* Backward pass: given dL/dlogit [batch] (float32, device) for the forward that filled
+ * `saved` with the same weights, write dL/dparam for every parameter. The ReLU/max-pool
+ * gradient goes to the first maximum of each pooled pair; the computation is FP32 over
+ * the saved BF16 activations and BF16-rounded weights. Deterministic. */
+int gpfc_cnn_backward(gpfc_ctx *ctx, const float *dlogit, int64_t batch, const gpfc_cnn_weights *weights,
+                      const void *saved, const gpfc_cnn_grads *grads);
+
+/* Mean binary cross-entropy with logits over n items, loss = mean(max(z,0) - z*y +
+ * log1p(exp(-|z|))), and its gradient dlogit = (sigmoid(z) - y) / n. logit, label [n]
+ * float32; loss [1] and dlogit [n] float32, either may be NULL. */
+int gpfc_bce_with_logits(gpfc_ctx *ctx, const float *logit, const float *label, int64_t n, float *loss,
+                         float *dlogit);
+
+/* One Adam step on n FP32 values in place (Kingma & Ba, Algorithm 1): m and v are the
+ * moment buffers, step the 1-based step count used for the bias corrections. */
+int gpfc_adam(gpfc_ctx *ctx, float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+              float beta1, float beta2, float eps, int64_t step);
+
 /* ------------------------------------------------------------------ best period
  * argmax over score[n_periods] (NaN never wins; ties go to the smaller index), Sec. 2.1:
  * the trial period with the strongest score. best_index [1] int64 (-1 if every score is

@@ -334,3 +334,99 @@ def gpfc_search(ctx: Context, times, flux, periods, nbins: int, t0: float = math
                                    float(t0), int(scorer), pp, _ptr(score), _ptr(best_index),
                                    _ptr(best_score)))
     return score, best_index, best_score
+
+
+# ---------------------------------------------------------------- training
+
+
+class CnnGrads(ctypes.Structure):
+    _fields_ = CnnWeights._fields_
+
+
+def _bind_training(L):
+    if getattr(L, "_gpfc_train_bound", False):
+        return
+    L.gpfc_cnn_saved_bytes.argtypes = [ctypes.c_int64]
+    L.gpfc_cnn_saved_bytes.restype = ctypes.c_size_t
+    L.gpfc_cnn_forward_train.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights),
+                                         _vp, _vp]
+    L.gpfc_cnn_backward.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.POINTER(CnnWeights), _vp,
+                                    ctypes.POINTER(CnnGrads)]
+    L.gpfc_bce_with_logits.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp]
+    L.gpfc_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_int64]
+    L._gpfc_train_bound = True
+
+
+def gpfc_cnn_forward_train(ctx: Context, folded, weights, counts=None):
+    """Training forward: returns (logit [B], saved activations uint8 buffer)."""
+    _bind_training(ctx.lib)
+    dev = ctx.device
+    _need(folded, torch.float32, dev, "folded")
+    B = folded.shape[0]
+    if counts is not None:
+        _need(counts, torch.int32, dev, "counts", folded.numel())
+    saved = torch.empty(int(ctx.lib.gpfc_cnn_saved_bytes(B)), dtype=torch.uint8, device=dev)
+    logit = torch.empty(B, dtype=torch.float32, device=dev)
+    w = _cnn_weights(ctx, weights)
+    ctx._check(ctx.lib.gpfc_cnn_forward_train(ctx.handle, _ptr(folded), _ptr(counts), B, int(folded.shape[1]),
+                                              ctypes.byref(w), _ptr(logit), _ptr(saved)))
+    return logit, saved
+
+
+def gpfc_cnn_backward(ctx: Context, dlogit, weights, saved, grads=None):
+    """Backward pass: dict of FP32 gradients (PyTorch layout) for dL/dlogit."""
+    _bind_training(ctx.lib)
+    dev = ctx.device
+    _need(dlogit, torch.float32, dev, "dlogit")
+    if grads is None:
+        grads = {n: torch.empty(CNN_PARAM_SHAPES[n], dtype=torch.float32, device=dev) for n in CNN_PARAM_NAMES}
+    g = CnnGrads(*[ctypes.c_void_p(grads[n].data_ptr()) for n in CNN_PARAM_NAMES])
+    w = _cnn_weights(ctx, weights)
+    ctx._check(ctx.lib.gpfc_cnn_backward(ctx.handle, _ptr(dlogit), dlogit.numel(), ctypes.byref(w), _ptr(saved),
+                                         ctypes.byref(g)))
+    return grads
+
+
+def gpfc_bce_with_logits(ctx: Context, logit, label, want_grad=True):
+    """Mean BCE-with-logits loss (device scalar) and dL/dlogit."""
+    _bind_training(ctx.lib)
+    dev = ctx.device
+    _need(logit, torch.float32, dev, "logit")
+    _need(label, torch.float32, dev, "label", logit.numel())
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    dlogit = torch.empty_like(logit) if want_grad else None
+    ctx._check(ctx.lib.gpfc_bce_with_logits(ctx.handle, _ptr(logit), _ptr(label), logit.numel(), _ptr(loss),
+                                            _ptr(dlogit)))
+    return loss, dlogit
+
+
+def gpfc_adam(ctx: Context, param, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One in-place Adam step on an FP32 tensor."""
+    _bind_training(ctx.lib)
+    for t, n in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, torch.float32, ctx.device, n, param.numel())
+    ctx._check(ctx.lib.gpfc_adam(ctx.handle, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr),
+                                 float(beta1), float(beta2), float(eps), int(step)))
+
+
+class CNNFunction(torch.autograd.Function):
+    """CNN scorer as an autograd function: forward and backward run in libgpfc's kernels.
+
+    CNNFunction.apply(gctx, folded, counts_or_None, *params) -> logits [B]; params in the
+    order of CNN_PARAM_NAMES (FP32 CUDA tensors, PyTorch layout).
+    """
+
+    @staticmethod
+    def forward(fctx, gctx, folded, counts, *params):
+        weights = dict(zip(CNN_PARAM_NAMES, params))
+        logit, saved = gpfc_cnn_forward_train(gctx, folded, weights, counts)
+        fctx.gctx = gctx
+        fctx.saved_buffer = saved
+        fctx.weights = weights
+        return logit
+
+    @staticmethod
+    def backward(fctx, grad_logit):
+        grads = gpfc_cnn_backward(fctx.gctx, grad_logit.contiguous().float(), fctx.weights, fctx.saved_buffer)
+        return (None, None, None) + tuple(grads[n] for n in CNN_PARAM_NAMES)

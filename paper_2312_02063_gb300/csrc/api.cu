@@ -469,6 +469,126 @@ int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, i
     return cnn_forward(ctx, folded, counts, n_periods, nbins, wt, nullptr, logit);
 }
 
+size_t gpfc_cnn_saved_bytes(int64_t batch) { return batch > 0 ? cnn_saved_bytes(batch) : 0; }
+
+static bool cnn_weights_ok(const gpfc_cnn_weights *wt)
+{
+    if (!wt) return false;
+    const float *ptrs[10] = {wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                             wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+    for (const float *q : ptrs)
+        if (!q) return false;
+    return true;
+}
+
+static CnnSrc cnn_src(const gpfc_cnn_weights *wt)
+{
+    return CnnSrc{wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                  wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+}
+
+int gpfc_cnn_forward_train(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t batch,
+                           int32_t nbins, const gpfc_cnn_weights *wt, float *logit, void *saved)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!folded || !logit || !saved || !cnn_weights_ok(wt)) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (nbins != 256) return set_err(ctx, GPFC_ENOTSUP, "the CNN scorer takes 256-bin profiles, got %d", nbins);
+    if (batch < 1 || batch > (int64_t)1 << 22) return set_err(ctx, GPFC_EINVAL, "batch outside [1, 2^22]");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    rc = ensure_ws(ctx, cnn_dev_bytes() + 256);
+    if (rc) return rc;
+    const CnnDev dev = cnn_dev_carve(ctx->ws);
+    cudaError_t e = launch_cnn_prep(cnn_src(wt), dev, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "CNN weight preparation");
+    const CnnSaved S = CnnSaved::layout(batch);
+    uint8_t *sv = static_cast<uint8_t *>(saved);
+    KernelTimer timer(ctx);
+    CnnConvParams cp{};
+    cp.folded = folded;
+    cp.counts = counts;
+    cp.k_begin = 0;
+    cp.np = batch;
+    cp.w = dev;
+    cp.h3t = sv + S.h3t;
+    cp.xsave = reinterpret_cast<float *>(sv + S.x);
+    cp.a1save = reinterpret_cast<float *>(sv + S.a1);
+    cp.h1save = reinterpret_cast<uint16_t *>(sv + S.h1);
+    cp.a2save = reinterpret_cast<float *>(sv + S.a2);
+    cp.h2save = reinterpret_cast<uint16_t *>(sv + S.h2);
+    cp.a3save = reinterpret_cast<float *>(sv + S.a3);
+    cp.status = ctx->status_dev;
+    e = launch_cnn_conv(cp, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "CNN conv kernel");
+    CnnFcParams fp{};
+    fp.h3t = sv + S.h3t;
+    fp.k_begin = 0;
+    fp.np = batch;
+    fp.w = dev;
+    fp.logit = logit;
+    fp.z1save = reinterpret_cast<float *>(sv + S.z1);
+    fp.status = ctx->status_dev;
+    e = launch_cnn_fc(fp, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "CNN fc kernel");
+    timer.stop();
+    return GPFC_OK;
+}
+
+int gpfc_cnn_backward(gpfc_ctx *ctx, const float *dlogit, int64_t batch, const gpfc_cnn_weights *wt,
+                      const void *saved, const gpfc_cnn_grads *gr)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!dlogit || !saved || !gr || !cnn_weights_ok(wt)) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    float *gp[10] = {gr->conv1_w, gr->conv1_b, gr->conv2_w, gr->conv2_b, gr->conv3_w,
+                     gr->conv3_b, gr->fc1_w,   gr->fc1_b,   gr->fc2_w,   gr->fc2_b};
+    for (float *q : gp)
+        if (!q) return set_err(ctx, GPFC_EINVAL, "NULL gradient buffer");
+    if (batch < 1 || batch > (int64_t)1 << 22) return set_err(ctx, GPFC_EINVAL, "batch outside [1, 2^22]");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    const int nblk = (int)std::min<int64_t>(batch, (int64_t)ctx->num_sms * 2);
+    rc = ensure_ws(ctx, cnn_backward_ws_bytes(batch, nblk));
+    if (rc) return rc;
+    const CnnGrads g{gr->conv1_w, gr->conv1_b, gr->conv2_w, gr->conv2_b, gr->conv3_w,
+                     gr->conv3_b, gr->fc1_w,   gr->fc1_b,   gr->fc2_w,   gr->fc2_b};
+    cudaError_t e = launch_cnn_backward(cnn_src(wt), static_cast<const uint8_t *>(saved), batch, dlogit, g, ctx->ws,
+                                        nblk, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "CNN backward kernels");
+    return GPFC_OK;
+}
+
+int gpfc_bce_with_logits(gpfc_ctx *ctx, const float *logit, const float *label, int64_t n, float *loss,
+                         float *dlogit)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!logit || !label || (!loss && !dlogit)) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1) return set_err(ctx, GPFC_EINVAL, "n < 1");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    rc = ensure_ws(ctx, 256 * sizeof(double) + 256);
+    if (rc) return rc;
+    cudaError_t e = launch_bce(logit, label, n, dlogit, loss, ctx->ws, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "loss kernel");
+    return GPFC_OK;
+}
+
+int gpfc_adam(gpfc_ctx *ctx, float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+              float beta1, float beta2, float eps, int64_t step)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!param || !grad || !m || !v) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1 || step < 1) return set_err(ctx, GPFC_EINVAL, "n and step must be >= 1");
+    cudaSetDevice(ctx->device);
+    const double c1 = 1.0 - std::pow((double)beta1, (double)step);
+    const double c2 = 1.0 - std::pow((double)beta2, (double)step);
+    cudaError_t e = launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "Adam kernel");
+    return GPFC_OK;
+}
+
 int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods, int64_t *best_index,
                      float *best_score)
 {

@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
                     float acc = S.b1[co];
 #pragma unroll
                     for (int k = 0; k < 5; ++k) acc = fmaf(S.w1[co * 5 + k], in[l + k], acc);
+                    if (p.a1save && (k0 + prof - p.k_begin) < p.np)
+                        p.a1save[((size_t)(k0 + prof - p.k_begin) * 16 + co) * 256 + 4 * lp + l] = acc;
                     a[l] = fmaxf(acc, 0.f);
                 }
                 h[0][co] = bf16_bits(fmaxf(a[0], a[1]));
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
                     const int64_t k = k0 + prof;
                     if ((k - p.k_begin) < p.np)
                         for (int co = 0; co < 32; ++co)
-                            p.a2save[((size_t)(k - p.k_begin) * 32 + co) * 128 + l] = bf16_bits(v[co] + S.b2[co]);
+                            p.a2save[((size_t)(k - p.k_begin) * 32 + co) * 128 + l] = v[co] + S.b2[co];
                 }
             }
         }
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
                     const float o = __shfl_xor_sync(0xffffffffu, a, 2);
                     h[co] = bf16_bits(fmaxf(a, o));
                     if (p.a3save && valid)
-                        p.a3save[((size_t)(k - p.k_begin) * 64 + co) * 64 + l] = bf16_bits(pre);
+                        p.a3save[((size_t)(k - p.k_begin) * 64 + co) * 64 + l] = pre;
                 }
             }
             if ((l & 1) == 0 && valid) {

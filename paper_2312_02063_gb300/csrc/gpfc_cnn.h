@@ -46,10 +46,11 @@ struct CnnConvParams {
     uint8_t *h3t;            // [ceil(np/128)][32][128 x 64 BF16 tile] (local profile index)
     // activations kept for the backward pass (NULL at inference), local profile index
     float *xsave;            // [np][256] normalised input (BF16 values)
+    float *a1save;           // [np][16][256] FP32 conv1 pre-activation
     uint16_t *h1save;        // [np][16][128] BF16
-    uint16_t *a2save;        // [np][32][128] BF16 conv2 pre-activation
+    float *a2save;           // [np][32][128] FP32 conv2 pre-activation
     uint16_t *h2save;        // [np][32][64] BF16
-    uint16_t *a3save;        // [np][64][64] BF16 conv3 pre-activation
+    float *a3save;           // [np][64][64] FP32 conv3 pre-activation
     uint32_t *status;
 };
 
@@ -63,6 +64,26 @@ struct CnnFcParams {
     float *z1save;           // [np][256] fc1 pre-activation (NULL at inference)
     uint32_t *status;
 };
+
+// Offsets (bytes) of the activations a training forward keeps for the backward pass.
+struct CnnSaved {
+    size_t x, a1, h1, a2, h2, a3, h3t, z1, total;
+    static CnnSaved layout(int64_t B);
+};
+
+// FP32 gradients in PyTorch layout (device), overwritten by the backward pass.
+struct CnnGrads {
+    float *w1, *b1, *w2, *b2, *w3, *b3, *wf1, *bf1, *wf2, *bf2;
+};
+
+size_t cnn_saved_bytes(int64_t B);
+size_t cnn_backward_ws_bytes(int64_t B, int nblk);
+cudaError_t launch_cnn_backward(const CnnSrc &w, const uint8_t *saved, int64_t B, const float *dlogit,
+                                const CnnGrads &g, void *ws, int nblk, cudaStream_t st);
+cudaError_t launch_bce(const float *z, const float *y, int64_t n, float *dlogit, float *loss, void *ws,
+                       cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, float c1, float c2, cudaStream_t st);
 
 size_t cnn_dev_bytes();
 CnnDev cnn_dev_carve(void *base);
