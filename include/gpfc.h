@@ -206,6 +206,38 @@ int gpfc_bce_with_logits(gpfc_ctx *ctx, const float *logit, const float *label, 
 int gpfc_adam(gpfc_ctx *ctx, float *param, const float *grad, float *m, float *v, int64_t n, float lr,
               float beta1, float beta2, float eps, int64_t step);
 
+/* ------------------------------------------------------------------ training profiles
+ * Folded training profiles generated on the device: light curve j (global index) has
+ * n_cadences samples at t_i = i * cadence (t0 = 0), flux = 1 + sigma z_i + signal, folded
+ * at its true period P plus a frequency offset giving at most drift_bins bins of phase
+ * drift over the baseline. Even j: a box transit (label 1). Odd j, by (j/2) mod 3: noise
+ * only, a sinusoid, an eclipsing-binary-like primary + secondary box half a period
+ * later (label 0). sigma log-uniform in [sigma_min, sigma_max]; P uniform in
+ * [p_min, p_max] days; epoch uniform in [0, P); duration uniform in [dur_min_h,
+ * dur_max_h] hours; depth (and sinusoid amplitude) log-uniform in [depth_min,
+ * depth_max]; secondary depth = depth * U[0.2, 1]. Random numbers: Philox4x32-10
+ * (Salmon et al. 2011) keyed by `seed`; counter (j, 0, 0, 2^32-1) and (j, 1, 0, 2^32-1)
+ * for the parameters, (j, i/4, 1, 0) for the normals of samples 4(i/4)..4(i/4)+3 via
+ * Box-Muller on u = (x >> 8) 2^-24. The fold is the 64-bit fixed-point fold of
+ * gpfc_fold (t0 = 0), one light curve per block, bins merged within a warp with
+ * __match_any_sync; the means are 1 + (sum of (flux - 1)) / count. */
+typedef struct {
+    int32_t n_cadences;
+    double cadence;
+    double sigma_min, sigma_max;
+    double depth_min, depth_max;
+    double dur_min_h, dur_max_h;
+    double p_min, p_max;
+    double drift_bins;
+} gpfc_synth_params;
+
+/* folded [n][nbins] float32 (NaN = empty bin); counts [n][nbins] int32, label [n]
+ * float32, fold_period [n] float64 and flux_std [n] float32 (population std of each
+ * light curve's flux, the noise scale gpfc_search uses) may be NULL. nbins 2..256. */
+int gpfc_synth_profiles(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, int32_t nbins,
+                        const gpfc_synth_params *params, float *folded, int32_t *counts, float *label,
+                        double *fold_period, float *flux_std);
+
 /* ------------------------------------------------------------------ best period
  * argmax over score[n_periods] (NaN never wins; ties go to the smaller index), Sec. 2.1:
  * the trial period with the strongest score. best_index [1] int64 (-1 if every score is

@@ -237,3 +237,84 @@ def cnn_init(seed: int = 20232304, bias_scale: float = 0.0) -> dict:
             v = rng.uniform(-lim, lim, shape)
         out[name] = round_to_bf16(v.astype(np.float32))
     return out
+
+
+# ---------------------------------------------------------------- counter-based generator
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+_M32 = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11): 4 x 32-bit counter,
+    2 x 32-bit key -> 4 x 32-bit output. Each round multiplies words 0 and 2 by M0 and M1,
+    mixes the high halves with words 1/3 and the key, and the key is bumped by (W0, W1)
+    between rounds."""
+    c0, c1, c2, c3 = (int(v) & _M32 for v in ctr)
+    k0, k1 = (int(v) & _M32 for v in key)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + _PHILOX_W0) & _M32
+            k1 = (k1 + _PHILOX_W1) & _M32
+        p0 = _PHILOX_M0 * c0
+        p1 = _PHILOX_M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0) & _M32, p1 & _M32, ((p0 >> 32) ^ c3 ^ k1) & _M32, p0 & _M32
+    return (c0, c1, c2, c3)
+
+
+def _u64(x):
+    return (x >> 8) * (1.0 / 16777216.0)
+
+
+TRAINING_SET = dict(n_cadences=65536, cadence=29.4 / 1440.0, sigma_min=1e-4, sigma_max=1e-3,
+                    depth_min=30e-6, depth_max=2000e-6, dur_min_h=0.5, dur_max_h=3.0, p_min=0.2, p_max=1.0,
+                    drift_bins=0.5)
+
+
+def training_light_curve(seed: int, j: int, sp: dict = TRAINING_SET):
+    """Light curve j of the seeded training set (the recipe of gpfc_synth_profiles).
+
+    Returns (times f64, flux f64, label, fold_period). Parameters from Philox counters
+    (j, 0, 0, 2^32-1) and (j, 1, 0, 2^32-1); normals of samples 4m..4m+3 from counter
+    (j, m, 1, 0) by Box-Muller on u = (x >> 8) 2^-24.
+    """
+    key = (seed & _M32, (seed >> 32) & _M32)
+    a = philox4x32_10((j, 0, 0, _M32), key)
+    b = philox4x32_10((j, 1, 0, _M32), key)
+    kind = 0 if j % 2 == 0 else 1 + (j // 2) % 3
+    sigma = np.exp(np.log(sp["sigma_min"]) + _u64(a[0]) * np.log(sp["sigma_max"] / sp["sigma_min"]))
+    period = sp["p_min"] + _u64(a[1]) * (sp["p_max"] - sp["p_min"])
+    epoch = _u64(a[2]) * period
+    dur = (sp["dur_min_h"] + _u64(a[3]) * (sp["dur_max_h"] - sp["dur_min_h"])) / 24.0
+    depth = np.exp(np.log(sp["depth_min"]) + _u64(b[0]) * np.log(sp["depth_max"] / sp["depth_min"]))
+    depth2 = depth * (0.2 + 0.8 * _u64(b[1]))
+    amp = np.exp(np.log(sp["depth_min"]) + _u64(b[2]) * np.log(sp["depth_max"] / sp["depth_min"]))
+    T = sp["n_cadences"] * sp["cadence"]
+    df = (2.0 * _u64(b[3]) - 1.0) * sp["drift_bins"] / (256.0 * T)
+    fold_period = 1.0 / (1.0 / period + df)
+    n = sp["n_cadences"]
+    t = np.arange(n, dtype=np.float64) * sp["cadence"]
+    z = np.empty(n)
+    for m in range((n + 3) // 4):
+        r = philox4x32_10((j, m, 1, 0), key)
+        for h in range(2):
+            u1 = 1.0 - _u64(r[2 * h])
+            u2 = _u64(r[2 * h + 1])
+            rad = np.sqrt(-2.0 * np.log(u1))
+            for q, v in ((2 * h, rad * np.cos(2 * np.pi * u2)), (2 * h + 1, rad * np.sin(2 * np.pi * u2))):
+                if 4 * m + q < n:
+                    z[4 * m + q] = v
+    x = sigma * z
+
+    def inbox(centre):
+        d = np.mod(t - centre + 0.5 * period, period) - 0.5 * period
+        return np.abs(d) < 0.5 * dur
+
+    if kind == 0:
+        x = x - depth * inbox(epoch)
+    elif kind == 2:
+        x = x + amp * np.sin(2 * np.pi * (t - epoch) / period)
+    elif kind == 3:
+        x = x - depth * inbox(epoch) - depth2 * inbox(epoch + 0.5 * period)
+    return t, 1.0 + x, float(kind == 0), fold_period

@@ -430,3 +430,42 @@ class CNNFunction(torch.autograd.Function):
     def backward(fctx, grad_logit):
         grads = gpfc_cnn_backward(fctx.gctx, grad_logit.contiguous().float(), fctx.weights, fctx.saved_buffer)
         return (None, None, None) + tuple(grads[n] for n in CNN_PARAM_NAMES)
+
+
+class SynthParams(ctypes.Structure):
+    _fields_ = [("n_cadences", ctypes.c_int32), ("cadence", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
+                ("dur_min_h", ctypes.c_double), ("dur_max_h", ctypes.c_double),
+                ("p_min", ctypes.c_double), ("p_max", ctypes.c_double), ("drift_bins", ctypes.c_double)]
+
+
+# Training-set recipe: 65,536-cadence light curves at 29.4 min, transits with depth
+# log-uniform 30-2,000 ppm, duration 0.5-3 h, period 0.2-1 d, folded at the true period
+# with up to half a bin of drift; white noise log-uniform 1e-4..1e-3.
+TRAINING_SET = dict(n_cadences=65536, cadence=29.4 / 1440.0, sigma_min=1e-4, sigma_max=1e-3,
+                    depth_min=30e-6, depth_max=2000e-6, dur_min_h=0.5, dur_max_h=3.0, p_min=0.2, p_max=1.0,
+                    drift_bins=0.5)
+
+
+def gpfc_synth_profiles(ctx: Context, seed: int, first: int, n: int, nbins: int = 256, params=None,
+                        want_counts=True, want_period=False, want_std=False):
+    """Generate n training profiles j = first..first+n-1.
+
+    Returns (folded, counts, label, period, flux_std); unrequested outputs are None.
+    """
+    L = ctx.lib
+    if not getattr(L, "_gpfc_synth_bound", False):
+        L.gpfc_synth_profiles.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(SynthParams), _vp, _vp, _vp, _vp, _vp]
+        L._gpfc_synth_bound = True
+    sp = SynthParams(**(params or TRAINING_SET))
+    dev = ctx.device
+    folded = torch.empty((n, nbins), dtype=torch.float32, device=dev)
+    counts = torch.empty((n, nbins), dtype=torch.int32, device=dev) if want_counts else None
+    label = torch.empty(n, dtype=torch.float32, device=dev)
+    period = torch.empty(n, dtype=torch.float64, device=dev) if want_period else None
+    std = torch.empty(n, dtype=torch.float32, device=dev) if want_std else None
+    ctx._check(L.gpfc_synth_profiles(ctx.handle, ctypes.c_uint64(seed), first, n, nbins, ctypes.byref(sp),
+                                     _ptr(folded), _ptr(counts), _ptr(label), _ptr(period), _ptr(std)))
+    return folded, counts, label, period, std

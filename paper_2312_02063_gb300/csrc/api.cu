@@ -13,6 +13,7 @@
 #include "gpfc.h"
 #include "gpfc_cnn.h"
 #include "gpfc_kernels.h"
+#include "gpfc_synth.h"
 
 using namespace gpfc;
 
@@ -586,6 +587,28 @@ int gpfc_adam(gpfc_ctx *ctx, float *param, const float *grad, float *m, float *v
     const double c2 = 1.0 - std::pow((double)beta2, (double)step);
     cudaError_t e = launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "Adam kernel");
+    return GPFC_OK;
+}
+
+int gpfc_synth_profiles(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, int32_t nbins,
+                        const gpfc_synth_params *params, float *folded, int32_t *counts, float *label,
+                        double *fold_period, float *flux_std)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!params || !folded) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1 || first < 0 || first + n > ((int64_t)1 << 32)) return set_err(ctx, GPFC_EINVAL, "bad index range");
+    if (nbins < 2 || nbins > 256) return set_err(ctx, GPFC_EINVAL, "nbins outside [2, 256]");
+    const gpfc_synth_params &sp = *params;
+    if (sp.n_cadences < 1 || !(sp.cadence > 0) || !(sp.sigma_min > 0) || !(sp.sigma_max >= sp.sigma_min) ||
+        !(sp.depth_min > 0) || !(sp.depth_max >= sp.depth_min) || !(sp.p_min > 0) || !(sp.p_max >= sp.p_min) ||
+        sp.dur_min_h < 0 || sp.dur_max_h < sp.dur_min_h || sp.drift_bins < 0)
+        return set_err(ctx, GPFC_EINVAL, "synthesis parameters out of range");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    SynthParams p{seed, first, n, nbins, sp, folded, counts, label, fold_period, flux_std};
+    cudaError_t e = launch_synth(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "synthesis kernel");
     return GPFC_OK;
 }
 

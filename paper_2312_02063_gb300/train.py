@@ -1,0 +1,136 @@
+"""Training and evaluation of the CNN scorer on device-generated folded profiles.
+
+Everything on the data path runs in libgpfc's kernels: light curves are generated and
+folded on the GPU (gpfc_synth_profiles), the network's forward and backward passes,
+the loss and the Adam updates are the library's own kernels. The detection comparison
+ranks held-out profiles by the CNN score and by the box-SNR statistic (in units of each
+light curve's flux standard deviation, as gpfc_search defines it) and reports the
+true-positive rate at a fixed false-positive rate.
+
+  python -m paper_2312_02063_gb300.train --profiles 2000000 --batch 4096 --out run.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import (CNN_PARAM_NAMES, CNN_PARAM_SHAPES, Context, gpfc_adam, gpfc_bce_with_logits, gpfc_cnn_backward,
+               gpfc_cnn_forward_train, gpfc_score_box, gpfc_score_cnn, gpfc_synth_profiles)
+
+TRAIN_SEED = 20234204
+EVAL_SEED = 20234999
+BOX_W_MAX = 160   # widest transit of the training set: 3 h at P = 0.2 d is 0.625 of a cycle
+
+
+def init_weights(device, seed: int = 1) -> dict:
+    """He-uniform weights U(+-sqrt(6/fan_in)), zero biases, FP32 master copies."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    out = {}
+    for n in CNN_PARAM_NAMES:
+        shape = CNN_PARAM_SHAPES[n]
+        if n.endswith(".b"):
+            t = torch.zeros(shape)
+        else:
+            fan_in = int(np.prod(shape[1:]))
+            lim = math.sqrt(6.0 / fan_in)
+            t = (torch.rand(shape, generator=g) * 2 - 1) * lim
+        out[n] = t.to(device=device, dtype=torch.float32).contiguous()
+    return out
+
+
+def train(ctx: Context, n_profiles: int, batch: int = 4096, lr: float = 1e-3, seed: int = 1,
+          data_seed: int = TRAIN_SEED, first: int = 0, weights: dict | None = None, log_every: int = 50):
+    """Adam on BCE-with-logits over n_profiles generated profiles (one pass, batch by batch).
+
+    Returns (weights, history) where history lists (step, loss) every log_every steps.
+    """
+    params = weights if weights is not None else init_weights(ctx.device, seed)
+    m = {n: torch.zeros_like(p) for n, p in params.items()}
+    v = {n: torch.zeros_like(p) for n, p in params.items()}
+    steps = (n_profiles + batch - 1) // batch
+    hist = []
+    for s in range(steps):
+        nb = min(batch, n_profiles - s * batch)
+        f, c, y, _, _ = gpfc_synth_profiles(ctx, data_seed, first + s * batch, nb)
+        logit, saved = gpfc_cnn_forward_train(ctx, f, params, c)
+        loss, dl = gpfc_bce_with_logits(ctx, logit, y)
+        grads = gpfc_cnn_backward(ctx, dl, params, saved)
+        for n in CNN_PARAM_NAMES:
+            gpfc_adam(ctx, params[n], grads[n], m[n], v[n], s + 1, lr)
+        if s % log_every == 0 or s == steps - 1:
+            hist.append((s, float(loss.item())))
+    ctx.sync()
+    return params, hist
+
+
+def tpr_at_fpr(pos, neg, fpr):
+    """TPR with the threshold at the (floor(fpr * n_neg) + 1)-th largest negative score."""
+    neg = np.sort(np.asarray(neg, np.float64))[::-1]
+    k = int(np.floor(fpr * len(neg)))
+    thr = neg[k] if k < len(neg) else -np.inf
+    return float(np.mean(np.asarray(pos, np.float64) > thr)), float(thr)
+
+
+def evaluate(ctx: Context, weights: dict, n_eval: int = 200_000, seed: int = EVAL_SEED, fpr: float = 1e-3,
+             chunk: int = 16384, w_max: int = BOX_W_MAX):
+    """Held-out detection comparison: CNN score vs box-SNR at a fixed false-positive rate."""
+    cnn, box, lab, kinds = [], [], [], []
+    for j0 in range(0, n_eval, chunk):
+        nb = min(chunk, n_eval - j0)
+        f, c, y, _, sd = gpfc_synth_profiles(ctx, seed, j0, nb, want_std=True)
+        s_cnn = gpfc_score_cnn(ctx, f, weights, c)
+        s_box, _, _ = gpfc_score_box(ctx, f, c, 1, w_max, 1.0, want_best=False)
+        cnn.append(s_cnn.cpu().numpy())
+        box.append((s_box / sd).cpu().numpy())
+        lab.append(y.cpu().numpy())
+        j = np.arange(j0, j0 + nb)
+        kinds.append(np.where(j % 2 == 0, 0, 1 + (j // 2) % 3))
+    ctx.sync()
+    cnn, box, lab, kinds = map(np.concatenate, (cnn, box, lab, kinds))
+    pos, neg = lab > 0.5, lab < 0.5
+    t_cnn, thr_cnn = tpr_at_fpr(cnn[pos], cnn[neg], fpr)
+    t_box, thr_box = tpr_at_fpr(box[pos], box[neg], fpr)
+    names = {1: "noise", 2: "sinusoid", 3: "eclipsing_binary"}
+    fa = {names[k]: {"cnn": float(np.mean(cnn[kinds == k] > thr_cnn)), "box": float(np.mean(box[kinds == k] > thr_box))}
+          for k in (1, 2, 3)}
+    return {"fpr": fpr, "n_pos": int(pos.sum()), "n_neg": int(neg.sum()), "tpr_cnn": t_cnn, "tpr_box": t_box,
+            "threshold_cnn": thr_cnn, "threshold_box": thr_box, "false_alarm_rate_by_kind": fa,
+            "accuracy_cnn_at_0.5": float(np.mean((cnn > 0.5) == pos))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profiles", type=int, default=2_000_000)
+    ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval", type=int, default=200_000)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--save", default=None, help="write the trained weights (torch.save of FP32 tensors)")
+    a = ap.parse_args()
+    ctx = Context(0)
+    t0 = time.time()
+    w = None
+    hist = []
+    for e in range(a.epochs):
+        w, h = train(ctx, a.profiles, a.batch, a.lr, weights=w)
+        hist += [(e, s, l) for s, l in h]
+    t_train = time.time() - t0
+    res = evaluate(ctx, w, a.eval)
+    res.update(train_profiles=a.profiles, epochs=a.epochs, batch=a.batch, lr=a.lr, train_seconds=t_train,
+               loss_history=hist)
+    print(json.dumps(res))
+    if a.out:
+        with open(a.out, "w") as fo:
+            json.dump(res, fo, indent=1)
+    if a.save:
+        torch.save({n: t.cpu() for n, t in w.items()}, a.save)
+
+
+if __name__ == "__main__":
+    main()
