@@ -267,8 +267,10 @@ int gpfc_best_period_noalloc(const float *score, int64_t n_periods, int64_t *bes
                              float *best_score, void *stream);
 
 /* ------------------------------------------------------------------ search
- * Fold + score in one pass (Fig. 1): the profiles stay on chip and are not written.
- * scorer GPFC_SCORER_BOX takes a gpfc_box_params* in scorer_params.
+ * Fold + score (Fig. 1) without returning the profiles. scorer GPFC_SCORER_BOX takes a
+ * gpfc_box_params* in scorer_params: the box search runs in the fold kernel's epilogue on
+ * the profile held on chip. GPFC_SCORER_CNN takes a gpfc_cnn_weights* (nbins must be
+ * 256): periods are folded in chunks whose profiles stay in L2 for the CNN kernels.
  * score [n_periods] float32; best_index [1] int64 and best_score [1] float32 (device,
  * may be NULL). Limits as for gpfc_fold. */
 typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;

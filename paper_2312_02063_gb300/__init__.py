@@ -310,7 +310,7 @@ def gpfc_best_period_noalloc(score, best_index, best_score, stream=None):
 
 def gpfc_search(ctx: Context, times, flux, periods, nbins: int, t0: float = math.nan, scorer: int = SCORER_BOX,
                 w_min: int = 1, w_max: int | None = None, sigma: float = 0.0, score=None, best_index=None,
-                best_score=None):
+                best_score=None, weights=None):
     """Fold + score without materialising profiles. Returns (score [P], best_index [1], best_score [1])."""
     dev = ctx.device
     n, npd = times.numel(), periods.numel()
@@ -328,8 +328,13 @@ def gpfc_search(ctx: Context, times, flux, periods, nbins: int, t0: float = math
             w_max = int(math.ceil(0.125 * nbins))
         params = BoxParams(int(w_min), int(w_max), float(sigma))
         pp = ctypes.cast(ctypes.pointer(params), _vp)
+    elif scorer == SCORER_CNN:
+        if weights is None:
+            raise ValueError("the CNN scorer needs weights")
+        params = _cnn_weights(ctx, weights)
+        pp = ctypes.cast(ctypes.pointer(params), _vp)
     else:
-        raise GpfcError(-6, f"scorer {scorer} is not available through this call yet")
+        raise GpfcError(-6, f"unknown scorer {scorer}")
     ctx._check(ctx.lib.gpfc_search(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), npd, int(nbins),
                                    float(t0), int(scorer), pp, _ptr(score), _ptr(best_index),
                                    _ptr(best_score)))

@@ -245,6 +245,112 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     return GPFC_OK;
 }
 
+bool cnn_weights_ok(const gpfc_cnn_weights *wt)
+{
+    if (!wt) return false;
+    const float *ptrs[10] = {wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                             wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+    for (const float *q : ptrs)
+        if (!q) return false;
+    return true;
+}
+
+CnnSrc cnn_src(const gpfc_cnn_weights *wt)
+{
+    return CnnSrc{wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
+                  wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
+}
+
+// Fold + CNN search of one star. Periods go through in chunks of one fold wave (one
+// block of 4 x 32 periods per SM); each chunk's means and counts, and the CNN's fc1
+// operand tiles for half a chunk at a time, stay resident in L2 between the kernels.
+int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                   int64_t np, int32_t nbins, double t0, const gpfc_cnn_weights *wt, float *score,
+                   int64_t *best_index, float *best_score)
+{
+    const int64_t wave = (int64_t)ctx->num_sms * 128;
+    const int64_t chunk = std::min<int64_t>(np, wave);
+    const int64_t half = (chunk + 1) / 2;
+    const FoldPlan pl = plan_fold(ctx, n, chunk, nbins);
+    FoldBuffers fb{};
+    Carver c(nullptr);
+    c.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
+    c.take<float>((size_t)chunk * nbins);
+    c.take<int32_t>((size_t)chunk * nbins);
+    c.take<uint8_t>(cnn_dev_bytes());
+    c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+    c.take<unsigned long long>(1);
+    int rc = ensure_ws(ctx, c.off + 256);
+    if (rc) return rc;
+    Carver w(ctx->ws);
+    uint8_t *fold_base = w.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
+    carve_fold(fold_base, pl, n, 1, nbins, fb);
+    float *cf = w.take<float>((size_t)chunk * nbins);
+    int32_t *cc = w.take<int32_t>((size_t)chunk * nbins);
+    const CnnDev dev = cnn_dev_carve(w.take<uint8_t>(cnn_dev_bytes()));
+    uint8_t *h3t = w.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+    unsigned long long *key = w.take<unsigned long long>(1);
+
+    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G, fb.stats,
+                                ctx->status_dev, ctx->stream);
+    if (e == cudaSuccess) e = launch_cnn_prep(cnn_src(wt), dev, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    KernelTimer timer(ctx);
+    for (int64_t k0 = 0; k0 < np; k0 += chunk) {
+        const int64_t nk = std::min<int64_t>(chunk, np - k0);
+        FoldParams p{};
+        p.smp = fb.smp;
+        p.n = n;
+        p.periods = periods + k0;
+        p.np = nk;
+        p.ntasks = (nk + pl.ppc - 1) / pl.ppc;
+        p.nstars = 1;
+        p.stats = fb.stats;
+        p.nbins = nbins;
+        p.shift = shift_of(nbins);
+        p.warps = pl.warps;
+        p.chunk = pl.chunk;
+        p.layout = pl.layout;
+        p.ws_sc = fb.ws_sc;
+        p.ws_cnt = fb.ws_cnt;
+        p.folded = cf;
+        p.counts = cc;
+        p.status = ctx->status_dev;
+        e = launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "fold kernel");
+        for (int64_t h0 = 0; h0 < nk; h0 += half) {
+            const int64_t nh = std::min<int64_t>(half, nk - h0);
+            CnnConvParams cp{};
+            cp.folded = cf;
+            cp.counts = cc;
+            cp.k_begin = h0;
+            cp.np = nh;
+            cp.w = dev;
+            cp.h3t = h3t;
+            cp.status = ctx->status_dev;
+            e = launch_cnn_conv(cp, ctx->num_sms, ctx->stream);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "CNN conv kernel");
+            CnnFcParams fp{};
+            fp.h3t = h3t;
+            fp.k_begin = h0;
+            fp.np = nh;
+            fp.w = dev;
+            fp.score = score + k0;
+            fp.status = ctx->status_dev;
+            e = launch_cnn_fc(fp, ctx->num_sms, ctx->stream);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "CNN fc kernel");
+        }
+    }
+    timer.stop();
+    if (best_index || best_score) {
+        e = cudaMemsetAsync(key, 0, sizeof(*key), ctx->stream);
+        if (e == cudaSuccess) e = launch_argmax(score, np, key, ctx->stream);
+        if (e == cudaSuccess) e = launch_argmax_finalize(key, 1, best_index, best_score, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "argmax kernels");
+    }
+    return GPFC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -472,22 +578,6 @@ int gpfc_cnn_logits(gpfc_ctx *ctx, const float *folded, const int32_t *counts, i
 
 size_t gpfc_cnn_saved_bytes(int64_t batch) { return batch > 0 ? cnn_saved_bytes(batch) : 0; }
 
-static bool cnn_weights_ok(const gpfc_cnn_weights *wt)
-{
-    if (!wt) return false;
-    const float *ptrs[10] = {wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
-                             wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
-    for (const float *q : ptrs)
-        if (!q) return false;
-    return true;
-}
-
-static CnnSrc cnn_src(const gpfc_cnn_weights *wt)
-{
-    return CnnSrc{wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
-                  wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
-}
-
 int gpfc_cnn_forward_train(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t batch,
                            int32_t nbins, const gpfc_cnn_weights *wt, float *logit, void *saved)
 {
@@ -659,6 +749,12 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
             if (e != cudaSuccess) return cuda_err(ctx, e, "argmax finalize");
         }
         return GPFC_OK;
+    }
+    if (scorer == GPFC_SCORER_CNN) {
+        const auto *wt = static_cast<const gpfc_cnn_weights *>(scorer_params);
+        if (!cnn_weights_ok(wt)) return set_err(ctx, GPFC_EINVAL, "CNN scorer needs gpfc_cnn_weights");
+        if (nbins != 256) return set_err(ctx, GPFC_ENOTSUP, "the CNN scorer takes 256 bins, got %d", nbins);
+        return run_search_cnn(ctx, times, flux, n, periods, n_periods, nbins, t0, wt, score, best_index, best_score);
     }
     return set_err(ctx, GPFC_ENOTSUP, "scorer %d not available", scorer);
 }

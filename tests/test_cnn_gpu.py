@@ -79,3 +79,26 @@ def test_cnn_degenerate_profiles(ctx):
     _, s = run(ctx, prof, w)
     _, so = oracle.cnn_score(w, prof)
     assert np.max(np.abs(s - so)) <= SCORE_ATOL
+
+
+def test_search_with_cnn_scorer_matches_fold_then_score(ctx):
+    # fused search (chunked fold -> CNN) equals the two-step path, and the oracle on samples
+    import paper_2312_02063_gb300 as g
+    lc = lcsynth.light_curve_kepler(seed=77, n_cad=20000)
+    periods = lcsynth.freq_grid(45_000)  # more than one fold wave: several chunks
+    w = scaled_weights(31, 0.25)
+    wd = dev_weights(ctx, w)
+    t = torch.from_numpy(lc.times).to(ctx.device)
+    f = torch.from_numpy(lc.flux).to(ctx.device)
+    p = torch.from_numpy(periods).to(ctx.device)
+    sc, bi, bs = g.gpfc_search(ctx, t, f, p, 256, lc.t0, g.SCORER_CNN, weights=wd)
+    fo, co = g.gpfc_fold(ctx, t, f, p, 256, lc.t0)
+    s2 = g.gpfc_score_cnn(ctx, fo, wd, co)
+    ctx.sync()
+    sc, s2 = sc.cpu().numpy(), s2.cpu().numpy()
+    assert np.array_equal(sc, s2)
+    assert int(bi.item()) == int(np.argmax(sc)) and float(bs.item()) == sc.max()
+    idx = np.random.default_rng(0).choice(len(periods), 40, replace=False)
+    mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods[idx], 256, lc.t0)
+    _, so = oracle.cnn_score(w, mean_o.astype(np.float32), cnt_o.astype(np.int32))
+    assert np.max(np.abs(sc[idx] - so)) <= SCORE_ATOL
