@@ -159,6 +159,63 @@ def run_reference(args, rank, world):
     return 0
 
 
+def timed(fn, flush, stream, reps=5):
+    """Median CUDA-event time (ms) of fn() with an L2 flush before every repetition."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args):
+    """Fold + CNN search on the same star, CNN and box scoring of 262,144 profiles, and the
+    CNN vs box-SNR detection comparison at FPR = 1e-3 after a short training run."""
+    import torch
+    from paper_2312_02063_gb300 import train as tr
+    peaks, src = measured_peaks()
+    n = lc.times.shape[0]
+    out = {}
+    w = tr.init_weights(ctx.device, 1)
+    score = torch.empty(len(periods), dtype=torch.float32, device=ctx.device)
+    ms = timed(lambda: g.gpfc_search(ctx, t_d, f_d, p_d, NBINS, lc.t0, g.SCORER_CNN, score=score, weights=w),
+               flush, stream)
+    out["cnn_search"] = {"ms": ms, "periods_scored_per_s": len(periods) / (ms * 1e-3),
+                         "folds_per_s": n * len(periods) / (ms * 1e-3),
+                         "workload": "same star and grid as the main line, scorer = CNN"}
+    npf = args.cnn_profiles
+    prof, counts, _, _, _ = g.gpfc_synth_profiles(ctx, 20233204, 0, npf)
+    sc = torch.empty(npf, dtype=torch.float32, device=ctx.device)
+    ms = timed(lambda: g.gpfc_score_cnn(ctx, prof, w, counts, score=sc), flush, stream)
+    flop = 3_056_128.0 * npf
+    peak_tf = float(peaks.get("bf16_tflops", 1900.0))
+    out["cnn_scoring"] = {"ms": ms, "profiles_per_s": npf / (ms * 1e-3), "tflops": flop / (ms * 1e-3) / 1e12,
+                          "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak_tf,
+                                       "unit": "TFLOP/s", "frac": flop / (ms * 1e-3) / 1e12 / peak_tf,
+                                       "peak_basis": f"{src} bf16_tflops (burst)"},
+                          "workload": f"{npf} folded 256-bin profiles (device-generated: half transits, half "
+                                      "noise/sinusoid/eclipsing binary), FP32 in, BF16 tensor-core compute"}
+    ms = timed(lambda: g.gpfc_score_box(ctx, prof, counts, 1, 32, 1.0, want_best=False), flush, stream)
+    out["box_scoring"] = {"ms": ms, "profiles_per_s": npf / (ms * 1e-3),
+                          "workload": f"same {npf} profiles, box widths 1..32"}
+    if args.train_steps > 0:
+        wt, hist = tr.train(ctx, args.train_steps * 4096, batch=4096, lr=2e-3)
+        res = tr.evaluate(ctx, wt, n_eval=args.eval_profiles, fpr=1e-3)
+        out["detection"] = {"tpr_cnn": res["tpr_cnn"], "tpr_box": res["tpr_box"], "fpr": 1e-3,
+                            "n_pos": res["n_pos"], "n_neg": res["n_neg"],
+                            "train_profiles": args.train_steps * 4096, "final_loss": hist[-1][1],
+                            "note": "short training in the bench; the full training run is reported separately"}
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2312_02063_gb300 as g
@@ -277,10 +334,12 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 6 * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }
+        if not args.no_cnn:
+            result.update(cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args))
         print(json.dumps(result), flush=True)
     ctx.close()
     if dist:
@@ -297,6 +356,10 @@ def main():
     ap.add_argument("--cpu-periods", type=int, default=6000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-periods", type=int, default=N_PERIODS)
+    ap.add_argument("--no-cnn", action="store_true", help="skip the CNN and detection measurements")
+    ap.add_argument("--train-steps", type=int, default=60)
+    ap.add_argument("--cnn-profiles", type=int, default=262_144)
+    ap.add_argument("--eval-profiles", type=int, default=40_000)
     args = ap.parse_args()
     globals()["N_PERIODS"] = args.n_periods
     rank, world, local_rank = env_rank()
