@@ -35,6 +35,10 @@ NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
 SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, per SM
+# DRAM bytes (read + write) of one fold_kernel<box> launch over 19,456 periods of the same
+# light curve, from the ncu capture summarised in profiles/fold_kernel_box_kepler62835.md;
+# scaled to the bench's period count (traffic grows with the number of periods).
+FOLD_DRAM_BYTES_19456 = 1.009152e6 + 18.938880e6
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -328,7 +332,9 @@ def run_gpu(args, rank, world, local_rank):
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
             "roofline": {"bound": "alu", "kernel": "fold_kernel<box>", "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
-                         "traffic": None, "kernel_ms": kmean,
+                         "traffic": FOLD_DRAM_BYTES_19456 * N_PERIODS / 19456,
+                         "traffic_basis": "ncu dram__bytes_read+write of a 19,456-period launch, scaled by periods",
+                         "kernel_ms": kmean,
                          "peak_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} bin updates/clk "
                                        f"(shared-memory pipe) x {smax:.0f} MHz ({src} sm_max_mhz)"},
             "cpu_baseline": cpu,
