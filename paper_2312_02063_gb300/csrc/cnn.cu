@@ -106,8 +106,7 @@ struct ConvSmem {
     float b1[16];
     float b2[32];
     float b3[64];
-    double red[2][4];
-    float stat[2][2];
+    float red[2][6];
     uint64_t bar;
     uint32_t tslot;
     int abort;
@@ -164,39 +163,58 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
                     for (int u = 0; u < 4; ++u) ne[u] = !(v[u] != v[u]);
                 }
             }
-            double sum = 0.0, cnt = 0.0;
+            // FP32 throughout (this GPU's FP64 rate is tiny): the sum of the values is
+            // compensated (TwoSum), the deviations v - m are small and exact-ish in FP32,
+            // and one reciprocal standard deviation per profile scales them.
+            float sh = 0.f, sl = 0.f, cnt = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (ne[u]) {
-                    sum += (double)v[u];
-                    cnt += 1.0;
+                    const float t = sh + v[u];
+                    const float bb = t - sh;
+                    sl += (sh - (t - bb)) + (v[u] - bb);
+                    sh = t;
+                    cnt += 1.f;
                 }
             for (int o = 16; o > 0; o >>= 1) {
-                sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
                 cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                const float t = sh + oh;
+                const float bb = t - sh;
+                sl += ol + ((sh - (t - bb)) + (oh - bb));
+                sh = t;
             }
             if (lane == 0) {
-                S.red[prof][(warp & 1) * 2 + 0] = sum;
-                S.red[prof][(warp & 1) * 2 + 1] = cnt;
+                S.red[prof][(warp & 1) * 3 + 0] = sh;
+                S.red[prof][(warp & 1) * 3 + 1] = sl;
+                S.red[prof][(warp & 1) * 3 + 2] = cnt;
             }
             __syncthreads();
-            const double n = S.red[prof][1] + S.red[prof][3];
-            const double m = n > 0.0 ? (S.red[prof][0] + S.red[prof][2]) / n : 0.0;
-            double d[4], ss = 0.0;
+            const float n = S.red[prof][2] + S.red[prof][5];
+            float m = 0.f;
+            if (n > 0.f) {
+                const float t = S.red[prof][0] + S.red[prof][3];
+                const float bb = t - S.red[prof][0];
+                const float lo = S.red[prof][1] + S.red[prof][4] + ((S.red[prof][0] - (t - bb)) + (S.red[prof][3] - bb));
+                m = (t + lo) / n;
+            }
+            float d[4], ss = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                d[u] = ne[u] ? (double)v[u] - m : 0.0;
-                ss += d[u] * d[u];
+                d[u] = ne[u] ? v[u] - m : 0.f;
+                ss = fmaf(d[u], d[u], ss);
             }
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
             __syncthreads();
-            if (lane == 0) S.red[prof][(warp & 1) * 2] = ss;
+            if (lane == 0) S.red[prof][(warp & 1) * 3] = ss;
             __syncthreads();
-            const double sd = n > 0.0 ? sqrt((S.red[prof][0] + S.red[prof][2]) / n) : 0.0;
+            const float var = n > 0.f ? (S.red[prof][0] + S.red[prof][3]) / n : 0.f;
+            const float inv_sd = var > 0.f ? 1.0f / sqrtf(var) : 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const double x = (sd > 0.0 && ne[u]) ? m + d[u] / sd : m;
-                S.X[prof][4 * q + u] = bf16_round((float)x);
+                const float x = (inv_sd > 0.f && ne[u]) ? fmaf(d[u], inv_sd, m) : m;
+                S.X[prof][4 * q + u] = bf16_round(x);
             }
             if (p.xsave && valid) {
                 // normalised BF16 input, kept for the backward pass
@@ -431,12 +449,12 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
     const uint32_t tmem = S.tslot;
     const float b2 = p.w.bf2[0];
     const int64_t ntiles = (p.np + 127) / 128;
-    const int64_t npairs = (ntiles + 1) / 2;
+    const int64_t npairs = (ntiles + p.tiles_per_block - 1) / p.tiles_per_block;
     uint32_t it_prod = 0, it_mma = 0, done_phase = 0;
 
     for (int64_t pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
-        const int64_t mt0 = 2 * pair;
-        const bool two = mt0 + 1 < ntiles;
+        const int64_t mt0 = (int64_t)p.tiles_per_block * pair;
+        const bool two = p.tiles_per_block == 2 && mt0 + 1 < ntiles;
         if (tid == 0) {
             // producer: stream the two activation tiles and fc1's weights, K chunk by chunk
             for (int kc = 0; kc < 32 && !S.abort; ++kc, ++it_prod) {
@@ -571,13 +589,17 @@ cudaError_t launch_cnn_conv(const CnnConvParams &p, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_cnn_fc(const CnnFcParams &p, int num_sms, cudaStream_t st)
+cudaError_t launch_cnn_fc(const CnnFcParams &p_in, int num_sms, cudaStream_t st)
 {
     cudaError_t e = cnn_register_kernels();
     if (e != cudaSuccess) return e;
+    CnnFcParams p = p_in;
     const int64_t ntiles = (p.np + 127) / 128;
-    const int64_t npairs = (ntiles + 1) / 2;
-    const int grid = (int)(npairs < (int64_t)num_sms ? npairs : (int64_t)num_sms);
+    // two tiles per block share each streamed weight chunk; with fewer tiles than two per
+    // SM, one tile per block keeps every SM busy instead
+    p.tiles_per_block = ntiles >= 2 * (int64_t)num_sms ? 2 : 1;
+    const int64_t nblk = (ntiles + p.tiles_per_block - 1) / p.tiles_per_block;
+    const int grid = (int)(nblk < (int64_t)num_sms ? nblk : (int64_t)num_sms);
     cnn_fc_kernel<<<grid, 128, sizeof(FcSmem), st>>>(p);
     return cudaGetLastError();
 }

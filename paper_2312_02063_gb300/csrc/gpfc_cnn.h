@@ -63,6 +63,7 @@ struct CnnFcParams {
     float *logit;            // [global] or NULL
     float *z1save;           // [np][256] fc1 pre-activation (NULL at inference)
     uint32_t *status;
+    int tiles_per_block;     // set by launch_cnn_fc: 128-profile tiles per block (1 or 2)
 };
 
 // Offsets (bytes) of the activations a training forward keeps for the backward pass.
