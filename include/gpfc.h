@@ -74,24 +74,58 @@ int gpfc_num_sms(const gpfc_ctx *ctx);
 int gpfc_set_timing(gpfc_ctx *ctx, int enable);
 int gpfc_kernel_time_ms(gpfc_ctx *ctx, float *ms);
 
-/* Launch configuration of the fold kernel (gpfc_fold, gpfc_search). Every field 0
- * means "automatic". The results do not depend on it except for the FP32 rounding of
- * the per-chunk partial sums (chunk).
- *   warps   warps per block, 32 trial periods per warp (1..16, capped by shared memory)
- *   layout  shared-memory bins: 1 = FP32 sum + 16-bit count (6 B per bin),
- *           2 = FP32 sum + 32-bit count in one 64-bit word (8 B per bin)
- *   chunk   samples per compensated chunk (rounded down to a multiple of 16, 256..65520) */
+/* Launch configuration of the fold kernel (gpfc_fold, gpfc_search, gpfc_search_batched).
+ * Every field 0 means "automatic" (the autotuner's choice if it has one, else a default).
+ * The results do not depend on it except for the FP32 rounding of the per-chunk partial
+ * sums (chunk): warps, layout, tile and blocks_per_sm give bit-identical outputs.
+ *   warps          warps per block, 32 trial periods per warp (1..16, capped by shared memory)
+ *   layout         shared-memory bins: 1 = FP32 sum + 16-bit count (6 B per bin),
+ *                  2 = FP32 sum + 32-bit count in one 64-bit word (8 B per bin)
+ *   chunk          samples per compensated chunk (rounded down to a multiple of 16, 256..65520)
+ *   tile           light-curve samples per bulk copy into shared memory: 512, 1024 or 2048
+ *   blocks_per_sm  resident blocks per multiprocessor of the persistent grid (capped by
+ *                  what fits) */
 typedef struct {
     int32_t warps;
     int32_t layout;
     int32_t chunk;
+    int32_t tile;
+    int32_t blocks_per_sm;
 } gpfc_fold_config;
 
-/* Set (cfg != NULL) or reset to automatic (cfg == NULL) the context's fold config. */
+/* Set (cfg != NULL) or reset to automatic (cfg == NULL) the context's fold config.
+ * GPFC_EINVAL if a field is out of range. */
 int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg);
 
-/* Largest `warps` the fold kernel fits in shared memory for nbins and layout (0 if none). */
+/* Largest `warps` the fold kernel fits in shared memory for nbins and layout with
+ * 1024-sample tiles (0 if none). */
 int gpfc_fold_max_warps(int32_t nbins, int32_t layout);
+
+/* The launch config of the context's most recent fold launch plan (all fields filled). */
+int gpfc_last_fold_plan(const gpfc_ctx *ctx, gpfc_fold_config *out);
+
+/* Autotuner. gpfc_autotune times the fold kernel on the given star (device arrays, as
+ * for gpfc_search) over its first min(n_periods, 4 * 128 * SMs) periods for every launch
+ * config (layout x tile x warps, with the blocks per SM that fit) whose resident periods
+ * per SM are at least half the largest, and keeps the fastest in the context under
+ * (nbins, scorer, floor(log2 n)). scorer GPFC_SCORER_BOX times the fold with its box-SNR
+ * epilogue (scorer_params: gpfc_box_params*), GPFC_SCORER_CNN the fold that writes
+ * profiles (scorer_params unused). The chosen config goes to *out (host, may be NULL).
+ * It synchronises the context's stream (GPFC_EINVAL under stream capture) and writes
+ * nothing the caller owns.
+ * With autotuning enabled (the default), gpfc_fold, gpfc_search and gpfc_search_batched
+ * use a tuned config with a matching key, and gpfc_search_batched tunes on its first
+ * star when there is none (keyed by the average star length), unless its stream is
+ * capturing. gpfc_set_autotune(ctx, 0) disables both; enable < 0 also forgets the
+ * tuned configs. Fields set by gpfc_set_fold_config take precedence. */
+int gpfc_autotune(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
+                  const double *periods, int64_t n_periods, int32_t nbins, int scorer,
+                  const void *scorer_params, gpfc_fold_config *out);
+int gpfc_set_autotune(gpfc_ctx *ctx, int enable);
+
+/* Device workspace (bytes) the context needs for gpfc_fold / gpfc_search (box scorer) of
+ * one star of n samples over n_periods periods under the current launch config. */
+int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes);
 
 /* ------------------------------------------------------------------ fold
  * Phase fold (Sec. 2.3: modular residual of each timestamp by the trial period, map to
@@ -279,6 +313,41 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
                 const double *periods, int64_t n_periods, int32_t nbins, double t0,
                 int scorer, const void *scorer_params, float *score,
                 int64_t *best_index, float *best_score);
+
+/* ------------------------------------------------------------------ batched search
+ * gpfc_search over many stars of uneven length, each with its own period grid, in one
+ * sequence of persistent launches (the paper folds one light curve at a time, Sec. 2.3;
+ * batching stars is this library's addition). Stars and grids are given in CSR form,
+ * all arrays DEVICE pointers owned by the caller:
+ *   lc_offsets   [n_stars + 1] int64: star s has samples lc_offsets[s] .. lc_offsets[s+1]-1
+ *                of times [n_total] float64 and flux [n_total] float32;
+ *                lc_offsets[0] = 0, lc_offsets[n_stars] = n_total, 1..2^24 samples a star
+ *   grid_offsets [n_stars + 1] int64, likewise over periods [n_periods_total] float64:
+ *                star s is folded at periods grid_offsets[s] .. grid_offsets[s+1]-1 (>= 1)
+ *   t0s          [n_stars] float64 phase origins, or NULL (NaN / NULL: the star's first time)
+ *   score        [n_periods_total] float32: the score of every (star, period), in the
+ *                order of `periods`
+ *   best_index   [n_stars] int64 (may be NULL): argmax of the star's scores as an index
+ *                into ITS grid (0 .. grid length - 1), ties to the smallest, -1 if none
+ *   best_score   [n_stars] float32 (may be NULL)
+ * scorer / scorer_params as for gpfc_search. Every score equals the one gpfc_search gives
+ * for that star alone (bit for bit).
+ * The offsets are validated on the device (no host synchronisation): a violation is
+ * latched and returned as GPFC_EINVAL by the next call or gpfc_sync, and the kernels then
+ * run on clamped offsets, staying inside the arrays.
+ * The launch sequence is captured into a CUDA graph on a private stream and replayed on
+ * the context's stream when an identical call (same pointers, sizes, parameters and
+ * workspace) follows; gpfc_set_graph(ctx, 0) enqueues the kernels directly instead. When
+ * the context's stream is itself capturing, the kernels are enqueued into that capture,
+ * provided the workspace is already large enough (make one identical call first).
+ * The timed region of gpfc_set_timing covers the whole sequence. */
+int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offsets,
+                        const double *times, const float *flux, int64_t n_total,
+                        const int64_t *grid_offsets, const double *periods,
+                        int64_t n_periods_total, const double *t0s, int32_t nbins, int scorer,
+                        const void *scorer_params, float *score, int64_t *best_index,
+                        float *best_score);
+int gpfc_set_graph(gpfc_ctx *ctx, int enable);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc",
+    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -38,7 +38,11 @@ class GpfcError(RuntimeError):
 
 
 class FoldConfig(ctypes.Structure):
-    _fields_ = [("warps", ctypes.c_int32), ("layout", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+    _fields_ = [("warps", ctypes.c_int32), ("layout", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 LAYOUT_PAIRED16 = 1
@@ -106,6 +110,15 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_cnn_logits.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(CnnWeights), _vp]
         L.gpfc_search.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.gpfc_search_batched.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
+                                          ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.gpfc_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_set_autotune.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int, _vp, ctypes.POINTER(FoldConfig)]
+        L.gpfc_last_fold_plan.argtypes = [_vp, ctypes.POINTER(FoldConfig)]
+        L.gpfc_workspace_size.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_size_t)]
         _lib = L
         return L
 
@@ -168,10 +181,29 @@ class Context:
     def sync(self):
         self._check(self.lib.gpfc_sync(self.handle))
 
-    def set_fold_config(self, warps=0, layout=0, chunk=0):
+    def set_fold_config(self, warps=0, layout=0, chunk=0, tile=0, blocks_per_sm=0):
         """Fold launch configuration; 0 means automatic for each field."""
-        cfg = FoldConfig(int(warps), int(layout), int(chunk))
+        cfg = FoldConfig(int(warps), int(layout), int(chunk), int(tile), int(blocks_per_sm))
         self._check(self.lib.gpfc_set_fold_config(self.handle, ctypes.byref(cfg)))
+
+    def last_fold_plan(self) -> dict:
+        """Launch config of the most recent fold plan (warps, layout, chunk, tile, blocks_per_sm)."""
+        cfg = FoldConfig()
+        self._check(self.lib.gpfc_last_fold_plan(self.handle, ctypes.byref(cfg)))
+        return cfg.as_dict()
+
+    def set_autotune(self, enable: int = 1):
+        """1: use and make tuned fold configs; 0: do not; -1: off and forget the tuned configs."""
+        self._check(self.lib.gpfc_set_autotune(self.handle, int(enable)))
+
+    def set_graph(self, enable: bool):
+        """Capture gpfc_search_batched into a CUDA graph and replay it (default on)."""
+        self._check(self.lib.gpfc_set_graph(self.handle, int(bool(enable))))
+
+    def workspace_size(self, n: int, n_periods: int, nbins: int) -> int:
+        v = ctypes.c_size_t()
+        self._check(self.lib.gpfc_workspace_size(self.handle, int(n), int(n_periods), int(nbins), ctypes.byref(v)))
+        return int(v.value)
 
     def reset_fold_config(self):
         self._check(self.lib.gpfc_set_fold_config(self.handle, None))
@@ -339,6 +371,72 @@ def gpfc_search(ctx: Context, times, flux, periods, nbins: int, t0: float = math
                                    float(t0), int(scorer), pp, _ptr(score), _ptr(best_index),
                                    _ptr(best_score)))
     return score, best_index, best_score
+
+
+def _scorer_params(ctx, scorer, nbins, w_min, w_max, sigma, weights):
+    if scorer == SCORER_BOX:
+        if w_max is None:
+            w_max = int(math.ceil(0.125 * nbins))
+        params = BoxParams(int(w_min), int(w_max), float(sigma))
+    elif scorer == SCORER_CNN:
+        if weights is None:
+            raise ValueError("the CNN scorer needs weights")
+        params = _cnn_weights(ctx, weights)
+    else:
+        raise GpfcError(-6, f"unknown scorer {scorer}")
+    return params, ctypes.cast(ctypes.pointer(params), _vp)
+
+
+def gpfc_search_batched(ctx: Context, lc_offsets, times, flux, grid_offsets, periods, nbins: int = 256, t0s=None,
+                        scorer: int = SCORER_BOX, w_min: int = 1, w_max: int | None = None, sigma: float = 0.0,
+                        weights=None, score=None, best_index=None, best_score=None):
+    """Fold + score many stars in one launch sequence (CSR offsets, all on the device).
+
+    lc_offsets [S+1] int64 into times f64 / flux f32; grid_offsets [S+1] int64 into periods
+    f64; t0s [S] f64 or None. Returns (score [sum of grid lengths] f32, best_index [S] int64
+    as an index into each star's own grid, best_score [S] f32).
+    """
+    dev = ctx.device
+    S = lc_offsets.numel() - 1
+    if S < 1:
+        raise ValueError("lc_offsets needs at least two entries")
+    _need(lc_offsets, torch.int64, dev, "lc_offsets")
+    _need(grid_offsets, torch.int64, dev, "grid_offsets", S + 1)
+    n, npd = times.numel(), periods.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    _need(periods, torch.float64, dev, "periods")
+    if t0s is not None:
+        _need(t0s, torch.float64, dev, "t0s", S)
+    if score is None:
+        score = torch.empty(npd, dtype=torch.float32, device=dev)
+    if best_index is None:
+        best_index = torch.empty(S, dtype=torch.int64, device=dev)
+    if best_score is None:
+        best_score = torch.empty(S, dtype=torch.float32, device=dev)
+    params, pp = _scorer_params(ctx, scorer, nbins, w_min, w_max, sigma, weights)
+    ctx._check(ctx.lib.gpfc_search_batched(ctx.handle, S, _ptr(lc_offsets), _ptr(times), _ptr(flux), n,
+                                           _ptr(grid_offsets), _ptr(periods), npd, _ptr(t0s), int(nbins),
+                                           int(scorer), pp, _ptr(score), _ptr(best_index), _ptr(best_score)))
+    return score, best_index, best_score
+
+
+def gpfc_autotune(ctx: Context, times, flux, periods, nbins: int, scorer: int = SCORER_BOX, w_min: int = 1,
+                  w_max: int | None = None, sigma: float = 0.0) -> dict:
+    """Time the fold's launch configs on this star and keep the fastest in the context."""
+    dev = ctx.device
+    n = times.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    _need(periods, torch.float64, dev, "periods")
+    if scorer == SCORER_BOX:
+        params, pp = _scorer_params(ctx, scorer, nbins, w_min, w_max, sigma, None)
+    else:
+        params, pp = None, None
+    out = FoldConfig()
+    ctx._check(ctx.lib.gpfc_autotune(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), periods.numel(),
+                                     int(nbins), int(scorer), pp, ctypes.byref(out)))
+    return out.as_dict()
 
 
 # ---------------------------------------------------------------- training

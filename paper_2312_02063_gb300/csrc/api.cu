@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gpfc.h"
 #include "gpfc_cnn.h"
@@ -25,7 +26,21 @@ struct gpfc_ctx {
     size_t ws_bytes = 0;
     uint32_t *status_host = nullptr;  // mapped pinned memory
     uint32_t *status_dev = nullptr;
-    gpfc_fold_config fold_cfg{0, 0, 0};
+    gpfc_fold_config fold_cfg{0, 0, 0, 0, 0};
+    // autotuner: tuned fold configs by (nbins, mode, floor(log2 n))
+    struct Tuned {
+        int nbins, mode, lg;
+        gpfc_fold_config cfg;
+        float ms;
+    };
+    std::vector<Tuned> tuned;
+    bool autotune = true;
+    // CUDA graph of the last batched search, replayed when the same call comes again
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint8_t> graph_key;
+    gpfc_fold_config last_plan{0, 0, 0, 0, 0};
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
@@ -80,6 +95,10 @@ int take_latched(gpfc_ctx *ctx)
     if (!bits) return GPFC_OK;
     *w = 0u;
     if (bits & kErrTimeout) return set_err(ctx, GPFC_ETIMEOUT, "a device-side wait timed out");
+    if (bits & kErrArgs)
+        return set_err(ctx, GPFC_EINVAL,
+                       "batched search: offsets are not a partition starting at 0 and ending at the totals, "
+                       "or a star has no samples, more than 2^24 samples or no periods");
     return set_err(ctx, GPFC_ERANGE,
                    "a period is not finite and > 0, or a time/frequency overflows the 64-bit fixed point");
 }
@@ -118,7 +137,7 @@ int ensure_ws(gpfc_ctx *ctx, size_t bytes)
 }
 
 struct FoldPlan {
-    int warps, ppc, grid, G, layout, chunk;
+    int warps, ppc, grid, G, layout, chunk, tile, bps;
     int64_t ntasks;
 };
 
@@ -128,13 +147,38 @@ int default_layout(int nbins)
     return kLayoutPaired16;
 }
 
-FoldPlan plan_fold(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins)
+int floor_log2(int64_t n)
+{
+    int l = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++l;
+    }
+    return l;
+}
+
+// The tuned config for (nbins, mode, n), if the autotuner has one.
+const gpfc_fold_config *find_tuned(const gpfc_ctx *ctx, int nbins, int mode, int64_t n)
+{
+    if (!ctx->autotune) return nullptr;
+    const int lg = floor_log2(n);
+    for (const auto &t : ctx->tuned)
+        if (t.nbins == nbins && t.mode == mode && t.lg == lg) return &t.cfg;
+    return nullptr;
+}
+
+// Launch plan of a fold over np periods of stars of about n samples. Fields of the
+// context's fold config that are set win; the rest come from `tuned` (if given) or the
+// defaults: 1024-sample tiles, the paired 16-bit count layout, the widest block that
+// still leaves one block per SM when the grid is short.
+FoldPlan plan_with(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const gpfc_fold_config &cfg)
 {
     FoldPlan pl{};
-    const gpfc_fold_config &cfg = ctx->fold_cfg;
+    pl.tile = cfg.tile ? cfg.tile : kTile;
     pl.layout = cfg.layout ? cfg.layout : default_layout(nbins);
-    if (fold_max_warps(nbins, pl.layout) < 1) pl.layout = kLayoutPaired16;
-    const int maxw = fold_max_warps(nbins, pl.layout);
+    if (fold_max_warps(nbins, pl.layout, pl.tile) < 1) pl.layout = kLayoutPaired16;
+    if (fold_max_warps(nbins, pl.layout, pl.tile) < 1) pl.tile = 512;
+    const int maxw = fold_max_warps(nbins, pl.layout, pl.tile);
     // enough blocks to cover the SMs when the grid is short, else the widest block
     int64_t per_sm = (np + (int64_t)32 * ctx->num_sms - 1) / ((int64_t)32 * ctx->num_sms);
     int w = (int)std::min<int64_t>(maxw, std::max<int64_t>(1, per_sm));
@@ -146,8 +190,24 @@ FoldPlan plan_fold(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins)
     pl.warps = w;
     pl.ppc = 32 * w;
     pl.ntasks = (np + pl.ppc - 1) / pl.ppc;
-    pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms);
+    const int occ = std::max(1, fold_blocks_per_sm(nbins, w, pl.layout, pl.tile));
+    pl.bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
+    pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms * pl.bps);
     pl.G = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 8191) / 8192));
+    return pl;
+}
+
+FoldPlan plan_fold(gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const gpfc_fold_config *tuned = nullptr)
+{
+    gpfc_fold_config cfg = ctx->fold_cfg;
+    if (tuned) {
+        if (!cfg.warps) cfg.warps = tuned->warps;
+        if (!cfg.layout) cfg.layout = tuned->layout;
+        if (!cfg.tile) cfg.tile = tuned->tile;
+        if (!cfg.blocks_per_sm) cfg.blocks_per_sm = tuned->blocks_per_sm;
+    }
+    const FoldPlan pl = plan_with(ctx, n, np, nbins, cfg);
+    ctx->last_plan = gpfc_fold_config{pl.warps, pl.layout, pl.chunk, pl.tile, pl.bps};
     return pl;
 }
 
@@ -204,7 +264,7 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
              int64_t np, int32_t nbins, double t0, int mode, FoldParams p, bool want_key,
              FoldBuffers *out_fb)
 {
-    const FoldPlan pl = plan_fold(ctx, n, np, nbins);
+    const FoldPlan pl = plan_fold(ctx, n, np, nbins, find_tuned(ctx, nbins, mode, n));
     FoldBuffers fb{};
     const size_t need = carve_fold(nullptr, pl, n, 1, nbins, fb);
     int rc = ensure_ws(ctx, need);
@@ -228,6 +288,7 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     p.warps = pl.warps;
     p.chunk = pl.chunk;
     p.layout = pl.layout;
+    p.tile = pl.tile;
     p.ws_sc = fb.ws_sc;
     p.ws_cnt = fb.ws_cnt;
     p.status = ctx->status_dev;
@@ -268,10 +329,10 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
                    int64_t np, int32_t nbins, double t0, const gpfc_cnn_weights *wt, float *score,
                    int64_t *best_index, float *best_score)
 {
-    const int64_t wave = (int64_t)ctx->num_sms * 128;
+    const FoldPlan pl = plan_fold(ctx, n, np, nbins, find_tuned(ctx, nbins, kModeFold, n));
+    const int64_t wave = (int64_t)pl.grid * pl.ppc;
     const int64_t chunk = std::min<int64_t>(np, wave);
     const int64_t half = (chunk + 1) / 2;
-    const FoldPlan pl = plan_fold(ctx, n, chunk, nbins);
     FoldBuffers fb{};
     Carver c(nullptr);
     c.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
@@ -311,6 +372,7 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
+        p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
         p.folded = cf;
@@ -348,6 +410,308 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         if (e == cudaSuccess) e = launch_argmax_finalize(key, 1, best_index, best_score, ctx->stream);
         if (e != cudaSuccess) return cuda_err(ctx, e, "argmax kernels");
     }
+    return GPFC_OK;
+}
+
+
+// ------------------------------------------------------------------ autotuner
+
+// Times the fold kernel of `mode` (kModeFold without output writes, or kModeBox) on one
+// star over its first periods, for every launch config whose resident periods per SM
+// are at least half the largest, and keeps the fastest under (nbins, mode, log2 n_key).
+int tune_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+              int64_t np, int nbins, int mode, const gpfc_box_params *bp, int64_t n_key, gpfc_fold_config *out)
+{
+    const int64_t P = std::min<int64_t>(np, (int64_t)4 * ctx->num_sms * 128);
+    struct Cand {
+        gpfc_fold_config cfg;
+        int resident;
+    };
+    std::vector<Cand> cands;
+    int best_res = 0;
+    for (int layout = 1; layout <= 2; ++layout) {
+        for (int tile = 512; tile <= kMaxTile; tile *= 2) {
+            const int maxw = fold_max_warps(nbins, layout, tile);
+            for (int w = 1; w <= maxw; ++w) {
+                const int bps = fold_blocks_per_sm(nbins, w, layout, tile);
+                if (bps < 1) continue;
+                const int res = 32 * w * bps;
+                cands.push_back(Cand{gpfc_fold_config{w, layout, 0, tile, bps}, res});
+                best_res = std::max(best_res, res);
+            }
+        }
+    }
+    if (cands.empty()) return set_err(ctx, GPFC_ENOTSUP, "no fold launch config fits nbins = %d", nbins);
+    // workspace: the largest carve of any candidate plus the sample score buffer
+    size_t need = 0;
+    for (const Cand &c : cands) {
+        if (2 * c.resident < best_res) continue;
+        FoldBuffers fb{};
+        need = std::max(need, carve_fold(nullptr, plan_with(ctx, n, P, nbins, c.cfg), n, 1, nbins, fb));
+    }
+    int rc = ensure_ws(ctx, need + (size_t)P * sizeof(float) + 512);
+    if (rc) return rc;
+    float *score = reinterpret_cast<float *>(static_cast<char *>(ctx->ws) + ((need + 255) & ~(size_t)255));
+    bool prepped = false;
+    float best_ms = 0.f;
+    gpfc_fold_config best{};
+    for (const Cand &c : cands) {
+        if (2 * c.resident < best_res) continue;
+        const FoldPlan pl = plan_with(ctx, n, P, nbins, c.cfg);
+        FoldBuffers fb{};
+        carve_fold(ctx->ws, pl, n, 1, nbins, fb);  // the sample scratch sits at the same place for all
+        cudaError_t e = cudaSuccess;
+        if (!prepped) {
+            e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, NAN, fb.smp, fb.partial, pl.G, fb.stats,
+                            ctx->status_dev, ctx->stream);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+            prepped = true;
+        }
+        FoldParams p{};
+        p.smp = fb.smp;
+        p.n = n;
+        p.periods = periods;
+        p.np = P;
+        p.ntasks = pl.ntasks;
+        p.nstars = 1;
+        p.stats = fb.stats;
+        p.nbins = nbins;
+        p.shift = shift_of(nbins);
+        p.warps = pl.warps;
+        p.chunk = pl.chunk;
+        p.layout = pl.layout;
+        p.tile = pl.tile;
+        p.ws_sc = fb.ws_sc;
+        p.ws_cnt = fb.ws_cnt;
+        p.status = ctx->status_dev;
+        if (mode == kModeBox) {
+            p.score = score;
+            p.w_min = bp->w_min;
+            p.w_max = bp->w_max;
+            p.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
+        }
+        e = launch_fold(p, mode, pl.grid, ctx->stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_start, ctx->stream);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_fold(p, mode, pl.grid, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_stop, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_stop);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev_start, ctx->ev_stop);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "autotune launch");
+        if ((rc = take_latched(ctx))) return rc;
+        ms *= 0.5f;
+        if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = gpfc_fold_config{pl.warps, pl.layout, 0, pl.tile, pl.bps};
+        }
+    }
+    ctx->timed = false;
+    const int lg = floor_log2(n_key);
+    bool found = false;
+    for (auto &t : ctx->tuned)
+        if (t.nbins == nbins && t.mode == mode && t.lg == lg) {
+            t.cfg = best;
+            t.ms = best_ms;
+            found = true;
+        }
+    if (!found) ctx->tuned.push_back(gpfc_ctx::Tuned{nbins, mode, lg, best, best_ms});
+    if (out) *out = best;
+    return GPFC_OK;
+}
+
+// ------------------------------------------------------------------ batched search
+
+struct BatchArgs {
+    int32_t S;
+    int32_t nbins;
+    int32_t scorer;
+    int32_t pad;
+    const int64_t *lc_off;
+    const double *times;
+    const float *flux;
+    int64_t n_total;
+    const int64_t *grid_off;
+    const double *periods;
+    int64_t np_total;
+    const double *t0s;
+    gpfc_box_params box;
+    gpfc_cnn_weights wt;
+    float *score;
+    int64_t *best_index;
+    float *best_score;
+};
+
+struct BatchBuffers {
+    int64_t *lc_s, *grid_s, *task_off;
+    FoldBuffers fb;
+    float *cf;
+    int32_t *cc;
+    int64_t *slot_k;
+    CnnDev dev;
+    uint8_t *h3t;
+};
+
+// Workspace of a batched search: validated offsets and task starts, the fold buffers of
+// all stars, and for the CNN one fold wave of profiles, their slot map, the CNN's weight
+// copies and fc1 operand tiles for half a wave.
+size_t carve_batched(void *base, const BatchArgs &A, const FoldPlan &pl, int64_t slots, BatchBuffers &B)
+{
+    Carver c(base);
+    B.lc_s = c.take<int64_t>(A.S + 1);
+    B.grid_s = c.take<int64_t>(A.S + 1);
+    B.task_off = c.take<int64_t>(A.S + 1);
+    FoldBuffers tmp{};
+    uint8_t *fold_base = c.take<uint8_t>(carve_fold(nullptr, pl, A.n_total, A.S, A.nbins, tmp));
+    carve_fold(fold_base, pl, A.n_total, A.S, A.nbins, B.fb);
+    if (A.scorer == GPFC_SCORER_CNN) {
+        const int64_t half = (slots + 1) / 2;
+        B.cf = c.take<float>((size_t)slots * A.nbins);
+        B.cc = c.take<int32_t>((size_t)slots * A.nbins);
+        B.slot_k = c.take<int64_t>(slots);
+        uint8_t *d = c.take<uint8_t>(cnn_dev_bytes());
+        B.dev = base ? cnn_dev_carve(d) : CnnDev{};
+        B.h3t = c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+    }
+    return c.off + 256;
+}
+
+// Upper bound of the total fold tasks: sum_s ceil(a_s / ppc) <= (sum_s a_s + S (ppc - 1)) / ppc.
+int64_t task_bound(const BatchArgs &A, int ppc) { return (A.np_total + (int64_t)A.S * (ppc - 1)) / ppc; }
+
+// All launches of a batched search on stream st (no host synchronisation, so the
+// sequence can be captured in a CUDA graph).
+cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &pl, const BatchBuffers &B,
+                            cudaStream_t st)
+{
+    const int64_t T = task_bound(A, pl.ppc);
+    cudaError_t e = launch_batch_plan(A.lc_off, A.grid_off, A.S, A.n_total, A.np_total, pl.ppc, B.lc_s, B.grid_s,
+                                      B.task_off, ctx->status_dev, st);
+    if (e == cudaSuccess)
+        e = launch_prep(A.times, A.flux, B.lc_s, A.n_total, A.S, 0, A.t0s, NAN, B.fb.smp, B.fb.partial, pl.G,
+                        B.fb.stats, ctx->status_dev, st);
+    if (e != cudaSuccess) return e;
+    FoldParams p{};
+    p.smp = B.fb.smp;
+    p.lc_off = B.lc_s;
+    p.n = A.n_total;
+    p.periods = A.periods;
+    p.grid_off = B.grid_s;
+    p.np = A.np_total;
+    p.task_off = B.task_off;
+    p.ntasks_dev = B.task_off + A.S;
+    p.nstars = A.S;
+    p.stats = B.fb.stats;
+    p.nbins = A.nbins;
+    p.shift = shift_of(A.nbins);
+    p.warps = pl.warps;
+    p.chunk = pl.chunk;
+    p.layout = pl.layout;
+    p.tile = pl.tile;
+    p.ws_sc = B.fb.ws_sc;
+    p.ws_cnt = B.fb.ws_cnt;
+    p.status = ctx->status_dev;
+    const bool want_best = A.best_index || A.best_score;
+    if (A.scorer == GPFC_SCORER_BOX) {
+        p.score = A.score;
+        p.w_min = A.box.w_min;
+        p.w_max = A.box.w_max;
+        p.sigma_user = A.box.sigma > 0.0 ? (float)A.box.sigma : 0.f;
+        if (want_best) {
+            p.best_key = B.fb.key;
+            e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long) * A.S, st);
+        }
+        p.task_begin = 0;
+        p.ntasks = T;
+        if (e == cudaSuccess) e = launch_fold(p, kModeBox, (int)std::min<int64_t>(T, pl.grid), st);
+        if (e == cudaSuccess && want_best) e = launch_argmax_finalize(B.fb.key, A.S, A.best_index, A.best_score, st);
+        return e;
+    }
+    e = launch_cnn_prep(cnn_src(&A.wt), B.dev, st);
+    const int64_t wave = (int64_t)pl.grid * 1;  // tasks per chunk: one per resident block
+    p.folded = B.cf;
+    p.counts = B.cc;
+    p.slot_k = B.slot_k;
+    for (int64_t tb = 0; tb < T && e == cudaSuccess; tb += wave) {
+        const int64_t te = std::min<int64_t>(T, tb + wave);
+        p.task_begin = tb;
+        p.ntasks = te;
+        e = launch_fold(p, kModeFold, (int)(te - tb), st);
+        const int64_t slots = (te - tb) * pl.ppc, half = (slots + 1) / 2;
+        for (int64_t h0 = 0; h0 < slots && e == cudaSuccess; h0 += half) {
+            const int64_t nh = std::min<int64_t>(half, slots - h0);
+            CnnConvParams cp{};
+            cp.folded = B.cf;
+            cp.counts = B.cc;
+            cp.k_begin = h0;
+            cp.np = nh;
+            cp.w = B.dev;
+            cp.h3t = B.h3t;
+            cp.status = ctx->status_dev;
+            e = launch_cnn_conv(cp, ctx->num_sms, st);
+            if (e != cudaSuccess) break;
+            CnnFcParams fp{};
+            fp.h3t = B.h3t;
+            fp.k_begin = h0;
+            fp.np = nh;
+            fp.w = B.dev;
+            fp.score = A.score;
+            fp.slot_k = B.slot_k;
+            fp.status = ctx->status_dev;
+            e = launch_cnn_fc(fp, ctx->num_sms, st);
+        }
+    }
+    if (e == cudaSuccess && want_best) {
+        e = launch_argmax_segmented(A.score, B.grid_s, A.S, B.fb.key, ctx->num_sms, st);
+        if (e == cudaSuccess) e = launch_argmax_finalize(B.fb.key, A.S, A.best_index, A.best_score, st);
+    }
+    return e;
+}
+
+void drop_graph(gpfc_ctx *ctx)
+{
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_key.clear();
+}
+
+// Capture the batched search into a CUDA graph on the context's private capture stream
+// (or reuse the graph of an identical earlier call) and launch it on the context's stream.
+int launch_batched_graph(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &pl, const BatchBuffers &B)
+{
+    std::vector<uint8_t> key(sizeof(BatchArgs) + sizeof(FoldPlan) + 2 * sizeof(size_t));
+    memcpy(key.data(), &A, sizeof(BatchArgs));
+    memcpy(key.data() + sizeof(BatchArgs), &pl, sizeof(FoldPlan));
+    const size_t wsinfo[2] = {reinterpret_cast<size_t>(ctx->ws), ctx->ws_bytes};
+    memcpy(key.data() + sizeof(BatchArgs) + sizeof(FoldPlan), wsinfo, sizeof(wsinfo));
+    cudaError_t e = cudaSuccess;
+    if (!ctx->graph_exec || key != ctx->graph_key) {
+        drop_graph(ctx);
+        if (!ctx->cap_stream) {
+            e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamCreateWithFlags");
+        }
+        e = cnn_register_kernels();  // attribute calls stay outside the capture
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFuncSetAttribute");
+        e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamBeginCapture");
+        const cudaError_t eq = enqueue_batched(ctx, A, pl, B, ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (eq != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_err(ctx, eq != cudaSuccess ? eq : e, "capture of the batched search");
+        }
+        e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->graph_exec = nullptr;
+            return cuda_err(ctx, e, "cudaGraphInstantiate");
+        }
+        ctx->graph_key = key;
+    }
+    e = cudaGraphLaunch(ctx->graph_exec, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGraphLaunch");
     return GPFC_OK;
 }
 
@@ -410,6 +774,8 @@ void gpfc_destroy(gpfc_ctx *ctx)
     if (ctx->status_host) cudaFreeHost(ctx->status_host);
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -417,11 +783,12 @@ int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg)
 {
     if (!ctx) return GPFC_EINVAL;
     if (!cfg) {
-        ctx->fold_cfg = gpfc_fold_config{0, 0, 0};
+        ctx->fold_cfg = gpfc_fold_config{0, 0, 0, 0, 0};
         return GPFC_OK;
     }
     if (cfg->warps < 0 || cfg->warps > kMaxFoldWarps || cfg->layout < 0 || cfg->layout > 2 ||
-        cfg->chunk < 0 || cfg->chunk > 65520)
+        cfg->chunk < 0 || cfg->chunk > 65520 || (cfg->tile != 0 && cfg->tile != 512 && cfg->tile != 1024 &&
+                                                   cfg->tile != 2048) || cfg->blocks_per_sm < 0)
         return set_err(ctx, GPFC_EINVAL, "fold config out of range");
     ctx->fold_cfg = *cfg;
     return GPFC_OK;
@@ -431,6 +798,67 @@ int gpfc_fold_max_warps(int32_t nbins, int32_t layout)
 {
     if (nbins < 2 || nbins > kMaxNbinsLane || layout < 1 || layout > 2) return 0;
     return fold_max_warps(nbins, layout);
+}
+
+int gpfc_last_fold_plan(const gpfc_ctx *ctx, gpfc_fold_config *out)
+{
+    if (!ctx || !out) return GPFC_EINVAL;
+    *out = ctx->last_plan;
+    return GPFC_OK;
+}
+
+int gpfc_set_autotune(gpfc_ctx *ctx, int enable)
+{
+    if (!ctx) return GPFC_EINVAL;
+    ctx->autotune = enable != 0;
+    if (enable < 0) ctx->tuned.clear();
+    return GPFC_OK;
+}
+
+int gpfc_set_graph(gpfc_ctx *ctx, int enable)
+{
+    if (!ctx) return GPFC_EINVAL;
+    ctx->use_graph = enable != 0;
+    if (!ctx->use_graph) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamSynchronize");
+        drop_graph(ctx);
+    }
+    return GPFC_OK;
+}
+
+int gpfc_autotune(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                  int64_t n_periods, int32_t nbins, int scorer, const void *scorer_params, gpfc_fold_config *out)
+{
+    int rc = check_fold_args(ctx, times, flux, n, periods, n_periods, nbins);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    if ((rc = take_latched(ctx))) return rc;
+    const gpfc_box_params *bp = nullptr;
+    if (scorer == GPFC_SCORER_BOX) {
+        bp = static_cast<const gpfc_box_params *>(scorer_params);
+        if (!bp || bp->w_min < 1 || bp->w_max < bp->w_min || bp->w_max > nbins)
+            return set_err(ctx, GPFC_EINVAL, "box scorer needs gpfc_box_params with 1 <= w_min <= w_max <= nbins");
+    } else if (scorer != GPFC_SCORER_CNN) {
+        return set_err(ctx, GPFC_ENOTSUP, "scorer %d not available", scorer);
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return set_err(ctx, GPFC_EINVAL, "autotune cannot run under stream capture");
+    return tune_fold(ctx, times, flux, n, periods, n_periods, nbins, scorer == GPFC_SCORER_BOX ? kModeBox : kModeFold,
+                     bp, n, out);
+}
+
+int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes)
+{
+    if (!ctx || !bytes) return GPFC_EINVAL;
+    if (n < 1 || n_periods < 1 || nbins < 2 || nbins > kMaxNbinsLane)
+        return set_err(ctx, GPFC_EINVAL, "bad sizes");
+    const FoldPlan pl = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
+    FoldBuffers fb{};
+    *bytes = carve_fold(nullptr, pl, n, 1, nbins, fb);
+    return GPFC_OK;
 }
 
 int gpfc_set_timing(gpfc_ctx *ctx, int enable)
@@ -757,6 +1185,95 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
         return run_search_cnn(ctx, times, flux, n, periods, n_periods, nbins, t0, wt, score, best_index, best_score);
     }
     return set_err(ctx, GPFC_ENOTSUP, "scorer %d not available", scorer);
+}
+
+int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offsets, const double *times,
+                        const float *flux, int64_t n_total, const int64_t *grid_offsets, const double *periods,
+                        int64_t n_periods_total, const double *t0s, int32_t nbins, int scorer,
+                        const void *scorer_params, float *score, int64_t *best_index, float *best_score)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!lc_offsets || !times || !flux || !grid_offsets || !periods || !score)
+        return set_err(ctx, GPFC_EINVAL, "NULL input or output array");
+    if (n_stars < 1 || n_stars > (1 << 24)) return set_err(ctx, GPFC_EINVAL, "n_stars = %d outside [1, 2^24]", n_stars);
+    if (n_total < n_stars || n_total > ((int64_t)1 << 40))
+        return set_err(ctx, GPFC_EINVAL, "n_total = %lld outside [n_stars, 2^40]", (long long)n_total);
+    if (n_periods_total < n_stars || n_periods_total > ((int64_t)1 << 40))
+        return set_err(ctx, GPFC_EINVAL, "n_periods_total = %lld outside [n_stars, 2^40]", (long long)n_periods_total);
+    if (nbins < 2) return set_err(ctx, GPFC_EINVAL, "nbins = %d < 2", nbins);
+    if (nbins > kMaxNbinsLane || fold_max_warps(nbins, kLayoutPaired16) < 1)
+        return set_err(ctx, GPFC_ENOTSUP, "nbins = %d > %d", nbins, kMaxNbinsLane);
+    BatchArgs A;
+    memset(&A, 0, sizeof(A));  // the graph cache compares the bytes, padding included
+    A.S = n_stars;
+    A.nbins = nbins;
+    A.scorer = scorer;
+    A.lc_off = lc_offsets;
+    A.times = times;
+    A.flux = flux;
+    A.n_total = n_total;
+    A.grid_off = grid_offsets;
+    A.periods = periods;
+    A.np_total = n_periods_total;
+    A.t0s = t0s;
+    A.score = score;
+    A.best_index = best_index;
+    A.best_score = best_score;
+    int mode = kModeFold;
+    if (scorer == GPFC_SCORER_BOX) {
+        const auto *bp = static_cast<const gpfc_box_params *>(scorer_params);
+        if (!bp) return set_err(ctx, GPFC_EINVAL, "box scorer needs gpfc_box_params");
+        if (bp->w_min < 1 || bp->w_max < bp->w_min || bp->w_max > nbins)
+            return set_err(ctx, GPFC_EINVAL, "box widths must satisfy 1 <= w_min <= w_max <= nbins");
+        A.box = *bp;
+        mode = kModeBox;
+    } else if (scorer == GPFC_SCORER_CNN) {
+        const auto *wt = static_cast<const gpfc_cnn_weights *>(scorer_params);
+        if (!cnn_weights_ok(wt)) return set_err(ctx, GPFC_EINVAL, "CNN scorer needs gpfc_cnn_weights");
+        if (nbins != 256) return set_err(ctx, GPFC_ENOTSUP, "the CNN scorer takes 256 bins, got %d", nbins);
+        A.wt = *wt;
+    } else {
+        return set_err(ctx, GPFC_ENOTSUP, "scorer %d not available", scorer);
+    }
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamIsCapturing");
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    const int64_t n_avg = n_total / n_stars;
+    const gpfc_fold_config *tuned = find_tuned(ctx, nbins, mode, n_avg);
+    if (!tuned && ctx->autotune && !capturing) {
+        // tune on the first star (its offsets are read back once)
+        int64_t off[2] = {0, 0};
+        e = cudaMemcpyAsync(off, lc_offsets, sizeof(off), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "reading the first star's offsets");
+        const int64_t n0 = off[1] - off[0];
+        if (off[0] >= 0 && n0 >= 1 && n0 <= ((int64_t)1 << 24) && off[1] <= n_total) {
+            rc = tune_fold(ctx, times + off[0], flux + off[0], n0, periods, n_periods_total, nbins, mode, &A.box,
+                           n_avg, nullptr);
+            if (rc) return rc;
+            tuned = find_tuned(ctx, nbins, mode, n_avg);
+        }
+    }
+    const FoldPlan pl = plan_fold(ctx, n_avg, n_periods_total, nbins, tuned);
+    BatchBuffers B{};
+    const int64_t slots = (int64_t)pl.grid * pl.ppc;
+    rc = ensure_ws(ctx, carve_batched(nullptr, A, pl, slots, B));
+    if (rc) return rc;
+    carve_batched(ctx->ws, A, pl, slots, B);
+    KernelTimer timer(ctx);
+    if (ctx->use_graph && !capturing) {
+        rc = launch_batched_graph(ctx, A, pl, B);
+        if (rc) return rc;
+    } else {
+        e = enqueue_batched(ctx, A, pl, B, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "batched search launches");
+    }
+    timer.stop();
+    return GPFC_OK;
 }
 
 }  // extern "C"

@@ -519,8 +519,11 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
             }
             if (kl < p.np) {
                 const float zz = dot + b2;
-                if (p.logit) p.logit[p.k_begin + kl] = zz;
-                if (p.score) p.score[p.k_begin + kl] = 1.f / (1.f + expf(-zz));
+                const int64_t o = p.slot_k ? p.slot_k[p.k_begin + kl] : p.k_begin + kl;
+                if (o >= 0) {
+                    if (p.logit) p.logit[o] = zz;
+                    if (p.score) p.score[o] = 1.f / (1.f + expf(-zz));
+                }
             }
         }
         tc_fence_before();

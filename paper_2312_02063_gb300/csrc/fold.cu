@@ -119,7 +119,7 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
     __syncthreads();
     const double f_ref = s_fref;
     double t0 = t0s ? t0s[s] : t0_scalar;
-    if (t0 != t0) t0 = times[b];
+    if (t0 != t0) t0 = len > 0 ? times[b] : 0.0;
     const int64_t base = scratch_start(b, s);
     const int64_t per = (len + G - 1) / G;
     const int64_t j0 = (int64_t)blockIdx.x * per;
@@ -719,19 +719,20 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     const int warp = threadIdx.x >> 5;
     const int nbins = p.nbins;
     const int ppc = 32 * p.warps;
+    const int tile = p.tile;
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     uint32_t *tl_buf = reinterpret_cast<uint32_t *>(smem + 128);
-    uint32_t *th_buf = tl_buf + 2 * kTile;
-    float *x_buf = reinterpret_cast<float *>(th_buf + 2 * kTile);
-    uint8_t *f_buf = reinterpret_cast<uint8_t *>(x_buf + 2 * kTile);  // [2][kTile / 16]
+    uint32_t *th_buf = tl_buf + 2 * tile;
+    float *x_buf = reinterpret_cast<float *>(th_buf + 2 * tile);
+    uint8_t *f_buf = reinterpret_cast<uint8_t *>(x_buf + 2 * tile);  // [2][tile / 16]
     using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64, StorePaired16>::type;
     St st;
     if constexpr (LAYOUT == kLayoutPacked64) {
-        uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (kTile / 16));
+        uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (tile / 16));
         st.v = v + (size_t)warp * nbins * 32 + lane;
     } else {
-        float *acc = reinterpret_cast<float *>(f_buf + 2 * (kTile / 16));
+        float *acc = reinterpret_cast<float *>(f_buf + 2 * (tile / 16));
         const int nb2 = (nbins + 1) & ~1;
         uint16_t *cnt = reinterpret_cast<uint16_t *>(acc + (size_t)p.warps * nbins * 32);
         st.acc = acc + (size_t)warp * nbins * 32 + lane;
@@ -749,7 +750,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     float2 *wsc_cta = p.ws_sc + (size_t)blockIdx.x * nbins * ppc + warp * 32 + lane;
     uint32_t *wcn_cta = p.ws_cnt + (size_t)blockIdx.x * nbins * ppc + warp * 32 + lane;
 
-    for (int64_t task = blockIdx.x; task < p.ntasks; task += gridDim.x) {
+    int64_t task_end = p.ntasks;
+    if (p.ntasks_dev) {
+        const int64_t t = *p.ntasks_dev;
+        task_end = t < task_end ? t : task_end;
+    }
+    for (int64_t task = p.task_begin + blockIdx.x; task < task_end; task += gridDim.x) {
         // resolve the star of this task and its period block
         int s = 0;
         int64_t tbase = 0;
@@ -766,7 +772,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         int64_t lb, le, gb, ge;
         star_range(p.lc_off, p.n, s, lb, le);
         star_range(p.grid_off, p.np, s, gb, ge);
-        const int64_t nsamp = le - lb;
+        // (more than 2^24 samples happens only for offsets the batch plan rejected)
+        const int64_t nsamp = min(le - lb, (int64_t)1 << 24);
         const int64_t sbase = scratch_start(lb, s);
         const int64_t k = gb + (task - tbase) * ppc + warp * 32 + lane;
         const bool kvalid = k < ge;
@@ -786,17 +793,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             }
         }
         for (int b = 0; b < nbins; ++b) st.put((uint32_t)b, 0.f, 0u);
-        const int ntiles = (int)((nsamp + kTile - 1) / kTile);
+        const int ntiles = (int)((nsamp + tile - 1) / tile);
         auto issue = [&](int t, int buf) {
-            const int64_t i0 = (int64_t)t * kTile;
-            const int nv = (int)min((int64_t)kTile, nsamp - i0);
+            const int64_t i0 = (int64_t)t * tile;
+            const int nv = (int)min((int64_t)tile, nsamp - i0);
             const uint32_t bytes = (uint32_t)(((nv + 3) & ~3) * 4);
             const uint32_t fbytes = (uint32_t)((((nv + 15) >> 4) + 15) & ~15);
             mbar_arrive_expect_tx(&bars[buf], 3u * bytes + fbytes);
-            bulk_g2s(tl_buf + buf * kTile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(th_buf + buf * kTile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(x_buf + buf * kTile, p.smp.x + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(f_buf + buf * (kTile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
+            bulk_g2s(tl_buf + buf * tile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
+            bulk_g2s(th_buf + buf * tile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
+            bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
+            bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
         __syncthreads();  // previous task's readers are done with both buffers
         if (threadIdx.x == 0) {
@@ -814,39 +821,46 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 s_abort = 1;
                 report_error(p.status, kErrTimeout);
             } else {
-                const int nv = (int)min((int64_t)kTile, nsamp - (int64_t)t * kTile);
-                const uint32_t *stl = tl_buf + buf * kTile;
-                const uint32_t *sth = th_buf + buf * kTile;
-                const float *sx = x_buf + buf * kTile;
-                // the tile's 64 regular-group flag bytes, packed into a register bit mask
-                unsigned long long fmask = 0ull;
-                {
-                    const uint4 *fw = reinterpret_cast<const uint4 *>(f_buf + buf * (kTile / 16));
+                const int nv = (int)min((int64_t)tile, nsamp - (int64_t)t * tile);
+                // the tile in sub-tiles of up to 1024 samples, each with its 64 regular-group
+                // flag bytes packed into a register bit mask
+                for (int sub = 0; sub < nv; sub += 1024) {
+                    const int nvs = min(1024, nv - sub);
+                    const uint32_t *stl = tl_buf + buf * tile + sub;
+                    const uint32_t *sth = th_buf + buf * tile + sub;
+                    const float *sx = x_buf + buf * tile + sub;
+                    unsigned long long fmask = 0ull;
+                    {
+                        const uint4 *fw = reinterpret_cast<const uint4 *>(f_buf + buf * (tile / 16) + sub / 16);
+                        const int nq = (nvs + 255) >> 8;  // 16-byte words holding the sub-tile's flags
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 w = fw[q];
-                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                        for (int q = 0; q < 4; ++q) {
+                            if (q < nq) {
+                                const uint4 w = fw[q];
+                                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            // bytes (0 or 1) j = 0..3 of a word -> bits j of a nibble
-                            const unsigned long long nib = ((ww[r] * 0x01020408u) >> 24) & 0xFu;
-                            fmask |= nib << (16 * q + 4 * r);
+                                for (int r = 0; r < 4; ++r) {
+                                    // bytes (0 or 1) j = 0..3 of a word -> bits j of a nibble
+                                    const unsigned long long nib = ((ww[r] * 0x01020408u) >> 24) & 0xFu;
+                                    fmask |= nib << (16 * q + 4 * r);
+                                }
+                            }
                         }
                     }
-                }
-                int i = 0;
-                while (i < nv) {
-                    // segments end at chunk boundaries (multiples of 4 samples) or the tile end
-                    const int seg = min(nv - i, chunk_left);
-                    fold_segment<POW2, St>(stl + i, sth + i, sx + i, fmask >> (i >> 4), seg, st, Fl, Fh,
-                                           (uint32_t)nbins, p.shift, safe);
-                    i += seg;
-                    chunk_left -= seg;
-                    const bool last = (t == ntiles - 1) && (i == nv);
-                    if (chunk_left == 0 || last) {
-                        over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
-                        first_flush = false;
-                        chunk_left = p.chunk;
+                    int i = 0;
+                    while (i < nvs) {
+                        // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
+                        const int seg = min(nvs - i, chunk_left);
+                        fold_segment<POW2, St>(stl + i, sth + i, sx + i, fmask >> (i >> 4), seg, st, Fl, Fh,
+                                               (uint32_t)nbins, p.shift, safe);
+                        i += seg;
+                        chunk_left -= seg;
+                        const bool last = (t == ntiles - 1) && (sub + i == nv);
+                        if (chunk_left == 0 || last) {
+                            over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
+                            first_flush = false;
+                            chunk_left = p.chunk;
+                        }
                     }
                 }
             }
@@ -857,14 +871,18 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
 
         // ---------------- epilogues (lane-private, no block barrier needed)
         if (MODE == kModeFold) {
-            if (kvalid) {
+            // output row: the period, or the lane's chunk slot
+            const int64_t row = p.slot_k ? (task - p.task_begin) * ppc + warp * 32 + lane : k;
+            if (p.slot_k) p.slot_k[row] = kvalid ? k : -1;
+            if (kvalid || p.slot_k) {
                 const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
                 for (int b = 0; b < nbins; ++b) {
-                    const uint32_t c = over ? wcn_cta[(size_t)b * ppc] : st.count((uint32_t)b);
+                    uint32_t c = over ? wcn_cta[(size_t)b * ppc] : st.count((uint32_t)b);
+                    if (!kvalid) c = 0u;
                     const float S = st.sum((uint32_t)b);
                     const float mean = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
-                    if (p.folded) p.folded[(size_t)k * nbins + b] = mean;
-                    if (p.counts) p.counts[(size_t)k * nbins + b] = (int32_t)c;
+                    if (p.folded) p.folded[(size_t)row * nbins + b] = mean;
+                    if (p.counts) p.counts[(size_t)row * nbins + b] = (int32_t)c;
                 }
             }
         } else if (MODE == kModeBox) {
@@ -886,6 +904,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 if (lane == 0 && key) atomicMax(&p.best_key[s], key);
             }
         }
+    }
+    if (MODE == kModeFold && p.slot_k) {
+        // slots of tasks in this launch's range that lie past the device task count
+        const int64_t t0 = task_end > p.task_begin ? task_end : p.task_begin;
+        for (int64_t task = t0 + blockIdx.x; task < p.ntasks; task += gridDim.x)
+            p.slot_k[(task - p.task_begin) * ppc + threadIdx.x] = -1;
     }
 }
 
@@ -915,19 +939,44 @@ int fold_register_kernels()
     return (int)e;
 }
 
-size_t fold_smem_bytes(int nbins, int warps, int layout)
+size_t fold_smem_bytes(int nbins, int warps, int layout, int tile)
 {
     const size_t nb2 = (size_t)((nbins + 1) & ~1);
     const size_t per_warp = layout == kLayoutPacked64 ? (size_t)32 * nbins * 8
                                                       : (size_t)32 * (nbins * 4 + nb2 * 2);
-    return 128 + (size_t)2 * kTile * 12 + 2 * (kTile / 16) + (size_t)warps * per_warp;
+    return 128 + (size_t)2 * tile * 12 + 2 * (tile / 16) + (size_t)warps * per_warp;
 }
 
-int fold_max_warps(int nbins, int layout)
+int fold_max_warps(int nbins, int layout, int tile)
 {
     int w = kMaxFoldWarps;
-    while (w > 1 && fold_smem_bytes(nbins, w, layout) > kSmemLimit - 1024) --w;
-    return fold_smem_bytes(nbins, w, layout) <= kSmemLimit - 1024 ? w : 0;
+    while (w > 1 && fold_smem_bytes(nbins, w, layout, tile) > kSmemLimit - 1024) --w;
+    return fold_smem_bytes(nbins, w, layout, tile) <= kSmemLimit - 1024 ? w : 0;
+}
+
+// Resident blocks per SM of a fold launch (0 if it does not fit).
+template <int MODE, bool POW2, int LAYOUT, int MAXW>
+static int occupancy_of(int threads, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fold_kernel<MODE, POW2, LAYOUT, MAXW>, threads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int fold_blocks_per_sm(int nbins, int warps, int layout, int tile)
+{
+    const size_t smem = fold_smem_bytes(nbins, warps, layout, tile);
+    if (smem > kSmemLimit - 1024) return 0;
+    const int threads = 32 * warps;
+    if (layout == kLayoutPacked64)
+        return warps <= 4 ? occupancy_of<kModeFold, true, kLayoutPacked64, 4>(threads, smem)
+                          : occupancy_of<kModeFold, true, kLayoutPacked64, kMaxFoldWarps>(threads, smem);
+    return warps <= 4 ? occupancy_of<kModeFold, true, kLayoutPaired16, 4>(threads, smem)
+                      : occupancy_of<kModeFold, true, kLayoutPaired16, kMaxFoldWarps>(threads, smem);
 }
 
 // Blocks of up to 4 warps use the instantiation with a 255-register budget (the 16-sample
@@ -946,7 +995,9 @@ static void launch_variant(const FoldParams &p, int grid, int threads, size_t sm
 
 cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st)
 {
-    const size_t smem = fold_smem_bytes(p.nbins, p.warps, p.layout);
+    if (p.tile != 512 && p.tile != 1024 && p.tile != 2048) return cudaErrorInvalidValue;
+    const size_t smem = fold_smem_bytes(p.nbins, p.warps, p.layout, p.tile);
+    if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
     const int threads = 32 * p.warps;
     const bool pow2 = p.shift >= 0;
     if (mode == kModeFold) {
@@ -1103,6 +1154,127 @@ cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *ke
     int64_t g = want < (int64_t)sms * 4 ? want : (int64_t)sms * 4;
     const int grid = (int)(g < 1 ? 1 : g);
     argmax_kernel<<<grid, 256, 0, st>>>(score, np, key);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched search plan
+
+constexpr int kPlanThreads = 1024;
+
+// Inclusive block scan (Hillis-Steele) of one value per thread, with op = max or +.
+template <bool MAX>
+__device__ int64_t block_scan(int64_t v, int64_t *buf)
+{
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        const int64_t u = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : (MAX ? INT64_MIN : 0);
+        __syncthreads();
+        v = MAX ? (u > v ? u : v) : v + u;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+    }
+    return v;
+}
+
+// Monotone copy of the offsets off[0..S] clamped to [0, total], with 0 first and total
+// last: o'[i] = max(0, max_{j <= i} min(off[j], total)). Returns true if o' == off.
+__device__ bool sanitise_offsets(const int64_t *off, int S, int64_t total, int64_t *out, int64_t *buf)
+{
+    const int per = (S + 1 + kPlanThreads - 1) / kPlanThreads;
+    const int a = threadIdx.x * per, b = min(S + 1, a + per);
+    int64_t m = 0;
+    for (int i = a; i < b; ++i) {
+        const int64_t v = min(off[i], total);
+        m = v > m ? v : m;
+    }
+    const int64_t incl = block_scan<true>(m, buf);
+    int64_t run = threadIdx.x > 0 ? buf[threadIdx.x - 1] : 0;
+    run = run > 0 ? run : 0;
+    __syncthreads();
+    bool same = true;
+    for (int i = a; i < b; ++i) {
+        const int64_t v = min(off[i], total);
+        run = v > run ? v : run;
+        int64_t o = i == 0 ? 0 : run;
+        if (i == S) o = total;
+        same &= o == off[i];
+        out[i] = o;
+    }
+    (void)incl;
+    return __syncthreads_and(same);
+}
+
+// Validated star offsets and the first fold task of every star (ceil(grid length /
+// ppc) tasks each); task_off[S] is the total. One block of kPlanThreads threads.
+__global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const int64_t *lc_off, const int64_t *grid_off,
+                                                                   int S, int64_t n_total, int64_t np_total, int ppc,
+                                                                   int64_t *lc_s, int64_t *grid_s, int64_t *task_off,
+                                                                   uint32_t *status)
+{
+    __shared__ int64_t buf[kPlanThreads];
+    bool ok = sanitise_offsets(lc_off, S, n_total, lc_s, buf);
+    ok &= sanitise_offsets(grid_off, S, np_total, grid_s, buf);
+    __syncthreads();
+    const int per = (S + kPlanThreads - 1) / kPlanThreads;
+    const int a = threadIdx.x * per, b = min(S, a + per);
+    int64_t t = 0;
+    bool good = true;
+    for (int i = a; i < b; ++i) {
+        const int64_t len = lc_s[i + 1] - lc_s[i], np = grid_s[i + 1] - grid_s[i];
+        good &= len >= 1 && len <= ((int64_t)1 << 24) && np >= 1 && np <= (int64_t)INT32_MAX;
+        t += (np + ppc - 1) / ppc;
+    }
+    const int64_t incl = block_scan<false>(t, buf);
+    int64_t run = incl - t;
+    for (int i = a; i < b; ++i) {
+        task_off[i] = run;
+        run += (grid_s[i + 1] - grid_s[i] + ppc - 1) / ppc;
+    }
+    if (threadIdx.x == kPlanThreads - 1) task_off[S] = incl;
+    ok &= __syncthreads_and(good);
+    if (!ok && threadIdx.x == 0) report_error(status, kErrArgs);
+}
+
+cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, int nstars, int64_t n_total,
+                              int64_t np_total, int ppc, int64_t *lc_s, int64_t *grid_s, int64_t *task_off,
+                              uint32_t *status, cudaStream_t st)
+{
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(lc_off, grid_off, nstars, n_total, np_total, ppc, lc_s, grid_s,
+                                                  task_off, status);
+    return cudaGetLastError();
+}
+
+// Per-star argmax key over score[grid_off[s] .. grid_off[s+1]) with the star-local index;
+// one block per star at a time.
+__global__ void argmax_segmented_kernel(const float *__restrict__ score, const int64_t *grid_off, int S,
+                                        unsigned long long *key)
+{
+    __shared__ unsigned long long red[8];
+    for (int s = blockIdx.x; s < S; s += gridDim.x) {
+        const int64_t gb = grid_off[s], ge = grid_off[s + 1];
+        unsigned long long best = 0ull;
+        for (int64_t k = gb + threadIdx.x; k < ge; k += blockDim.x) {
+            const unsigned long long v = argmax_key(score[k], k - gb);
+            best = v > best ? v : best;
+        }
+        best = warp_max_u64(best);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0ull;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+            key[s] = m;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_argmax_segmented(const float *score, const int64_t *grid_off, int nstars,
+                                    unsigned long long *key, int num_sms, cudaStream_t st)
+{
+    const int grid = nstars < num_sms * 8 ? nstars : num_sms * 8;
+    argmax_segmented_kernel<<<grid, 256, 0, st>>>(score, grid_off, nstars, key);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ struct CnnFcParams {
     CnnDev w;
     float *score;            // [global] sigmoid(logit), or NULL
     float *logit;            // [global] or NULL
+    const int64_t *slot_k;   // NULL, or the output index of each profile (< 0: not written)
     float *z1save;           // [np][256] fc1 pre-activation (NULL at inference)
     uint32_t *status;
     int tiles_per_block;     // set by launch_cnn_fc: 128-profile tiles per block (1 or 2)

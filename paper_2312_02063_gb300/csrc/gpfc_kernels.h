@@ -11,9 +11,11 @@ namespace gpfc {
 enum : uint32_t {
     kErrRange = 1u,    // period not finite/positive, or tau / F outside the fixed point
     kErrTimeout = 2u,  // a bounded wait on an mbarrier gave up
+    kErrArgs = 4u,     // batched search: star or grid offsets not a valid partition
 };
 
-constexpr int kTile = 1024;            // light-curve samples per bulk-copy tile
+constexpr int kTile = 1024;            // default light-curve samples per bulk-copy tile
+constexpr int kMaxTile = 2048;         // tiles are 512, 1024 or 2048 samples
 constexpr int kMaxFoldWarps = 16;      // warps per fold block (32 periods each)
 constexpr int kMaxNbinsLane = 1024;    // largest nbins of the lane-private fold
 constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block (227 KB); kernels ask
@@ -50,7 +52,9 @@ struct FoldParams {
     const int64_t *grid_off;   // [S+1] period offsets, or NULL (one grid of np periods)
     int64_t np;
     const int64_t *task_off;   // [S+1] first fold task of each star, or NULL
-    int64_t ntasks;
+    int64_t ntasks;            // end of this launch's task range (host bound)
+    int64_t task_begin;        // first task of this launch
+    const int64_t *ntasks_dev; // device task count that also bounds the range, or NULL
     int nstars;
     const StarStats *stats;
     int nbins;
@@ -58,11 +62,14 @@ struct FoldParams {
     int warps;                 // warps per block; periods per block = 32 * warps
     int chunk;                 // samples per shared-memory chunk: multiple of 16, <= 65520
     int layout;                // FoldLayout
+    int tile;                  // samples per bulk-copy tile: 512, 1024 or 2048
     float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
-    // kModeFold outputs ([global period][nbins])
+    // kModeFold outputs ([global period][nbins], or [slot][nbins] when slot_k is set)
     float *folded;
     int32_t *counts;
+    int64_t *slot_k;           // chunk slots: slot (task - task_begin) * 32 * warps + lane of
+                               // the block gets period k, or -1 (then counts 0, means NaN)
     // kModeBox outputs
     float *score;              // [global period]
     int32_t *best_s;
@@ -75,8 +82,9 @@ struct FoldParams {
     uint32_t *status;
 };
 
-size_t fold_smem_bytes(int nbins, int warps, int layout);
-int fold_max_warps(int nbins, int layout);
+size_t fold_smem_bytes(int nbins, int warps, int layout, int tile = kTile);
+int fold_max_warps(int nbins, int layout, int tile = kTile);
+int fold_blocks_per_sm(int nbins, int warps, int layout, int tile);
 int fold_register_kernels();
 
 cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
@@ -87,12 +95,17 @@ cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, in
                                   int w_min, int w_max, float sigma, float *score, int32_t *best_s,
                                   int32_t *best_w, cudaStream_t st);
 cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *key, cudaStream_t st);
+cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, int nstars, int64_t n_total,
+                              int64_t np_total, int ppc, int64_t *lc_s, int64_t *grid_s, int64_t *task_off,
+                              uint32_t *status, cudaStream_t st);
+cudaError_t launch_argmax_segmented(const float *score, const int64_t *grid_off, int nstars,
+                                    unsigned long long *key, int num_sms, cudaStream_t st);
 cudaError_t launch_argmax_finalize(const unsigned long long *key, int nstars, int64_t *best_index,
                                    float *best_score, cudaStream_t st);
 
 inline int64_t scratch_elems(int64_t total_samples, int nstars)
 {
-    return 256 * ((total_samples + 255) / 256 + nstars) + 4 * kTile;
+    return 256 * ((total_samples + 255) / 256 + nstars) + 2 * kMaxTile;
 }
 
 }  // namespace gpfc

@@ -72,3 +72,36 @@ def test_sm103a_binary_is_built():
     g.load_library()
     logs = glob.glob(os.path.join(ROOT, "paper_2312_02063_gb300", "_build", "*.ptxas.txt"))
     assert logs and any("sm_103a" in open(l).read() for l in logs)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof / offsetof of the public structs, compiled from include/gpfc.h with gcc, equal
+    the ctypes mirrors the Python binding passes across the boundary."""
+    import shutil
+    import subprocess
+    import paper_2312_02063_gb300 as g
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "gpfc.h"\n'
+        'int main(void) {\n'
+        '  printf("%zu %zu %zu %zu\\n", sizeof(gpfc_fold_config), sizeof(gpfc_box_params),\n'
+        '         sizeof(gpfc_cnn_weights), offsetof(gpfc_fold_config, blocks_per_sm));\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(g.FoldConfig)
+    assert int(out[1]) == ctypes.sizeof(g.BoxParams)
+    assert int(out[2]) == ctypes.sizeof(g.CnnWeights)
+    assert int(out[3]) == g.FoldConfig.blocks_per_sm.offset
+
+
+def test_batched_entry_rejects_null_context_without_gpu():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    assert lib.gpfc_search_batched(None, 1, None, None, None, 1, None, None, 1, None, 64, 0, None, None, None,
+                                   None) == -1
+    assert lib.gpfc_set_graph(None, 1) == -1
+    assert lib.gpfc_set_autotune(None, 1) == -1
