@@ -220,6 +220,56 @@ def cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args):
     return out
 
 
+def batched_measurements(g, ctx, flush, stream, args):
+    """Many-star search: stars of 8,192-70,000 samples with gaps, each with its own grid of
+    20,000-250,000 periods, 256 bins, CNN (and box-SNR) scorer. The batched call (one
+    graph-captured launch sequence, autotuned fold) against a loop of single-star calls."""
+    import torch
+    import lcsynth
+    from paper_2312_02063_gb300 import train as tr
+    sb = lcsynth.star_batch(n_stars=args.batch_stars)
+    dev = ctx.device
+    d = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in
+         (sb.lc_offsets, sb.times, sb.flux, sb.grid_offsets, sb.periods, sb.t0s)]
+    S = args.batch_stars
+    lens = np.diff(sb.lc_offsets)
+    grids = np.diff(sb.grid_offsets)
+    folds = float(np.sum(lens.astype(np.float64) * grids))
+    npt = int(sb.grid_offsets[-1])
+    w = tr.init_weights(dev, 1)
+    score = torch.empty(npt, dtype=torch.float32, device=dev)
+    bi = torch.empty(S, dtype=torch.int64, device=dev)
+    bs = torch.empty(S, dtype=torch.float32, device=dev)
+    out = {"workload": f"{S} stars, N {lens.min()}..{lens.max()} samples (sum {int(lens.sum())}), "
+                       f"grids {grids.min()}..{grids.max()} periods (sum {npt}), 256 bins",
+           "sample_period_folds": folds}
+    for name, scorer, kw in (("cnn", g.SCORER_CNN, {"weights": w}), ("box", g.SCORER_BOX, {"w_max": W_MAX})):
+        def run_batched():
+            g.gpfc_search_batched(ctx, d[0], d[1], d[2], d[3], d[4], NBINS, d[5], scorer, score=score,
+                                  best_index=bi, best_score=bs, **kw)
+        per = [(int(sb.lc_offsets[s]), int(sb.lc_offsets[s + 1]), int(sb.grid_offsets[s]),
+                int(sb.grid_offsets[s + 1])) for s in range(S)]
+        bi1 = torch.empty(1, dtype=torch.int64, device=dev)
+        bs1 = torch.empty(1, dtype=torch.float32, device=dev)
+
+        def run_loop():
+            for (a, b, c, e) in per:
+                g.gpfc_search(ctx, d[1][a:b], d[2][a:b], d[4][c:e], NBINS, 0.0, scorer, score=score[c:e],
+                              best_index=bi1, best_score=bs1, **kw)
+        ms_b = timed(run_batched, flush, stream, reps=2)
+        ms_l = timed(run_loop, flush, stream, reps=2)
+        plan = ctx.last_fold_plan()
+        out[name] = {"batched_ms": ms_b, "unbatched_ms": ms_l, "speedup": ms_l / ms_b,
+                     "stars_per_s": S / (ms_b * 1e-3), "periods_per_s": npt / (ms_b * 1e-3),
+                     "folds_per_s": folds / (ms_b * 1e-3),
+                     "unbatched_stars_per_s": S / (ms_l * 1e-3), "unbatched_periods_per_s": npt / (ms_l * 1e-3)}
+        # the plan of the batched call (the loop's last call may differ)
+        run_batched()
+        out[name]["fold_plan"] = ctx.last_fold_plan()
+    ctx.sync()
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2312_02063_gb300 as g
@@ -346,6 +396,8 @@ def run_gpu(args, rank, world, local_rank):
         }
         if not args.no_cnn:
             result.update(cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args))
+        if args.batch_stars > 0:
+            result["batched"] = batched_measurements(g, ctx, flush, stream, args)
         print(json.dumps(result), flush=True)
     ctx.close()
     if dist:
@@ -366,6 +418,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=60)
     ap.add_argument("--cnn-profiles", type=int, default=262_144)
     ap.add_argument("--eval-profiles", type=int, default=40_000)
+    ap.add_argument("--batch-stars", type=int, default=64,
+                    help="stars of the many-star search measurement (0: skip)")
     args = ap.parse_args()
     globals()["N_PERIODS"] = args.n_periods
     rank, world, local_rank = env_rank()
