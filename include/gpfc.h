@@ -123,6 +123,14 @@ int gpfc_autotune(gpfc_ctx *ctx, const double *times, const float *flux, int64_t
                   const void *scorer_params, gpfc_fold_config *out);
 int gpfc_set_autotune(gpfc_ctx *ctx, int enable);
 
+/* Self-test of the device-side failure path. Every wait in the kernels (on the
+ * bulk-copy and tensor-core mbarriers) gives up after about two seconds, latches a
+ * timeout bit, lets the block's own copies and MMAs land and returns, so a stuck wait
+ * never hangs the GPU. This call launches one thread that waits on an mbarrier nothing
+ * arrives on, with a limit of limit_cycles clock cycles (1e3 .. 4e9): the wait gives up,
+ * and gpfc_sync (or the next call) returns GPFC_ETIMEOUT. The context stays usable. */
+int gpfc_check_wait_timeout(gpfc_ctx *ctx, int64_t limit_cycles);
+
 /* Device workspace (bytes) the context needs for gpfc_fold / gpfc_search (box scorer) of
  * one star of n samples over n_periods periods under the current launch config. */
 int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes);

@@ -113,6 +113,7 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_search_batched.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                           ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.gpfc_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_check_wait_timeout.argtypes = [_vp, ctypes.c_int64]
         L.gpfc_set_autotune.argtypes = [_vp, ctypes.c_int]
         L.gpfc_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_int, _vp, ctypes.POINTER(FoldConfig)]
@@ -199,6 +200,10 @@ class Context:
     def set_graph(self, enable: bool):
         """Capture gpfc_search_batched into a CUDA graph and replay it (default on)."""
         self._check(self.lib.gpfc_set_graph(self.handle, int(bool(enable))))
+
+    def check_wait_timeout(self, limit_cycles: int = 2_000_000):
+        """Run the bounded-wait self-test: the next sync raises GpfcError(GPFC_ETIMEOUT)."""
+        self._check(self.lib.gpfc_check_wait_timeout(self.handle, int(limit_cycles)))
 
     def workspace_size(self, n: int, n_periods: int, nbins: int) -> int:
         v = ctypes.c_size_t()

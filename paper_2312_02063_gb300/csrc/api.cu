@@ -850,6 +850,19 @@ int gpfc_autotune(gpfc_ctx *ctx, const double *times, const float *flux, int64_t
                      bp, n, out);
 }
 
+int gpfc_check_wait_timeout(gpfc_ctx *ctx, int64_t limit_cycles)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (limit_cycles < 1000 || limit_cycles > 4000000000LL)
+        return set_err(ctx, GPFC_EINVAL, "limit_cycles outside [1e3, 4e9]");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    cudaError_t e = launch_wait_selftest((long long)limit_cycles, ctx->status_dev, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "wait self-test kernel");
+    return GPFC_OK;
+}
+
 int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes)
 {
     if (!ctx || !bytes) return GPFC_EINVAL;

@@ -402,7 +402,12 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
         tc_fence_after();
         if (S.abort) break;
     }
-    if (S.abort && tid == 0) report_error(p.status, kErrTimeout);
+    if (S.abort && tid == 0) {
+        report_error(p.status, kErrTimeout);
+        // the last commit tracks every MMA this block issued: let them finish before the
+        // accumulator columns are released
+        mbar_wait_bounded(&S.bar, phase ^ 1u);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 128);
@@ -422,6 +427,7 @@ struct FcSmem {
     uint64_t done;
     uint32_t tslot;
     int abort;
+    uint32_t drain_from;  // first stage use the MMA thread did not consume (abort path)
 };
 
 __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
@@ -531,7 +537,17 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
         tc_fence_after();
         if (S.abort) break;
     }
-    if (S.abort && tid == 0) report_error(p.status, kErrTimeout);
+    if (S.abort) {
+        // let the bulk copies and MMAs this block issued land before it exits
+        if (tid == 32) S.drain_from = it_mma;
+        __syncthreads();
+        if (tid == 0) {
+            report_error(p.status, kErrTimeout);
+            for (uint32_t it = S.drain_from; it < it_prod; ++it)
+                if (!mbar_wait_bounded(&S.full[it % kFcStages], (it / kFcStages) & 1u)) break;
+        }
+        if (tid == 32) mbar_wait_bounded(&S.done, done_phase ^ 1u);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);

@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
         __syncthreads();  // previous task's readers are done with both buffers
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && ntiles > 0) {  // a star without samples issues nothing
             issue(0, 0);
             if (ntiles > 1) issue(1, 1);
         }
@@ -865,7 +865,14 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 }
             }
             __syncthreads();
-            if (s_abort) return;
+            if (s_abort) {
+                if (threadIdx.x == 0) {
+                    // let this block's bulk copies in flight (tiles t and t + 1) land first
+                    mbar_wait_bounded(&bars[buf], ((parity_bits >> buf) & 1u) ^ 1u);
+                    if (t + 1 < ntiles) mbar_wait_bounded(&bars[buf ^ 1], (parity_bits >> (buf ^ 1)) & 1u);
+                }
+                return;
+            }
             if (threadIdx.x == 0 && t + 2 < ntiles) issue(t + 2, buf);
         }
 
@@ -1154,6 +1161,26 @@ cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *ke
     int64_t g = want < (int64_t)sms * 4 ? want : (int64_t)sms * 4;
     const int grid = (int)(g < 1 ? 1 : g);
     argmax_kernel<<<grid, 256, 0, st>>>(score, np, key);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bounded-wait self-test
+
+// One thread waits on an mbarrier that nothing arrives on, with a cycle limit, the way
+// every wait of the kernels above is bounded; when the limit passes it latches the
+// timeout bit and returns.
+__global__ void wait_selftest_kernel(long long limit, uint32_t *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0u, limit)) report_error(status, kErrTimeout);
+}
+
+cudaError_t launch_wait_selftest(long long limit, uint32_t *status, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit, status);
     return cudaGetLastError();
 }
 

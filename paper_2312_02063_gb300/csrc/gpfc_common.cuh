@@ -61,13 +61,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of an mbarrier to complete; false after kWaitLimitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of an mbarrier to complete; false after `limit` clock cycles
+// (kWaitLimitCycles, about two seconds, by default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = kWaitLimitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long start = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - start > kWaitLimitCycles) return false;
+        if (clock64() - start > limit) return false;
     }
     return true;
 }

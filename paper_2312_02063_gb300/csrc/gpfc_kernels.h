@@ -100,6 +100,7 @@ cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, in
                               uint32_t *status, cudaStream_t st);
 cudaError_t launch_argmax_segmented(const float *score, const int64_t *grid_off, int nstars,
                                     unsigned long long *key, int num_sms, cudaStream_t st);
+cudaError_t launch_wait_selftest(long long limit, uint32_t *status, cudaStream_t st);
 cudaError_t launch_argmax_finalize(const unsigned long long *key, int nstars, int64_t *best_index,
                                    float *best_score, cudaStream_t st);
 

@@ -105,3 +105,4 @@ def test_batched_entry_rejects_null_context_without_gpu():
                                    None) == -1
     assert lib.gpfc_set_graph(None, 1) == -1
     assert lib.gpfc_set_autotune(None, 1) == -1
+    assert lib.gpfc_check_wait_timeout(None, 10000) == -1

@@ -307,3 +307,20 @@ def test_fold_and_search_every_kernel_variant(ctx, layout, chunk):
                 check_box(score.cpu().numpy(), sc_o)
     finally:
         ctx.reset_fold_config()
+
+
+def test_bounded_wait_gives_up_reports_timeout_and_context_recovers(ctx):
+    """A wait that nothing completes (an mbarrier no copy or MMA arrives on) gives up after
+    its cycle limit, latches the timeout bit and returns; the host reads GPFC_ETIMEOUT and
+    the context keeps working."""
+    import paper_2312_02063_gb300 as g
+    ctx.check_wait_timeout(2_000_000)
+    with pytest.raises(g.GpfcError) as ei:
+        ctx.sync()
+    assert ei.value.code == -5
+    ctx.sync()  # the bit was cleared when it was reported
+    lc = lcsynth.light_curve_tiny()
+    periods = lcsynth.freq_grid(300)
+    fo, co = gpu_fold(ctx, lc.times, lc.flux, periods, 64, lc.t0)
+    mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods, 64, lc.t0)
+    check_fold(fo, co, mean_o, cnt_o)
