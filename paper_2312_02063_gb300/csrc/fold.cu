@@ -408,12 +408,51 @@ __device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
     }
 }
 
+// Fold a run of ng consecutive groups of U samples in which no two samples of a group
+// share a bin (regular-cadence groups at a safe period), as a three-stage software
+// pipeline: while the bin reads of group g are in flight, the tile data of group g+2 is
+// fetched and the bins of group g+1 are computed from registers; then group g is
+// written back. Each group's U reads are all issued before its U writes.
+template <bool POW2, class St, int U>
+__device__ __forceinline__ void fold_run_regular(const uint32_t *__restrict__ stl,
+                                                 const uint32_t *__restrict__ sth,
+                                                 const float *__restrict__ sx, int ng, const St &st,
+                                                 uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift)
+{
+    uint32_t b[U];
+    float x[U];
+    TileRegs<U> T1;
+    load_tile_regs<U>(stl, sth, sx, 0, T1);
+    bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, b, x);
+    load_tile_regs<U>(stl, sth, sx, ng > 1 ? U : 0, T1);
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+        float sm[U];
+        uint32_t c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) st.load(b[u], sm[u], c[u]);
+        TileRegs<U> T2;
+        load_tile_regs<U>(stl, sth, sx, U * min(g + 2, ng - 1), T2);
+        uint32_t nb[U];
+        float nx[U];
+        bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, nb, nx);
+#pragma unroll
+        for (int u = 0; u < U; ++u) st.put(b[u], sm[u] + x[u], c[u] + 1u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            b[u] = nb[u];
+            x[u] = nx[u];
+        }
+        T1 = T2;
+    }
+}
+
 // Fold nvalid samples (a segment starting on a 16-sample boundary of the tile) in groups
-// of 16. A group flagged regular by the prep pass, folded at a period for which 15
-// regular steps can never bring two samples into one bin (`safe`), needs no collision
-// check: its 16 bin reads are all issued before its 16 writes. Other groups, and the
-// tail, go through the checked path.
-template <bool POW2, class St>
+// of 16. Runs of groups flagged regular by the prep pass, folded at a period for which 15
+// regular steps can never bring two samples into one bin (`safe`), need no collision
+// check and go through the pipelined run (in groups of RU = 16 samples, or 8 where the
+// register budget is 128). Other groups, and the tail, go through the checked path.
+template <bool POW2, class St, int RU>
 __device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
                                              const uint32_t *__restrict__ sth,
                                              const float *__restrict__ sx, unsigned long long fmask,
@@ -422,22 +461,19 @@ __device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
 {
     const int ng = nvalid >> 4;
     if (!safe) fmask = 0ull;
+    if (ng < 64) fmask &= (1ull << ng) - 1ull;
+    int g = 0;
 #pragma unroll 1
-    for (int g = 0; g < ng; ++g) {
-        const int i = g << 4;
-        if ((fmask >> g) & 1ull) {
-            TileRegs<16> T;
-            load_tile_regs<16>(stl, sth, sx, i, T);
-            uint32_t b[16];
-            float x[16];
-            bins_from_regs<POW2, 16>(T, Fl, Fh, nbins, shift, b, x);
-            float sm[16];
-            uint32_t c[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) st.load(b[u], sm[u], c[u]);
-#pragma unroll
-            for (int u = 0; u < 16; ++u) st.put(b[u], sm[u] + x[u], c[u] + 1u);
+    while (g < ng) {
+        const unsigned long long rest = fmask >> g;
+        if (rest & 1ull) {
+            // length of the run of flagged groups starting at g
+            const int run = (~rest == 0ull) ? 64 - g : __ffsll((long long)~rest) - 1;
+            fold_run_regular<POW2, St, RU>(stl + 16 * g, sth + 16 * g, sx + 16 * g, run * (16 / RU), st, Fl, Fh,
+                                          nbins, shift);
+            g += run;
         } else {
+            const int i = g << 4;
 #pragma unroll 1
             for (int q = 0; q < 16; q += 4) {
                 TileRegs<4> T;
@@ -462,6 +498,7 @@ __device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
                     }
                 }
             }
+            ++g;
         }
     }
     if (nvalid & 15)
@@ -585,12 +622,16 @@ struct StagedBins {
 };
 
 // Box-SNR search over one profile held by this lane (bin sums centred on a reference,
-// counts). For start s and width w the in-box sums come from running totals: starts
-// s0..s0+7 are scored in one walk over bins s0..s0+6+w_max, so every bin read serves 8
-// boxes and the 8 evaluations are independent. The search maximises
+// counts). The search maximises
 //     v = (S n_in - S_in N) / sqrt(n_in n_out)      (= snr * sigma * sqrt(N))
-// in FP32; ties keep the smaller w, then the smaller s. The winning box is re-evaluated
-// in FP64 from the same bin sums.
+// in FP32 over every circular box of w_min..w_max bins. With the running prefix
+// A(j) = S Pn(j) - N PS(j) of the bins walked so far, the numerator of a box is
+// A(end) - A(start): one subtraction. Starts s0..s0+7 are scored in one walk over bins
+// s0..s0+6+w_max, so every bin read serves 8 boxes and the 8 evaluations are
+// independent. For a fixed start the widths arrive in increasing order, so a strict '>'
+// keeps the smallest width among equal values; the 8 per-start winners are then merged
+// into the profile's best with ties to the smaller w, then the smaller s. The winning
+// box is re-evaluated in FP64 from the same bin sums.
 template <class Bins>
 __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
                                            float &score, int &best_s, int &best_w)
@@ -603,37 +644,43 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
     }
     float bv = -INFINITY;
     int bkey = 0x7fffffff;
-    auto eval = [&](float sin_, float nin, int key, bool ok) {
-        const float nout = Ntot - nin;
-        const float q = nin * nout;
-        const float D = fmaf(Stot, nin, -(sin_ * Ntot));
-        const float v = D * rsqrtf(q);
-        const bool take = ok & (q >= 1.f) & ((v > bv) | ((v == bv) & (key < bkey)));
-        bv = take ? v : bv;
-        bkey = take ? key : bkey;
-    };
     for (int s0 = 0; s0 < nbins; s0 += R) {
         const bool full = s0 + R <= nbins;
-        float bS[R], bN[R];
-        int cr[R];  // key = (w << 12) | s = ((t + 1) << 12) + cr[r]
+        float bA[R], bN[R];     // prefix values at each start
+        float rv[R];            // best value per start
+        int rt[R];              // its walk step t (width = t - r + 1)
 #pragma unroll
-        for (int r = 0; r < R; ++r) cr[r] = s0 + r - (r << 12);
-        float runS = 0.f, runN = 0.f;
+        for (int r = 0; r < R; ++r) {
+            rv[r] = -INFINITY;
+            rt[r] = -1;
+        }
+        float runA = 0.f, runN = 0.f;
         int j = s0;
+        auto step = [&](int t) {
+            const float c = B.c(j);
+            runA = fmaf(Stot, c, fmaf(-Ntot, B.s(j), runA));
+            runN += c;
+            j = (j + 1 == nbins) ? 0 : j + 1;
+            (void)t;
+        };
+        auto eval = [&](int r, int t, bool ok) {
+            const float nin = runN - bN[r];
+            const float q = nin * (Ntot - nin);
+            const float v = (runA - bA[r]) * rsqrtf(q);
+            const bool take = ok & (q >= 1.f) & (v > rv[r]);
+            rv[r] = take ? v : rv[r];
+            rt[r] = take ? t : rt[r];
+        };
         // head: t = 0..R-1; start r is entered at t = r
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            bS[t] = runS;
+            bA[t] = runA;
             bN[t] = runN;
-            runS += B.s(j);
-            runN += B.c(j);
-            j = (j + 1 == nbins) ? 0 : j + 1;
-            const int T = (t + 1) << 12;
+            step(t);
 #pragma unroll
             for (int r = 0; r <= t; ++r) {
                 const int w = t - r + 1;
-                eval(runS - bS[r], runN - bN[r], T + cr[r],
-                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
+                eval(r, t, (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
             }
         }
         const int tend = R - 1 + w_max;  // exclusive
@@ -644,36 +691,34 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
             tb = R;
         }
         for (int t = R; t < min(ta, tend); ++t) {
-            runS += B.s(j);
-            runN += B.c(j);
-            j = (j + 1 == nbins) ? 0 : j + 1;
-            const int T = (t + 1) << 12;
+            step(t);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int w = t - r + 1;
-                eval(runS - bS[r], runN - bN[r], T + cr[r],
-                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
+                eval(r, t, (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
             }
         }
         for (int t = ta; t < tb; ++t) {  // every (r, w) valid here
-            runS += B.s(j);
-            runN += B.c(j);
-            j = (j + 1 == nbins) ? 0 : j + 1;
-            const int T = (t + 1) << 12;
+            step(t);
 #pragma unroll
-            for (int r = 0; r < R; ++r) eval(runS - bS[r], runN - bN[r], T + cr[r], true);
+            for (int r = 0; r < R; ++r) eval(r, t, true);
         }
         for (int t = max(tb, R); t < tend; ++t) {
-            runS += B.s(j);
-            runN += B.c(j);
-            j = (j + 1 == nbins) ? 0 : j + 1;
-            const int T = (t + 1) << 12;
+            step(t);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int w = t - r + 1;
-                eval(runS - bS[r], runN - bN[r], T + cr[r],
-                     (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
+                eval(r, t, (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
             }
+        }
+        // merge the per-start winners: larger v, then smaller w, then smaller s
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (rt[r] < 0) continue;
+            const int key = ((rt[r] - r + 1) << 12) | (s0 + r);
+            const bool take = (rv[r] > bv) | ((rv[r] == bv) & (key < bkey));
+            bv = take ? rv[r] : bv;
+            bkey = take ? key : bkey;
         }
     }
     if (bkey == 0x7fffffff) {
@@ -851,8 +896,9 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     while (i < nvs) {
                         // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
                         const int seg = min(nvs - i, chunk_left);
-                        fold_segment<POW2, St>(stl + i, sth + i, sx + i, fmask >> (i >> 4), seg, st, Fl, Fh,
-                                               (uint32_t)nbins, p.shift, safe);
+                        fold_segment<POW2, St, (MAXW <= 4 ? 16 : 8)>(stl + i, sth + i, sx + i, fmask >> (i >> 4),
+                                                                     seg, st, Fl, Fh, (uint32_t)nbins, p.shift,
+                                                                     safe);
                         i += seg;
                         chunk_left -= seg;
                         const bool last = (t == ntiles - 1) && (sub + i == nv);
