@@ -259,40 +259,42 @@ __device__ __forceinline__ uint32_t cidx(uint32_t b) { return ((b >> 1) << 6) | 
 // word (b / 2) * 32 + lane holds bins 2j and 2j+1, which keeps count accesses
 // conflict-free too. Counts of one chunk stay below 65536.
 struct StorePaired16 {
-    float *acc;     // sums, lane offset applied
-    uint16_t *cnt;  // counts, 2 * lane offset applied
+    uint32_t acc;  // shared address of this lane's bin-0 sum
+    uint32_t cnt;  // shared address of this lane's bin-0/1 count word
     static constexpr bool kSaturates = true;
+    __device__ __forceinline__ static uint32_t soff(uint32_t b) { return b << 7; }
+    __device__ __forceinline__ static uint32_t coff(uint32_t b) { return ((b >> 1) << 7) | ((b & 1u) << 1); }
     __device__ __forceinline__ void load(uint32_t b, float &s, uint32_t &c) const
     {
-        s = acc[b << 5];
-        c = cnt[cidx(b)];
+        s = lds_f32(acc + soff(b));
+        c = lds_u16(cnt + coff(b));
     }
     __device__ __forceinline__ void put(uint32_t b, float s, uint32_t c) const
     {
-        acc[b << 5] = s;
-        cnt[cidx(b)] = (uint16_t)c;
+        sts_f32(acc + soff(b), s);
+        sts_u16(cnt + coff(b), c);
     }
-    __device__ __forceinline__ float sum(uint32_t b) const { return acc[b << 5]; }
-    __device__ __forceinline__ uint32_t count(uint32_t b) const { return cnt[cidx(b)]; }
+    __device__ __forceinline__ float sum(uint32_t b) const { return lds_f32(acc + soff(b)); }
+    __device__ __forceinline__ uint32_t count(uint32_t b) const { return lds_u16(cnt + coff(b)); }
 };
 
 // FP32 sum and 32-bit count packed in one 64-bit word (8 bytes per bin): one shared
 // load and one store per update.
 struct StorePacked64 {
-    uint2 *v;  // lane offset applied
+    uint32_t v;  // shared address of this lane's bin-0 word
     static constexpr bool kSaturates = false;
     __device__ __forceinline__ void load(uint32_t b, float &s, uint32_t &c) const
     {
-        const uint2 t = v[b << 5];
+        const uint2 t = lds_u32x2(v + (b << 8));
         s = __uint_as_float(t.x);
         c = t.y;
     }
     __device__ __forceinline__ void put(uint32_t b, float s, uint32_t c) const
     {
-        v[b << 5] = make_uint2(__float_as_uint(s), c);
+        sts_u32x2(v + (b << 8), make_uint2(__float_as_uint(s), c));
     }
-    __device__ __forceinline__ float sum(uint32_t b) const { return __uint_as_float(v[b << 5].x); }
-    __device__ __forceinline__ uint32_t count(uint32_t b) const { return v[b << 5].y; }
+    __device__ __forceinline__ float sum(uint32_t b) const { return __uint_as_float(lds_u32x2(v + (b << 8)).x); }
+    __device__ __forceinline__ uint32_t count(uint32_t b) const { return lds_u32x2(v + (b << 8)).y; }
 };
 
 // Tile data of U consecutive samples, held in registers.
@@ -303,16 +305,16 @@ struct TileRegs {
     float4 f[U / 4];  // flux - f_ref
 };
 
+// Tile data (shared addresses of the tau-low, tau-high and flux words of sample 0).
 template <int U>
-__device__ __forceinline__ void load_tile_regs(const uint32_t *__restrict__ stl,
-                                               const uint32_t *__restrict__ sth,
-                                               const float *__restrict__ sx, int i, TileRegs<U> &T)
+__device__ __forceinline__ void load_tile_regs(uint32_t stl, uint32_t sth, uint32_t sx, int i, TileRegs<U> &T)
 {
 #pragma unroll
     for (int q = 0; q < U / 4; ++q) {
-        T.a[q] = *reinterpret_cast<const uint4 *>(stl + i + 4 * q);
-        T.h[q] = *reinterpret_cast<const uint4 *>(sth + i + 4 * q);
-        T.f[q] = *reinterpret_cast<const float4 *>(sx + i + 4 * q);
+        const uint32_t o = 4u * (uint32_t)(i + 4 * q);
+        T.a[q] = lds_u32x4(stl + o);
+        T.h[q] = lds_u32x4(sth + o);
+        T.f[q] = lds_f32x4(sx + o);
     }
 }
 
@@ -350,9 +352,7 @@ __device__ __forceinline__ bool hazard_u(const uint32_t (&b)[U])
 // then group g is written back. A group in which two samples share a bin is applied
 // one sample at a time.
 template <bool POW2, class St, int U>
-__device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
-                                          const uint32_t *__restrict__ sth,
-                                          const float *__restrict__ sx, int nvalid, const St &st,
+__device__ __forceinline__ void fold_tile(uint32_t stl, uint32_t sth, uint32_t sx, int nvalid, const St &st,
                                           uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift)
 {
     const int ng = nvalid / U;
@@ -400,23 +400,39 @@ __device__ __forceinline__ void fold_tile(const uint32_t *__restrict__ stl,
         }
     }
     for (int i = U * ng; i < nvalid; ++i) {
-        const uint32_t bb = phase_bin<POW2>(stl[i], sth[i], Fl, Fh, nbins, shift);
+        const uint32_t bb = phase_bin<POW2>(lds_u32(stl + 4u * i), lds_u32(sth + 4u * i), Fl, Fh, nbins, shift);
+        const float xi = lds_f32(sx + 4u * i);
         float s1;
         uint32_t c1;
         st.load(bb, s1, c1);
-        st.put(bb, s1 + sx[i], c1 + 1u);
+        st.put(bb, s1 + xi, c1 + 1u);
     }
 }
 
+// Largest group of consecutive regular samples (16, 8, or 0 for none) that can never put
+// two of its samples into one bin at this lane's frequency F: for every distance k up to
+// the group size minus one, k regular steps (each in [d0, d0 + 2] tau units) move the
+// phase by at least one bin, without wrapping round to the same bin.
+__device__ __forceinline__ int regular_group_size(unsigned long long F, long long d0, uint32_t nbins)
+{
+    if (d0 <= 0 || F == 0ull || F > 0xFFFFFFFFFFFFFFFFull / 32ull) return 0;
+    for (int k = 1; k < 16; ++k) {
+        const unsigned long long ph = (unsigned long long)k * (unsigned long long)d0 * F;  // mod 2^64
+        const unsigned long long dist = ph < (0ull - ph) ? ph : (0ull - ph);  // circular distance
+        const unsigned long long jitter = (unsigned long long)(2 * k) * F;
+        if (dist <= jitter || __umul64hi(dist - jitter, (unsigned long long)nbins) == 0ull)  // < 1 bin
+            return k < 8 ? 0 : 8;
+    }
+    return 16;
+}
+
 // Fold a run of ng consecutive groups of U samples in which no two samples of a group
-// share a bin (regular-cadence groups at a safe period), as a three-stage software
-// pipeline: while the bin reads of group g are in flight, the tile data of group g+2 is
-// fetched and the bins of group g+1 are computed from registers; then group g is
-// written back. Each group's U reads are all issued before its U writes.
+// share a bin (regular-cadence groups, U within the period's safe group size), as a
+// three-stage software pipeline: while the bin reads of group g are in flight, the tile
+// data of group g+2 is fetched and the bins of group g+1 are computed from registers;
+// then group g is written back. Each group's U reads are all issued before its U writes.
 template <bool POW2, class St, int U>
-__device__ __forceinline__ void fold_run_regular(const uint32_t *__restrict__ stl,
-                                                 const uint32_t *__restrict__ sth,
-                                                 const float *__restrict__ sx, int ng, const St &st,
+__device__ __forceinline__ void fold_run_regular(uint32_t stl, uint32_t sth, uint32_t sx, int ng, const St &st,
                                                  uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift)
 {
     uint32_t b[U];
@@ -448,19 +464,18 @@ __device__ __forceinline__ void fold_run_regular(const uint32_t *__restrict__ st
 }
 
 // Fold nvalid samples (a segment starting on a 16-sample boundary of the tile) in groups
-// of 16. Runs of groups flagged regular by the prep pass, folded at a period for which 15
-// regular steps can never bring two samples into one bin (`safe`), need no collision
-// check and go through the pipelined run (in groups of RU = 16 samples, or 8 where the
-// register budget is 128). Other groups, and the tail, go through the checked path.
-template <bool POW2, class St, int RU>
-__device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
-                                             const uint32_t *__restrict__ sth,
-                                             const float *__restrict__ sx, unsigned long long fmask,
+// of 16. Runs of groups flagged regular by the prep pass go through the pipelined run
+// without collision checks when the warp's group size `wg` allows it: 16-sample groups
+// (wg = 16, blocks with the 255-register budget) or 8-sample halves (wg = 8, or wg = 16
+// where the register budget is 128). Other groups, and the tail, go through the checked
+// path.
+template <bool POW2, class St, bool WIDE16>
+__device__ __forceinline__ void fold_segment(uint32_t stl, uint32_t sth, uint32_t sx, unsigned long long fmask,
                                              int nvalid, const St &st, uint32_t Fl, uint32_t Fh,
-                                             uint32_t nbins, int shift, bool safe)
+                                             uint32_t nbins, int shift, int wg)
 {
     const int ng = nvalid >> 4;
-    if (!safe) fmask = 0ull;
+    if (wg == 0) fmask = 0ull;
     if (ng < 64) fmask &= (1ull << ng) - 1ull;
     int g = 0;
 #pragma unroll 1
@@ -469,8 +484,12 @@ __device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
         if (rest & 1ull) {
             // length of the run of flagged groups starting at g
             const int run = (~rest == 0ull) ? 64 - g : __ffsll((long long)~rest) - 1;
-            fold_run_regular<POW2, St, RU>(stl + 16 * g, sth + 16 * g, sx + 16 * g, run * (16 / RU), st, Fl, Fh,
-                                          nbins, shift);
+            if (WIDE16 && wg == 16)
+                fold_run_regular<POW2, St, 16>(stl + 64u * g, sth + 64u * g, sx + 64u * g, run, st, Fl, Fh, nbins,
+                                               shift);
+            else
+                fold_run_regular<POW2, St, 8>(stl + 64u * g, sth + 64u * g, sx + 64u * g, 2 * run, st, Fl, Fh,
+                                              nbins, shift);
             g += run;
         } else {
             const int i = g << 4;
@@ -502,24 +521,8 @@ __device__ __forceinline__ void fold_segment(const uint32_t *__restrict__ stl,
         }
     }
     if (nvalid & 15)
-        fold_tile<POW2, St, 4>(stl + 16 * ng, sth + 16 * ng, sx + 16 * ng, nvalid & 15, st, Fl, Fh,
+        fold_tile<POW2, St, 4>(stl + 64u * ng, sth + 64u * ng, sx + 64u * ng, nvalid & 15, st, Fl, Fh,
                                nbins, shift);
-}
-
-// True if, for this lane's frequency F, samples 1..15 regular steps apart (each step in
-// [d0, d0 + 2] tau units) are always at least one bin width apart in phase, so they can
-// never share a bin.
-__device__ __forceinline__ bool regular_steps_safe(unsigned long long F, long long d0, uint32_t nbins)
-{
-    if (d0 <= 0 || F == 0ull || F > 0xFFFFFFFFFFFFFFFFull / 32ull) return false;
-    for (int k = 1; k < 16; ++k) {
-        const unsigned long long ph = (unsigned long long)k * (unsigned long long)d0 * F;  // mod 2^64
-        const unsigned long long dist = ph < (0ull - ph) ? ph : (0ull - ph);  // circular distance
-        const unsigned long long jitter = (unsigned long long)(2 * k) * F;
-        if (dist <= jitter) return false;
-        if (__umul64hi(dist - jitter, (unsigned long long)nbins) == 0ull) return false;  // < 1 bin
-    }
-    return true;
 }
 
 // Fold this lane's chunk partials into the Kahan workspace (sum, compensation) and the
@@ -775,13 +778,13 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     St st;
     if constexpr (LAYOUT == kLayoutPacked64) {
         uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (tile / 16));
-        st.v = v + (size_t)warp * nbins * 32 + lane;
+        st.v = smem_u32(v + (size_t)warp * nbins * 32 + lane);
     } else {
         float *acc = reinterpret_cast<float *>(f_buf + 2 * (tile / 16));
         const int nb2 = (nbins + 1) & ~1;
         uint16_t *cnt = reinterpret_cast<uint16_t *>(acc + (size_t)p.warps * nbins * 32);
-        st.acc = acc + (size_t)warp * nbins * 32 + lane;
-        st.cnt = cnt + (size_t)warp * nb2 * 32 + 2 * lane;
+        st.acc = smem_u32(acc + (size_t)warp * nbins * 32 + lane);
+        st.cnt = smem_u32(cnt + (size_t)warp * nb2 * 32 + 2 * lane);
     }
 
     if (threadIdx.x == 0) {
@@ -824,7 +827,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         const bool kvalid = k < ge;
 
         uint32_t Fl = 0u, Fh = 0u;
-        bool safe = false;
+        int gsize = 16;  // lanes past the grid do not restrict the warp's group size
         if (kvalid) {
             const double P = p.periods[k];
             const double q = kTwo40 / P;
@@ -832,11 +835,14 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 const unsigned long long F = (unsigned long long)__double2ll_rn(q);
                 Fl = (uint32_t)F;
                 Fh = (uint32_t)(F >> 32);
-                safe = regular_steps_safe(F, p.stats[s].dtau0, (uint32_t)nbins);
+                gsize = regular_group_size(F, p.stats[s].dtau0, (uint32_t)nbins);
             } else {
+                gsize = 0;
                 report_error(p.status, kErrRange);
             }
         }
+        // one group size for the whole warp, so its lanes never diverge between paths
+        const int wg = __all_sync(0xffffffffu, gsize >= 16) ? 16 : (__all_sync(0xffffffffu, gsize >= 8) ? 8 : 0);
         for (int b = 0; b < nbins; ++b) st.put((uint32_t)b, 0.f, 0u);
         const int ntiles = (int)((nsamp + tile - 1) / tile);
         auto issue = [&](int t, int buf) {
@@ -871,9 +877,9 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 // flag bytes packed into a register bit mask
                 for (int sub = 0; sub < nv; sub += 1024) {
                     const int nvs = min(1024, nv - sub);
-                    const uint32_t *stl = tl_buf + buf * tile + sub;
-                    const uint32_t *sth = th_buf + buf * tile + sub;
-                    const float *sx = x_buf + buf * tile + sub;
+                    const uint32_t stl = smem_u32(tl_buf + buf * tile + sub);
+                    const uint32_t sth = smem_u32(th_buf + buf * tile + sub);
+                    const uint32_t sx = smem_u32(x_buf + buf * tile + sub);
                     unsigned long long fmask = 0ull;
                     {
                         const uint4 *fw = reinterpret_cast<const uint4 *>(f_buf + buf * (tile / 16) + sub / 16);
@@ -896,9 +902,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     while (i < nvs) {
                         // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
                         const int seg = min(nvs - i, chunk_left);
-                        fold_segment<POW2, St, (MAXW <= 4 ? 16 : 8)>(stl + i, sth + i, sx + i, fmask >> (i >> 4),
-                                                                     seg, st, Fl, Fh, (uint32_t)nbins, p.shift,
-                                                                     safe);
+                        fold_segment<POW2, St, (MAXW <= 4)>(stl + 4u * i, sth + 4u * i, sx + 4u * i, fmask >> (i >> 4),
+                                                             seg, st, Fl, Fh, (uint32_t)nbins, p.shift, wg);
                         i += seg;
                         chunk_left -= seg;
                         const bool last = (t == ntiles - 1) && (sub + i == nv);
