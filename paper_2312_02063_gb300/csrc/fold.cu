@@ -629,17 +629,17 @@ struct StagedBins {
 //     v = (S n_in - S_in N) / sqrt(n_in n_out)      (= snr * sigma * sqrt(N))
 // in FP32 over every circular box of w_min..w_max bins. With the running prefix
 // A(j) = S Pn(j) - N PS(j) of the bins walked so far, the numerator of a box is
-// A(end) - A(start): one subtraction. Starts s0..s0+7 are scored in one walk over bins
-// s0..s0+6+w_max, so every bin read serves 8 boxes and the 8 evaluations are
-// independent. For a fixed start the widths arrive in increasing order, so a strict '>'
-// keeps the smallest width among equal values; the 8 per-start winners are then merged
+// A(end) - A(start): one subtraction. R starts s0..s0+R-1 (R = 16, or 8 under a
+// 128-register budget) are scored in one walk over bins s0..s0+R-2+w_max, so every bin
+// read serves R boxes and the R evaluations are independent. For a fixed start the widths
+// arrive in increasing order, so a strict '>' keeps the smallest width among equal
+// values; the R per-start winners are then merged
 // into the profile's best with ties to the smaller w, then the smaller s. The winning
 // box is re-evaluated in FP64 from the same bin sums.
-template <class Bins>
+template <int R, class Bins>
 __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
                                            float &score, int &best_s, int &best_w)
 {
-    constexpr int R = 8;
     float Stot = 0.f, Ntot = 0.f;
     for (int b = 0; b < nbins; ++b) {
         Stot += B.s(b);
@@ -659,11 +659,15 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
         }
         float runA = 0.f, runN = 0.f;
         int j = s0;
+        // the next bin's sum and count are read one step ahead of their use
+        float pf_s = B.s(j), pf_c = B.c(j);
         auto step = [&](int t) {
-            const float c = B.c(j);
-            runA = fmaf(Stot, c, fmaf(-Ntot, B.s(j), runA));
-            runN += c;
+            const float c = pf_c, sv = pf_s;
             j = (j + 1 == nbins) ? 0 : j + 1;
+            pf_s = B.s(j);
+            pf_c = B.c(j);
+            runA = fmaf(Stot, c, fmaf(-Ntot, sv, runA));
+            runN += c;
             (void)t;
         };
         auto eval = [&](int r, int t, bool ok) {
@@ -951,7 +955,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 if (!(sig > 0.f)) sig = p.stats[s].sigma;
                 if (!(sig > 0.f)) sig = 1.f;
                 const LaneBins<St> B{st, wcn_cta, (size_t)ppc, over};
-                box_search(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
+                box_search<(MAXW <= 4 ? 16 : 8)>(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
                 p.score[k] = sc;
                 if (p.best_s) p.best_s[k] = bs;
                 if (p.best_w) p.best_w[k] = bw;
@@ -1137,7 +1141,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) box_kernel(const float *__rest
             float sc;
             int bs, bw;
             const StagedBins B{Sw + lane, Cw + lane, counts + (size_t)k * nbins, big_lane};
-            box_search(B, nbins, w_min, w_max, sigma, sc, bs, bw);
+            box_search<8>(B, nbins, w_min, w_max, sigma, sc, bs, bw);
             score[k] = sc;
             if (best_s) best_s[k] = bs;
             if (best_w) best_w[k] = bw;
