@@ -62,6 +62,8 @@ def lib():
             L.or_bins.argtypes = [_i64p, ctypes.c_int64, _u64p, ctypes.c_int64, ctypes.c_int32, _i32p]
             L.or_fold.argtypes = [_dp, _fp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_double, _dp, _i64p, _dp]
+            L.or_fold_equal_count.argtypes = [_dp, _fp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, _dp, _i64p]
             L.or_bins_naive_fp64.argtypes = [_dp, ctypes.c_int64, _dp, ctypes.c_int64,
                                              ctypes.c_int32, ctypes.c_double, _i32p]
             L.or_box_snr.argtypes = [_dp, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -137,6 +139,25 @@ def fold(times, flux, periods, nbins, t0=None):
     if rc != 0:
         raise ValueError("time or period outside the 64-bit fixed-point range")
     return mean, cnt, s
+
+
+def fold_equal_count(times, flux, periods, nfine, nbins, t0=None):
+    """Two-tier equal-count fold (Sec. 2.3): nfine equal-width fine bins merged left to
+    right into nbins bins of n/nbins samples each. Returns (mean [P][nbins] f64,
+    fine_count [P][nfine] i64)."""
+    times = _c(times, np.float64)
+    flux = _c(flux, np.float32)
+    periods = _c(periods, np.float64)
+    if t0 is None or (isinstance(t0, float) and np.isnan(t0)):
+        t0 = float(times[0])
+    n, npd = times.shape[0], periods.shape[0]
+    mean = np.empty((npd, nbins), np.float64)
+    fc = np.empty((npd, nfine), np.int64)
+    rc = lib().or_fold_equal_count(_p(times, _dp), _p(flux, _fp), n, _p(periods, _dp), npd, int(nfine),
+                                   int(nbins), float(t0), _p(mean, _dp), _p(fc, _i64p))
+    if rc != 0:
+        raise ValueError("time or period outside the 64-bit fixed-point range")
+    return mean, fc
 
 
 def bins_naive_fp64(times, periods, nbins, t0):

@@ -113,6 +113,63 @@ int or_fold(const double *times, const float *flux, int64_t n, const double *per
     return rc;
 }
 
+/* Two-tier equal-count fold (Sec. 2.3, Fig. 4 (a)-(e)): the samples go to nfine
+ * equal-width bins by their fixed-point phase, each fine bin keeping its count and flux
+ * sum (steps 1-3); a left-to-right scan over the fine bins then fills the nbins final
+ * bins one after the other with exactly n / nbins samples each, merging adjacent fine
+ * bins and splitting the fine bin that straddles a boundary (step 4); each final mean is
+ * its flux sum over n / nbins (step 5).
+ * Reading of the split (the paper leaves it open): a fine bin that gives k of its c
+ * samples to a final bin gives it k / c of its flux sum. The scan counts in units of
+ * 1 / nbins sample, so every boundary (a multiple of n units) is exact in integers.
+ * mean is [np][nbins]; fine_count (may be NULL) [np][nfine]. Returns 0 or -4. */
+int or_fold_equal_count(const double *times, const float *flux, int64_t n, const double *periods,
+                        int64_t np, int32_t nfine, int32_t nbins, double t0, double *mean,
+                        int64_t *fine_count)
+{
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(np > 0 ? np : 1));
+    double *s = (double *)malloc(sizeof(double) * (size_t)nfine);
+    int64_t *c = (int64_t *)malloc(sizeof(int64_t) * (size_t)nfine);
+    int rc = or_quantise_times(times, n, t0, tau);
+    int rc2 = or_quantise_periods(periods, np, F);
+    if (rc == 0) rc = rc2;
+    const int64_t cap = n; /* units per final bin */
+    for (int64_t k = 0; k < np; k++) {
+        for (int32_t f = 0; f < nfine; f++) { s[f] = 0.0; c[f] = 0; }
+        for (int64_t i = 0; i < n; i++) {
+            uint32_t f = or_bin(tau[i], F[k], nfine);
+            c[f] += 1;
+            s[f] += (double)flux[i];
+        }
+        if (fine_count)
+            for (int32_t f = 0; f < nfine; f++) fine_count[k * nfine + f] = c[f];
+        int32_t j = 0;      /* final bin being filled */
+        int64_t fill = 0;   /* units already in it */
+        double acc = 0.0;   /* its flux sum */
+        for (int32_t f = 0; f < nfine && j < nbins; f++) {
+            int64_t left = c[f] * (int64_t)nbins; /* units of fine bin f not yet placed */
+            const int64_t whole = left;
+            while (left > 0 && j < nbins) {
+                const int64_t room = cap - fill;
+                const int64_t take = left < room ? left : room;
+                acc += s[f] * ((double)take / (double)whole);
+                fill += take;
+                left -= take;
+                if (fill == cap) {
+                    mean[k * nbins + j] = acc / ((double)n / (double)nbins);
+                    j++;
+                    fill = 0;
+                    acc = 0.0;
+                }
+            }
+        }
+        for (; j < nbins; j++) mean[k * nbins + j] = NAN; /* only when n == 0 */
+    }
+    free(tau); free(F); free(s); free(c);
+    return rc;
+}
+
 /* The phase the paper states, frac((t - t0) / P), taken directly in FP64. Returns
  * floor(frac * nbins) per (k, i); used only to report how often the fixed-point bins
  * differ from it (at bin edges). */
