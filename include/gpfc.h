@@ -308,6 +308,25 @@ int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods,
 int gpfc_best_period_noalloc(const float *score, int64_t n_periods, int64_t *best_index,
                              float *best_score, void *stream);
 
+/* ------------------------------------------------------------------ two-tier fold
+ * The paper's own fold (Sec. 2.3, Fig. 4 (a)-(e)): each sample goes to one of nfine
+ * equal-width fine bins by its fixed-point phase (as in gpfc_fold); the fine bins are then
+ * merged left to right into nbins final bins of exactly n / nbins samples each, the fine
+ * bin that straddles a boundary giving each side the share of its flux sum that it gives
+ * of its samples (the paper does not say how a boundary bin's sum is divided; this
+ * proportional split is this library's reading); each output is the bin's mean flux. No
+ * final bin is empty. The paper uses nfine = 4096, nbins = 256.
+ *  - times [n] f64, flux [n] f32, periods [n_periods] f64: device; folded [n_periods][nbins]
+ *    f32 means: device, caller-owned.
+ *  - 1 <= n < 2^24; 2 <= nbins <= nfine <= 4096; t0 as for gpfc_fold.
+ * Sums are exact fixed-point integers (quantum 2^-k per light curve, with
+ * n max|flux - mean| 2^k < 2^38), so the result does not depend on summation order.
+ * Returns GPFC_OK, GPFC_EINVAL, GPFC_ENOTSUP or GPFC_ECUDA; bad periods are reported
+ * later as GPFC_ERANGE. */
+int gpfc_fold_equal_count(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
+                          const double *periods, int64_t n_periods, int32_t nfine, int32_t nbins,
+                          double t0, float *folded);
+
 /* ------------------------------------------------------------------ search
  * Fold + score (Fig. 1) without returning the profiles. scorer GPFC_SCORER_BOX takes a
  * gpfc_box_params* in scorer_params: the box search runs in the fold kernel's epilogue on

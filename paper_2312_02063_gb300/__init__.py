@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -113,6 +113,8 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_search_batched.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                           ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.gpfc_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_fold_equal_count.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_double, _vp]
         L.gpfc_check_wait_timeout.argtypes = [_vp, ctypes.c_int64]
         L.gpfc_set_autotune.argtypes = [_vp, ctypes.c_int]
         L.gpfc_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
@@ -252,6 +254,23 @@ def gpfc_fold(ctx: Context, times, flux, periods, nbins: int, t0: float = math.n
     ctx._check(ctx.lib.gpfc_fold(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), npd, int(nbins),
                                  float(t0), _ptr(folded), _ptr(counts)))
     return folded, counts
+
+
+def gpfc_fold_equal_count(ctx: Context, times, flux, periods, nbins: int = 256, nfine: int = 4096,
+                          t0: float = math.nan, folded=None):
+    """The paper's two-tier fold: nfine equal-width fine bins merged into nbins bins of
+    n/nbins samples each. Returns folded f32 [P][nbins] (means)."""
+    dev = ctx.device
+    n, npd = times.numel(), periods.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    _need(periods, torch.float64, dev, "periods")
+    if folded is None:
+        folded = torch.empty((npd, nbins), dtype=torch.float32, device=dev)
+    _need(folded, torch.float32, dev, "folded", npd * nbins)
+    ctx._check(ctx.lib.gpfc_fold_equal_count(ctx.handle, _ptr(times), _ptr(flux), n, _ptr(periods), npd,
+                                             int(nfine), int(nbins), float(t0), _ptr(folded)))
+    return folded
 
 
 def gpfc_score_box(ctx: Context, folded, counts, w_min: int, w_max: int, sigma: float = 0.0,

@@ -15,6 +15,7 @@
 #include "gpfc_cnn.h"
 #include "gpfc_kernels.h"
 #include "gpfc_synth.h"
+#include "gpfc_twotier.h"
 
 using namespace gpfc;
 
@@ -925,6 +926,72 @@ int gpfc_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, 
     p.folded = folded;
     p.counts = counts;
     return run_fold(ctx, times, flux, n, periods, n_periods, nbins, t0, kModeFold, p, false, nullptr);
+}
+
+int gpfc_fold_equal_count(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                          int64_t n_periods, int32_t nfine, int32_t nbins, double t0, float *folded)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!times || !flux || !periods || !folded) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1 || n >= ((int64_t)1 << 24)) return set_err(ctx, GPFC_EINVAL, "n = %lld outside [1, 2^24 - 1]", (long long)n);
+    if (n_periods < 1 || n_periods > (int64_t)INT32_MAX)
+        return set_err(ctx, GPFC_EINVAL, "n_periods = %lld outside [1, 2^31-1]", (long long)n_periods);
+    if (nbins < 2 || nfine < nbins || nfine > kEqMaxFine)
+        return set_err(ctx, GPFC_EINVAL, "need 2 <= nbins <= nfine <= %d (nbins %d, nfine %d)", kEqMaxFine, nbins, nfine);
+    const int ppb = eq_periods_per_block(nfine);
+    if (ppb < 1) return set_err(ctx, GPFC_ENOTSUP, "nfine = %d does not fit shared memory", nfine);
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    const int G = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 8191) / 8192));
+    auto carve = [&](void *base, double **partial, StarStats **stats, SampleScratch *smp, long long **q,
+                     unsigned int **maxbits, int **kscale) {
+        Carver c(base);
+        *partial = c.take<double>((size_t)3 * G);
+        *stats = c.take<StarStats>(1);
+        const int64_t se = scratch_elems(n, 1);
+        smp->tau_lo = c.take<uint32_t>(se);
+        smp->tau_hi = c.take<int32_t>(se);
+        smp->x = c.take<float>(se);
+        smp->flags = c.take<uint8_t>(se / 16 + 64);
+        *q = c.take<long long>(n);
+        *maxbits = c.take<unsigned int>(1);
+        *kscale = c.take<int>(1);
+        return c.off + 256;
+    };
+    double *partial;
+    StarStats *stats;
+    SampleScratch smp{};
+    long long *q;
+    unsigned int *maxbits;
+    int *kscale;
+    rc = ensure_ws(ctx, carve(nullptr, &partial, &stats, &smp, &q, &maxbits, &kscale));
+    if (rc) return rc;
+    carve(ctx->ws, &partial, &stats, &smp, &q, &maxbits, &kscale);
+    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, smp, partial, G, stats,
+                                ctx->status_dev, ctx->stream);
+    if (e == cudaSuccess) e = launch_eq_prep(smp.x, n, maxbits, q, kscale, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    EqParams p{};
+    p.tau_lo = smp.tau_lo;
+    p.tau_hi = smp.tau_hi;
+    p.q = q;
+    p.n = n;
+    p.periods = periods;
+    p.np = n_periods;
+    p.nfine = nfine;
+    p.nbins = nbins;
+    p.fshift = shift_of(nfine);
+    p.ppb = ppb;
+    p.kscale = kscale;
+    p.stats = stats;
+    p.folded = folded;
+    p.status = ctx->status_dev;
+    KernelTimer timer(ctx);
+    e = launch_eq_fold(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "two-tier fold kernel");
+    timer.stop();
+    return GPFC_OK;
 }
 
 int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts, int64_t n_periods,
