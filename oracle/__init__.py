@@ -64,6 +64,9 @@ def lib():
                                   ctypes.c_double, _dp, _i64p, _dp]
             L.or_fold_equal_count.argtypes = [_dp, _fp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_double, _dp, _i64p]
+            L.or_peaks.argtypes = [_fp, _dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_int32, _dp, _i64p, _i64p, _fp, _i32p, _i32p]
+            L.or_peaks.restype = ctypes.c_int32
             L.or_bins_naive_fp64.argtypes = [_dp, ctypes.c_int64, _dp, ctypes.c_int64,
                                              ctypes.c_int32, ctypes.c_double, _i32p]
             L.or_box_snr.argtypes = [_dp, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -284,6 +287,28 @@ def adam_step(param, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     mhat = m / (1.0 - beta1 ** t)
     vhat = v / (1.0 - beta2 ** t)
     return param - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def peaks(score, periods, k_sigma=3.0, min_width=4, harmonic_tol=1e-3, max_peaks=8):
+    """Per-star decision over a periodogram: SDE (Eq. 3) and the peak rule of Sec. 4.2.
+
+    Returns a dict with mean, sd, sde, best_index (-1 if no qualifying peak), n_peaks and
+    the listed peaks (index, height, width, harmonic), highest first.
+    """
+    score = _c(score, np.float32)
+    periods = _c(periods, np.float64)
+    npd = score.shape[0]
+    st = np.empty(3, np.float64)
+    best = np.empty(2, np.int64)
+    idx = np.empty(max(1, max_peaks), np.int64)
+    h = np.empty(max(1, max_peaks), np.float32)
+    w = np.empty(max(1, max_peaks), np.int32)
+    hm = np.empty(max(1, max_peaks), np.int32)
+    n = lib().or_peaks(_p(score, _fp), _p(periods, _dp), npd, float(k_sigma), int(min_width), float(harmonic_tol),
+                       int(max_peaks), _p(st, _dp), _p(best, _i64p), _p(idx, _i64p), _p(h, _fp), _p(w, _i32p),
+                       _p(hm, _i32p))
+    return {"mean": st[0], "sd": st[1], "sde": st[2], "best_index": int(best[0]), "n_peaks": int(best[1]),
+            "index": idx[:n].copy(), "height": h[:n].copy(), "width": w[:n].copy(), "harmonic": hm[:n].copy()}
 
 
 def sigmoid(z):

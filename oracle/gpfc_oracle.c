@@ -266,6 +266,84 @@ int64_t or_argmax(const float *score, int64_t np)
     return best;
 }
 
+/* ---------------------------------------------------------------- per-star decision */
+
+/* Decision over one star's periodogram score[0..np-1] (non-finite entries are left out
+ * of the statistics and never belong to a peak):
+ *  - mean and population standard deviation of the finite scores;
+ *  - SDE = (max - mean) / sd (Eq. 3; 0 when sd is 0);
+ *  - peaks (Sec. 4.2): maximal runs of consecutive periods scoring above
+ *    mean + k_sigma * sd; a run qualifies when it is at least min_width periods wide
+ *    ("more than 3" is min_width = 4). Its height is its largest score, at its first
+ *    occurrence. The best peak is the highest (ties: smaller index);
+ *  - the qualifying peaks by decreasing height (ties: smaller index), at most max_peaks,
+ *    each with a harmonic flag against the best peak's period Pb (Fig. 14 notes peaks
+ *    at harmonics): 1 for the best, +m if P = m Pb, -m if P = Pb / m (m = 2..4, within
+ *    relative tolerance harmonic_tol), else 0.
+ * out_stats: mean, sd, sde. out_best: best index (-1 if none), n_peaks.
+ * peaks_*: [max_peaks]. Returns the number of peaks listed. */
+int32_t or_peaks(const float *score, const double *periods, int64_t np, double k_sigma, int32_t min_width,
+                 double harmonic_tol, int32_t max_peaks, double *out_stats, int64_t *out_best,
+                 int64_t *peak_index, float *peak_height, int32_t *peak_width, int32_t *peak_harm)
+{
+    double sum = 0.0, cnt = 0.0, mx = -INFINITY;
+    for (int64_t k = 0; k < np; k++)
+        if (isfinite(score[k])) { sum += (double)score[k]; cnt += 1.0; if ((double)score[k] > mx) mx = score[k]; }
+    const double mean = cnt > 0 ? sum / cnt : NAN;
+    double ss = 0.0;
+    for (int64_t k = 0; k < np; k++)
+        if (isfinite(score[k])) { const double d = (double)score[k] - mean; ss += d * d; }
+    const double sd = cnt > 0 ? sqrt(ss / cnt) : NAN;
+    out_stats[0] = mean;
+    out_stats[1] = sd;
+    out_stats[2] = cnt > 0 ? (sd > 0 ? (mx - mean) / sd : 0.0) : NAN;
+    const double thr = mean + k_sigma * sd;
+    /* qualifying runs */
+    int64_t nq = 0, cap = np > 0 ? np : 1;
+    int64_t *ri = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    float *rh = (float *)malloc(sizeof(float) * (size_t)cap);
+    int32_t *rw = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    int64_t k = 0;
+    while (k < np) {
+        if (!(isfinite(score[k]) && (double)score[k] > thr)) { k++; continue; }
+        int64_t e = k, arg = k;
+        while (e < np && isfinite(score[e]) && (double)score[e] > thr) {
+            if (score[e] > score[arg]) arg = e;
+            e++;
+        }
+        if (e - k >= min_width) { ri[nq] = arg; rh[nq] = score[arg]; rw[nq] = (int32_t)(e - k); nq++; }
+        k = e;
+    }
+    out_best[1] = nq;
+    /* order by height, then index (selection of the top max_peaks) */
+    int32_t listed = 0;
+    char *taken = (char *)calloc((size_t)(nq > 0 ? nq : 1), 1);
+    for (; listed < max_peaks && listed < nq; listed++) {
+        int64_t b = -1;
+        for (int64_t q = 0; q < nq; q++)
+            if (!taken[q] && (b < 0 || rh[q] > rh[b] || (rh[q] == rh[b] && ri[q] < ri[b]))) b = q;
+        taken[b] = 1;
+        peak_index[listed] = ri[b];
+        peak_height[listed] = rh[b];
+        peak_width[listed] = rw[b];
+    }
+    out_best[0] = listed > 0 ? peak_index[0] : -1;
+    for (int32_t q = 0; q < listed; q++) {
+        int32_t h = 0;
+        if (q == 0) h = 1;
+        else {
+            const double r = periods[peak_index[q]] / periods[peak_index[0]];
+            for (int32_t m = 2; m <= 4 && h == 0; m++) {
+                if (fabs(r - m) <= harmonic_tol * m) h = m;
+                else if (fabs(1.0 / r - m) <= harmonic_tol * m) h = -m;
+            }
+        }
+        peak_harm[q] = h;
+    }
+    free(ri); free(rh); free(rw); free(taken);
+    return listed;
+}
+
 /* ---------------------------------------------------------------- CNN */
 
 #define L0 256
