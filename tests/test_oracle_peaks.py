@@ -73,7 +73,7 @@ def test_non_finite_scores_break_runs():
 def test_harmonic_flags():
     N = 2000
     periods = np.linspace(0.1, 2.0, N)
-    best = 600
+    best = 500
     Pb = periods[best]
 
     def at(P):
