@@ -341,6 +341,45 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
                 int scorer, const void *scorer_params, float *score,
                 int64_t *best_index, float *best_score);
 
+/* ------------------------------------------------------------------ per-star decision
+ * Decision over periodograms (the scores of gpfc_search / gpfc_search_batched, one per
+ * trial period). For each star, over its finite scores: the mean and population standard
+ * deviation; SDE = (max - mean) / sd (Eq. 3; 0 when sd is 0); peaks as in Sec. 4.2:
+ * maximal runs of consecutive periods scoring above mean + k_sigma * sd that are at least
+ * min_width periods wide (the paper's "height of 3 sigma and width of more than 3" is
+ * k_sigma = 3, min_width = 4). A peak's height is its largest score (first occurrence).
+ * The best peak is the highest (ties: smaller index). The highest max_peaks peaks are
+ * listed, each with a harmonic flag against the best peak's period Pb (Fig. 14 shows
+ * peaks at harmonics of the transit period): 1 for the best, +m if its period is m Pb,
+ * -m if it is Pb / m (m = 2..4, within relative tolerance harmonic_tol), else 0.
+ * Non-finite scores are left out of the statistics and end a run. */
+typedef struct {
+    double sde;
+    double mean;
+    double sd;
+    int64_t best_index;   /* index into the star's grid of the best peak, -1 if none */
+    float best_score;     /* its height (NaN if none) */
+    int32_t n_peaks;      /* qualifying peaks */
+    int32_t truncated;    /* 1 if more than 2048 qualified: the list covers the first 2048 found */
+    int32_t n_listed;     /* entries written to the star's peak list */
+} gpfc_star_summary;
+
+typedef struct {
+    int64_t index;        /* into the star's grid */
+    float height;
+    int32_t width;        /* periods in the run */
+    int32_t harmonic;
+    int32_t reserved;
+} gpfc_peak;
+
+/* score [n_periods] f32 and periods [n_periods] f64: device. grid_offsets: device [n_stars+1]
+ * (as for gpfc_search_batched), or NULL with n_stars = 1 for one star. summary: device
+ * [n_stars]; peaks: device [n_stars][max_peaks] or NULL (0 <= max_peaks <= 64).
+ * Returns GPFC_OK, GPFC_EINVAL or GPFC_ECUDA. */
+int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t n_stars,
+               const int64_t *grid_offsets, int64_t n_periods, double k_sigma, int32_t min_width,
+               double harmonic_tol, int32_t max_peaks, gpfc_star_summary *summary, gpfc_peak *peaks);
+
 /* ------------------------------------------------------------------ batched search
  * gpfc_search over many stars of uneven length, each with its own period grid, in one
  * sequence of persistent launches (the paper folds one light curve at a time, Sec. 2.3;

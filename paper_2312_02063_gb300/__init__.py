@@ -13,6 +13,7 @@ import math
 import os
 import threading
 
+import numpy as np
 import torch
 
 from . import _build
@@ -20,7 +21,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -113,6 +114,8 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_search_batched.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                           ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.gpfc_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_peaks.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                 ctypes.c_double, ctypes.c_int32, _vp, _vp]
         L.gpfc_fold_equal_count.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_double, _vp]
         L.gpfc_check_wait_timeout.argtypes = [_vp, ctypes.c_int64]
@@ -443,6 +446,39 @@ def gpfc_search_batched(ctx: Context, lc_offsets, times, flux, grid_offsets, per
                                            _ptr(grid_offsets), _ptr(periods), npd, _ptr(t0s), int(nbins),
                                            int(scorer), pp, _ptr(score), _ptr(best_index), _ptr(best_score)))
     return score, best_index, best_score
+
+
+STAR_SUMMARY_DTYPE = np.dtype([("sde", "<f8"), ("mean", "<f8"), ("sd", "<f8"), ("best_index", "<i8"),
+                               ("best_score", "<f4"), ("n_peaks", "<i4"), ("truncated", "<i4"), ("n_listed", "<i4")])
+PEAK_DTYPE = np.dtype([("index", "<i8"), ("height", "<f4"), ("width", "<i4"), ("harmonic", "<i4"),
+                       ("reserved", "<i4")])
+
+
+def gpfc_peaks(ctx: Context, score, periods, grid_offsets=None, k_sigma: float = 3.0, min_width: int = 4,
+               harmonic_tol: float = 1e-3, max_peaks: int = 8):
+    """Per-star decision over periodograms (SDE of Eq. 3, the peak rule of Sec. 4.2,
+    harmonic flags). Returns device byte tensors (summary [S] records, peaks [S][max_peaks]
+    records); `peaks_to_numpy` decodes them."""
+    dev = ctx.device
+    npd = score.numel()
+    _need(score, torch.float32, dev, "score")
+    _need(periods, torch.float64, dev, "periods", npd)
+    S = 1 if grid_offsets is None else grid_offsets.numel() - 1
+    if grid_offsets is not None:
+        _need(grid_offsets, torch.int64, dev, "grid_offsets")
+    summary = torch.empty(S * STAR_SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    peaks = torch.empty(max(1, S * max_peaks * PEAK_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    ctx._check(ctx.lib.gpfc_peaks(ctx.handle, _ptr(score), _ptr(periods), S, _ptr(grid_offsets), npd,
+                                  float(k_sigma), int(min_width), float(harmonic_tol), int(max_peaks),
+                                  _ptr(summary), _ptr(peaks) if max_peaks > 0 else None))
+    return summary, peaks
+
+
+def peaks_to_numpy(summary, peaks, max_peaks: int = 8):
+    """Copy gpfc_peaks' outputs to the host as numpy record arrays (summary [S], peaks [S][max_peaks])."""
+    sm = np.frombuffer(summary.cpu().numpy().tobytes(), dtype=STAR_SUMMARY_DTYPE)
+    pk = np.frombuffer(peaks.cpu().numpy().tobytes()[: len(sm) * max_peaks * PEAK_DTYPE.itemsize], dtype=PEAK_DTYPE)
+    return sm, pk.reshape(len(sm), max_peaks)
 
 
 def gpfc_autotune(ctx: Context, times, flux, periods, nbins: int, scorer: int = SCORER_BOX, w_min: int = 1,

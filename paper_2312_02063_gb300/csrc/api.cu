@@ -16,6 +16,7 @@
 #include "gpfc_kernels.h"
 #include "gpfc_synth.h"
 #include "gpfc_twotier.h"
+#include "gpfc_decide.h"
 
 using namespace gpfc;
 
@@ -1265,6 +1266,41 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
         return run_search_cnn(ctx, times, flux, n, periods, n_periods, nbins, t0, wt, score, best_index, best_score);
     }
     return set_err(ctx, GPFC_ENOTSUP, "scorer %d not available", scorer);
+}
+
+static_assert(sizeof(gpfc_star_summary) == sizeof(PeakSummaryDev), "summary layout");
+static_assert(sizeof(gpfc_peak) == sizeof(PeakDev), "peak layout");
+
+int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t n_stars,
+               const int64_t *grid_offsets, int64_t n_periods, double k_sigma, int32_t min_width,
+               double harmonic_tol, int32_t max_peaks, gpfc_star_summary *summary, gpfc_peak *peaks)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!score || !periods || !summary) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n_stars < 1 || (!grid_offsets && n_stars != 1)) return set_err(ctx, GPFC_EINVAL, "bad n_stars / offsets");
+    if (n_periods < 1 || n_periods > (int64_t)INT32_MAX) return set_err(ctx, GPFC_EINVAL, "bad n_periods");
+    if (min_width < 1 || max_peaks < 0 || max_peaks > 64 || !(k_sigma == k_sigma) || !(harmonic_tol >= 0.0))
+        return set_err(ctx, GPFC_EINVAL, "bad decision parameters");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    PeakParams p{};
+    p.score = score;
+    p.periods = periods;
+    p.grid_off = grid_offsets;
+    p.np = n_periods;
+    p.nstars = n_stars;
+    p.k_sigma = k_sigma;
+    p.min_width = min_width;
+    p.harm_tol = harmonic_tol;
+    p.max_peaks = max_peaks;
+    p.summary = reinterpret_cast<PeakSummaryDev *>(summary);
+    p.peaks = max_peaks > 0 ? reinterpret_cast<PeakDev *>(peaks) : nullptr;
+    KernelTimer timer(ctx);
+    cudaError_t e = launch_peaks(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "decision kernel");
+    timer.stop();
+    return GPFC_OK;
 }
 
 int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offsets, const double *times,

@@ -86,8 +86,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "gpfc.h"\n'
         'int main(void) {\n'
-        '  printf("%zu %zu %zu %zu\\n", sizeof(gpfc_fold_config), sizeof(gpfc_box_params),\n'
-        '         sizeof(gpfc_cnn_weights), offsetof(gpfc_fold_config, blocks_per_sm));\n'
+        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gpfc_fold_config), sizeof(gpfc_box_params),\n'
+        '         sizeof(gpfc_cnn_weights), offsetof(gpfc_fold_config, blocks_per_sm),\n'
+        '         sizeof(gpfc_star_summary), sizeof(gpfc_peak));\n'
         '  return 0;\n}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -96,6 +97,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert int(out[1]) == ctypes.sizeof(g.BoxParams)
     assert int(out[2]) == ctypes.sizeof(g.CnnWeights)
     assert int(out[3]) == g.FoldConfig.blocks_per_sm.offset
+    assert int(out[4]) == g.STAR_SUMMARY_DTYPE.itemsize
+    assert int(out[5]) == g.PEAK_DTYPE.itemsize
 
 
 def test_batched_entry_rejects_null_context_without_gpu():
@@ -106,3 +109,5 @@ def test_batched_entry_rejects_null_context_without_gpu():
     assert lib.gpfc_set_graph(None, 1) == -1
     assert lib.gpfc_set_autotune(None, 1) == -1
     assert lib.gpfc_check_wait_timeout(None, 10000) == -1
+    assert lib.gpfc_peaks(None, None, None, 1, None, 1, 3.0, 4, 1e-3, 8, None, None) == -1
+    assert lib.gpfc_fold_equal_count(None, None, None, 1, None, 1, 4096, 256, 0.0, None) == -1
