@@ -38,7 +38,7 @@ SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, pe
 # DRAM bytes (read + write) of one fold_kernel<box> launch over 19,456 periods of the same
 # light curve, from the ncu capture summarised in profiles/fold_kernel_box_kepler62835.md;
 # scaled to the bench's period count (traffic grows with the number of periods).
-FOLD_DRAM_BYTES_19456 = 1.009152e6 + 18.938880e6
+FOLD_DRAM_BYTES_19456 = 1.048576e6 + 24.092928e6
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -270,6 +270,30 @@ def batched_measurements(g, ctx, flush, stream, args):
     return out
 
 
+def paper_fold_and_decision(g, ctx, lc, periods, t_d, f_d, p_d, score, flush, stream):
+    """The paper's two-tier equal-count fold (4096 fine bins -> 256 bins of n/256 samples)
+    on the same star and grid, and the per-star decision (SDE, peak rule, harmonics) over
+    the box-SNR periodogram of the main step."""
+    import torch
+    n = lc.times.shape[0]
+    out = torch.empty((len(periods), NBINS), dtype=torch.float32, device=ctx.device)
+    ms = timed(lambda: g.gpfc_fold_equal_count(ctx, t_d, f_d, p_d, NBINS, 4096, lc.t0, out), flush, stream)
+    res = {"two_tier_fold": {"ms": ms, "folds_per_s": n * len(periods) / (ms * 1e-3),
+                             "workload": f"same star and grid, 4096 fine bins merged into {NBINS} equal-count bins"}}
+    ms = timed(lambda: g.gpfc_peaks(ctx, score, p_d), flush, stream)
+    sm, pk = g.peaks_to_numpy(*g.gpfc_peaks(ctx, score, p_d), 8)
+    ctx.sync()
+    bi = int(sm[0]["best_index"])
+    res["decision"] = {"ms": ms, "sde": float(sm[0]["sde"]), "n_peaks": int(sm[0]["n_peaks"]),
+                       "best_period_d": float(periods[bi]) if bi >= 0 else None,
+                       "injected_period_d": float(lc.truth["period"]) if hasattr(lc, "truth") and
+                       lc.truth and "period" in lc.truth else None,
+                       "harmonics": [int(h) for h in pk[0]["harmonic"][: int(sm[0]["n_listed"])]],
+                       "workload": "box-SNR periodogram of the main step: SDE, peaks above mean + 3 sd wider "
+                                   "than 3 periods, harmonic flags"}
+    return res
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2312_02063_gb300 as g
@@ -396,6 +420,8 @@ def run_gpu(args, rank, world, local_rank):
         }
         if not args.no_cnn:
             result.update(cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args))
+        if not args.no_cnn:
+            result.update(paper_fold_and_decision(g, ctx, lc, periods, t_d, f_d, p_d, score, flush, stream))
         if args.batch_stars > 0:
             result["batched"] = batched_measurements(g, ctx, flush, stream, args)
         print(json.dumps(result), flush=True)
