@@ -605,10 +605,11 @@ struct LaneBins {
     size_t cbs;
     bool big;
     __device__ __forceinline__ float s(int b) const { return st.sum((uint32_t)b); }
-    __device__ __forceinline__ float c(int b) const
+    __device__ __forceinline__ uint32_t ci(int b) const
     {
-        return big ? (float)Cbig[(size_t)b * cbs] : (float)st.count((uint32_t)b);
+        return big ? Cbig[(size_t)b * cbs] : st.count((uint32_t)b);
     }
+    __device__ __forceinline__ float c(int b) const { return (float)ci(b); }
 };
 
 // Bins of one profile staged transposed for the standalone scorer ([bin][33]).
@@ -618,16 +619,29 @@ struct StagedBins {
     const int32_t *Cbig;   // the caller's counts row when a count exceeds 65535
     bool big;
     __device__ __forceinline__ float s(int b) const { return S[b * 33]; }
-    __device__ __forceinline__ float c(int b) const
+    __device__ __forceinline__ uint32_t ci(int b) const
     {
-        return big ? (float)max(Cbig[b], 0) : (float)C[b * 33];
+        return big ? (uint32_t)max(Cbig[b], 0) : (uint32_t)C[b * 33];
     }
+    __device__ __forceinline__ float c(int b) const { return (float)ci(b); }
 };
+
+// a_hi + a_lo += x with an error-free transformation (Knuth's TwoSum): the pair carries
+// about 48 bits of the running sum
+__device__ __forceinline__ void two_sum_acc(float &a_hi, float &a_lo, float x)
+{
+    const float s = a_hi + x;
+    const float bb = s - a_hi;
+    const float err = (a_hi - (s - bb)) + (x - bb);
+    a_hi = s;
+    a_lo += err;
+}
 
 // Box-SNR search over one profile held by this lane (bin sums centred on a reference,
 // counts). The search maximises
 //     v = (S n_in - S_in N) / sqrt(n_in n_out)      (= snr * sigma * sqrt(N))
-// in FP32 over every circular box of w_min..w_max bins. With the running prefix
+// in FP32 over every circular box of w_min..w_max bins, comparing boxes through
+// v |v| = D |D| / q (D the numerator, q = n_in n_out) by cross-multiplication. With the running prefix
 // A(j) = S Pn(j) - N PS(j) of the bins walked so far, the numerator of a box is
 // A(end) - A(start): one subtraction. R starts s0..s0+R-1 (R = 16, or 8 under a
 // 128-register budget) are scored in one walk over bins s0..s0+R-2+w_max, so every bin
@@ -650,11 +664,14 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
     for (int s0 = 0; s0 < nbins; s0 += R) {
         const bool full = s0 + R <= nbins;
         float bA[R], bN[R];     // prefix values at each start
-        float rv[R];            // best value per start
-        int rt[R];              // its walk step t (width = t - r + 1)
+        // best per start, kept as E = D |D| and q = n_in n_out (v = sign(E) sqrt(|E| / q), so
+        // E1 q2 > E2 q1 orders two boxes as v does without a square root)
+        float rE[R], rq[R];
+        int rt[R];  // walk step t of the best (width = t - r + 1)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            rv[r] = -INFINITY;
+            rE[r] = -INFINITY;
+            rq[r] = 1.f;
             rt[r] = -1;
         }
         float runA = 0.f, runN = 0.f;
@@ -673,9 +690,11 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
         auto eval = [&](int r, int t, bool ok) {
             const float nin = runN - bN[r];
             const float q = nin * (Ntot - nin);
-            const float v = (runA - bA[r]) * rsqrtf(q);
-            const bool take = ok & (q >= 1.f) & (v > rv[r]);
-            rv[r] = take ? v : rv[r];
+            const float D = runA - bA[r];
+            const float E = D * fabsf(D);
+            const bool take = ok & (q >= 1.f) & (E * rq[r] > rE[r] * q);
+            rE[r] = take ? E : rE[r];
+            rq[r] = take ? q : rq[r];
             rt[r] = take ? t : rt[r];
         };
         // head: t = 0..R-1; start r is entered at t = r
@@ -722,9 +741,10 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (rt[r] < 0) continue;
+            const float vr = rE[r] >= 0.f ? sqrtf(rE[r] / rq[r]) : -sqrtf(-rE[r] / rq[r]);
             const int key = ((rt[r] - r + 1) << 12) | (s0 + r);
-            const bool take = (rv[r] > bv) | ((rv[r] == bv) & (key < bkey));
-            bv = take ? rv[r] : bv;
+            const bool take = (vr > bv) | ((vr == bv) & (key < bkey));
+            bv = take ? vr : bv;
             bkey = take ? key : bkey;
         }
     }
@@ -735,19 +755,22 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
         return;
     }
     const int bw = bkey >> 12, bs = bkey & 4095;
-    // FP64 re-evaluation: snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out))
-    double St = 0.0, Nt = 0.0, Si = 0.0, Ni = 0.0;
+    // re-evaluation of the winner, snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out)):
+    // exact integer counts, double-float sums, FP64 for the last few operations
+    float sth = 0.f, stl = 0.f, sih = 0.f, sil = 0.f;
+    uint32_t nt = 0u, ni = 0u;
     for (int b = 0; b < nbins; ++b) {
-        St += (double)B.s(b);
-        Nt += (double)B.c(b);
+        two_sum_acc(sth, stl, B.s(b));
+        nt += B.ci(b);
     }
     int j = bs;
     for (int w = 0; w < bw; ++w) {
-        Si += (double)B.s(j);
-        Ni += (double)B.c(j);
+        two_sum_acc(sih, sil, B.s(j));
+        ni += B.ci(j);
         j = (j + 1 == nbins) ? 0 : j + 1;
     }
-    const double No = Nt - Ni;
+    const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
+    const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
     score = (float)((St * Ni - Si * Nt) / ((double)sigma * sqrt(Nt * Ni * No)));
     best_s = bs;
     best_w = bw;
