@@ -431,36 +431,40 @@ __device__ __forceinline__ int regular_group_size(unsigned long long F, long lon
 // three-stage software pipeline: while the bin reads of group g are in flight, the tile
 // data of group g+2 is fetched and the bins of group g+1 are computed from registers;
 // then group g is written back. Each group's U reads are all issued before its U writes.
+// The loop body holds two stages with swapped register roles, so no register array is
+// copied from one iteration to the next.
 template <bool POW2, class St, int U>
 __device__ __forceinline__ void fold_run_regular(uint32_t stl, uint32_t sth, uint32_t sx, int ng, const St &st,
                                                  uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift)
 {
-    uint32_t b[U];
-    float x[U];
-    TileRegs<U> T1;
-    load_tile_regs<U>(stl, sth, sx, 0, T1);
-    bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, b, x);
-    load_tile_regs<U>(stl, sth, sx, ng > 1 ? U : 0, T1);
-#pragma unroll 1
-    for (int g = 0; g < ng; ++g) {
+    // One pipeline stage: issue the bin reads of the group whose bins are in (cb, cx), fetch
+    // the tile data of group `fetch` into Tn, compute the next group's bins from Tc into
+    // (nb, nx), then write the current group back. Two stages per iteration with the
+    // register roles swapped, so nothing is copied between iterations.
+    auto stage = [&](const uint32_t (&cb)[U], const float (&cx)[U], const TileRegs<U> &Tc, TileRegs<U> &Tn,
+                     uint32_t (&nb)[U], float (&nx)[U], int fetch) {
         float sm[U];
         uint32_t c[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) st.load(b[u], sm[u], c[u]);
-        TileRegs<U> T2;
-        load_tile_regs<U>(stl, sth, sx, U * min(g + 2, ng - 1), T2);
-        uint32_t nb[U];
-        float nx[U];
-        bins_from_regs<POW2, U>(T1, Fl, Fh, nbins, shift, nb, nx);
+        for (int u = 0; u < U; ++u) st.load(cb[u], sm[u], c[u]);
+        load_tile_regs<U>(stl, sth, sx, U * fetch, Tn);
+        bins_from_regs<POW2, U>(Tc, Fl, Fh, nbins, shift, nb, nx);
 #pragma unroll
-        for (int u = 0; u < U; ++u) st.put(b[u], sm[u] + x[u], c[u] + 1u);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            b[u] = nb[u];
-            x[u] = nx[u];
-        }
-        T1 = T2;
+        for (int u = 0; u < U; ++u) st.put(cb[u], sm[u] + cx[u], c[u] + 1u);
+    };
+    uint32_t b0[U], b1[U];
+    float x0[U], x1[U];
+    TileRegs<U> T0, T1;
+    load_tile_regs<U>(stl, sth, sx, 0, T0);
+    bins_from_regs<POW2, U>(T0, Fl, Fh, nbins, shift, b0, x0);  // group 0
+    load_tile_regs<U>(stl, sth, sx, ng > 1 ? U : 0, T1);        // group 1
+    int g = 0;
+#pragma unroll 1
+    for (; g + 1 < ng; g += 2) {
+        stage(b0, x0, T1, T0, b1, x1, min(g + 2, ng - 1));  // write g; bins of g+1; fetch g+2
+        stage(b1, x1, T0, T1, b0, x0, min(g + 3, ng - 1));  // write g+1; bins of g+2; fetch g+3
     }
+    if (g < ng) stage(b0, x0, T1, T0, b1, x1, g);  // the last group (odd count)
 }
 
 // Fold nvalid samples (a segment starting on a 16-sample boundary of the tile) in groups
