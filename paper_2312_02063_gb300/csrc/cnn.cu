@@ -35,9 +35,20 @@ namespace gpfc {
 
 // ------------------------------------------------------------------ layouts
 
-constexpr int kA2Chunk = 132 * 16;   // conv2 input: positions -2..129, 8 channels, BF16
-constexpr int kA2Prof = 2 * kA2Chunk;
-constexpr int kA3Chunk = 68 * 2 * 16;  // conv3 input: positions -2..65 x 2 profiles x 8 channels
+// Activations of conv2's and conv3's inputs are stored as two planes, even and odd
+// positions, each with one halo row on either side, profiles interleaved per row: the
+// input window of pooled output q for pool member j and tap u starts at position
+// 2q + j + u - 2, i.e. plane (j + u) & 1, row q + ((j + u) >> 1) - 1, so one MMA K step
+// (one tap, 16 channels) reads rows 16 bytes apart whatever j and u are.
+constexpr int kA2Rows = 66;                          // conv2 input: plane index -1..64
+constexpr int kA2ChunkB = kA2Rows * 2 * 16;          // [row][profile of the pair][8 channels]
+constexpr int kA2PlaneB = 2 * kA2ChunkB;             // 2 channel chunks
+constexpr int kA2PairB = 2 * kA2PlaneB;              // 2 planes
+constexpr int kA3Rows = 34;                          // conv3 input: plane index -1..32
+constexpr int kA3ChunkB = kA3Rows * 4 * 16;          // [row][profile of the quad][8 channels]
+constexpr int kA3PlaneB = 4 * kA3ChunkB;             // 4 channel chunks
+constexpr int kA1ProfB = 128 * 16;                   // conv1 im2col rows: positions 2q-2 .. 2q+5
+constexpr int kB1Bytes = 32 * 16 * 2;
 constexpr int kB2Bytes = 32 * 80 * 2;
 constexpr int kB3Bytes = 64 * 160 * 2;
 constexpr int kTileBytes = 128 * 64 * 2;  // one fc1 operand block: 128 rows x 64 K
@@ -73,16 +84,24 @@ __global__ void cnn_prep_kernel(CnnSrc src, CnnDev dst)
         dst.wf2[i] = bf16_round(src.wf2[i]);
     }
     if (tid == 0) dst.bf2[0] = src.bf2[0];
-    // conv2 B operand: row n = output channel, K index q*8 + j with q = c*5 + k
-    // (channel chunk c, tap k) and input channel c*8 + j
+    // conv1 B operand: row n = j * 16 + co (pool member j: position 2q + j), K index u = tap
+    // offset into the 8-position im2col row 2q-2 .. 2q+5: weight w1[co][u - j] where it exists
+    for (int i = tid; i < 32 * 16; i += stride) {
+        const int n = i / 16, u = i % 16, jj = n >> 4, co = n & 15, k = u - jj;
+        const float v = (k >= 0 && k < 5) ? src.w1[co * 5 + k] : 0.f;
+        *reinterpret_cast<uint16_t *>(dst.B1 + canon(n, u, 128, 256)) = bf16_bits(v);
+    }
+    // conv2 B operand: row n = output channel, K index q*8 + e with q = k*2 + c
+    // (tap k, channel chunk c) and input channel c*8 + e
     for (int i = tid; i < 32 * 80; i += stride) {
-        const int n = i / 80, kk = i % 80, q = kk >> 3, j = kk & 7, c = q / 5, k = q % 5;
-        const float v = src.w2[(n * 16 + c * 8 + j) * 5 + k];
+        const int n = i / 80, kk = i % 80, q = kk >> 3, e = kk & 7, k = q >> 1, c = q & 1;
+        const float v = src.w2[(n * 16 + c * 8 + e) * 5 + k];
         *reinterpret_cast<uint16_t *>(dst.B2 + canon(n, kk, 128, 1280)) = bf16_bits(v);
     }
+    // conv3: q = k*4 + c
     for (int i = tid; i < 64 * 160; i += stride) {
-        const int n = i / 160, kk = i % 160, q = kk >> 3, j = kk & 7, c = q / 5, k = q % 5;
-        const float v = src.w3[(n * 32 + c * 8 + j) * 5 + k];
+        const int n = i / 160, kk = i % 160, q = kk >> 3, e = kk & 7, k = q >> 2, c = q & 3;
+        const float v = src.w3[(n * 32 + c * 8 + e) * 5 + k];
         *reinterpret_cast<uint16_t *>(dst.B3 + canon(n, kk, 128, 2560)) = bf16_bits(v);
     }
     // fc1 weights, K chunk kc = pooled position l', K index kk = channel c:
@@ -97,35 +116,60 @@ __global__ void cnn_prep_kernel(CnnSrc src, CnnDev dst)
 // ------------------------------------------------------------------ conv kernel
 
 struct ConvSmem {
+    uint8_t B1[kB1Bytes];
     uint8_t B2[kB2Bytes];
     uint8_t B3[kB3Bytes];
-    uint8_t A2[2 * kA2Prof];
-    uint8_t A3[4 * kA3Chunk];
-    float X[2][256];
-    float w1[80];
+    uint8_t A1[4][kA1ProfB];      // conv1 im2col, one per profile of the quad
+    uint8_t A1zero[kA1ProfB];     // K chunk 1 of conv1 (taps 8..15): zeros
+    uint8_t A2[2][kA2PairB];      // conv2 input of each pair of the quad
+    uint8_t A3[2 * kA3PlaneB];    // conv3 input of the quad
+    uint16_t X[4][256];           // normalised inputs (BF16)
     float b1[16];
     float b2[32];
     float b3[64];
-    float red[2][6];
     uint64_t bar;
     uint32_t tslot;
     int abort;
 };
 
 constexpr int kConvThreads = 128;
+constexpr int kConvProfiles = 4;  // profiles per block iteration
 
-__global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvParams p)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
+}
+
+// Issue the MMAs of one stage and wait for them (thread 0 issues; everyone waits).
+#define CONV_MMA_WAIT(...)                                                                         \
+    do {                                                                                          \
+        fence_proxy_async_smem();                                                                 \
+        tc_fence_before();                                                                        \
+        __syncthreads();                                                                          \
+        tc_fence_after();                                                                         \
+        if (tid == 0) {                                                                           \
+            __VA_ARGS__;                                                                          \
+            umma_commit(&S.bar);                                                                  \
+        }                                                                                         \
+        if (!mbar_wait_bounded(&S.bar, phase)) S.abort = 1;                                       \
+        phase ^= 1u;                                                                              \
+        tc_fence_after();                                                                         \
+    } while (0)
+
+__global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConvParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     ConvSmem &S = *reinterpret_cast<ConvSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // stage the weights once per block
+    for (int i = tid; i < kB1Bytes / 16; i += kConvThreads)
+        reinterpret_cast<uint4 *>(S.B1)[i] = reinterpret_cast<const uint4 *>(p.w.B1)[i];
     for (int i = tid; i < kB2Bytes / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(S.B2)[i] = reinterpret_cast<const uint4 *>(p.w.B2)[i];
     for (int i = tid; i < kB3Bytes / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(S.B3)[i] = reinterpret_cast<const uint4 *>(p.w.B3)[i];
-    for (int i = tid; i < 80; i += kConvThreads) S.w1[i] = p.w.w1[i];
+    for (int i = tid; i < kA1ProfB / 16; i += kConvThreads) reinterpret_cast<uint4 *>(S.A1zero)[i] = make_uint4(0, 0, 0, 0);
     if (tid < 16) S.b1[tid] = p.w.b1[tid];
     if (tid < 32) S.b2[tid] = p.w.b2[tid];
     if (tid < 64) S.b3[tid] = p.w.b3[tid];
@@ -140,35 +184,49 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tslot;
+    const uint32_t tlane = (uint32_t)(warp * 32) << 16;
     uint32_t phase = 0u;
-    const int64_t npairs = (p.np + 1) / 2;
+    const int64_t nquads = (p.np + kConvProfiles - 1) / kConvProfiles;
 
-    for (int64_t pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
-        const int64_t k0 = p.k_begin + 2 * pair;  // global index of the pair's first profile
-        // ---- load and noise-normalise two profiles (64 threads per profile, 4 bins each)
+    for (int64_t quad = blockIdx.x; quad < nquads; quad += gridDim.x) {
+        const int64_t l0 = kConvProfiles * quad;  // local index of the quad's first profile
+        // ---- noise normalisation (Sec. 2.1): warp w takes profile w, 8 bins per lane
         {
-            const int prof = tid >> 6, q = tid & 63;
-            const int64_t k = k0 + prof;
-            const bool valid = (k - p.k_begin) < p.np;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            bool ne[4] = {false, false, false, false};
-            if (valid) {
-                const float4 f = *reinterpret_cast<const float4 *>(p.folded + (size_t)k * 256 + 4 * q);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-                if (p.counts) {
-                    const int4 c = *reinterpret_cast<const int4 *>(p.counts + (size_t)k * 256 + 4 * q);
-                    ne[0] = c.x > 0; ne[1] = c.y > 0; ne[2] = c.z > 0; ne[3] = c.w > 0;
-                } else {
+            const int64_t kl = l0 + warp;
+            const bool valid = kl < p.np;
+            const int64_t k = p.k_begin + kl;
+            float v[8];
+            bool ne[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) ne[u] = !(v[u] != v[u]);
+            for (int u = 0; u < 8; ++u) {
+                v[u] = 0.f;
+                ne[u] = false;
+            }
+            if (valid) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 f = *reinterpret_cast<const float4 *>(p.folded + (size_t)k * 256 + 8 * lane + 4 * h);
+                    v[4 * h] = f.x;
+                    v[4 * h + 1] = f.y;
+                    v[4 * h + 2] = f.z;
+                    v[4 * h + 3] = f.w;
+                    if (p.counts) {
+                        const int4 c = *reinterpret_cast<const int4 *>(p.counts + (size_t)k * 256 + 8 * lane + 4 * h);
+                        ne[4 * h] = c.x > 0;
+                        ne[4 * h + 1] = c.y > 0;
+                        ne[4 * h + 2] = c.z > 0;
+                        ne[4 * h + 3] = c.w > 0;
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) ne[4 * h + u] = !(v[4 * h + u] != v[4 * h + u]);
+                    }
                 }
             }
-            // FP32 throughout (this GPU's FP64 rate is tiny): the sum of the values is
-            // compensated (TwoSum), the deviations v - m are small and exact-ish in FP32,
-            // and one reciprocal standard deviation per profile scales them.
+            // FP32 throughout: the sum is compensated (TwoSum), the deviations v - m are
+            // small, and one reciprocal standard deviation per profile scales them
             float sh = 0.f, sl = 0.f, cnt = 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
                 if (ne[u]) {
                     const float t = sh + v[u];
                     const float bb = t - sh;
@@ -185,216 +243,204 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_kernel(const CnnConvPar
                 sl += ol + ((sh - (t - bb)) + (oh - bb));
                 sh = t;
             }
-            if (lane == 0) {
-                S.red[prof][(warp & 1) * 3 + 0] = sh;
-                S.red[prof][(warp & 1) * 3 + 1] = sl;
-                S.red[prof][(warp & 1) * 3 + 2] = cnt;
-            }
-            __syncthreads();
-            const float n = S.red[prof][2] + S.red[prof][5];
-            float m = 0.f;
-            if (n > 0.f) {
-                const float t = S.red[prof][0] + S.red[prof][3];
-                const float bb = t - S.red[prof][0];
-                const float lo = S.red[prof][1] + S.red[prof][4] + ((S.red[prof][0] - (t - bb)) + (S.red[prof][3] - bb));
-                m = (t + lo) / n;
-            }
-            float d[4], ss = 0.f;
+            const float m = cnt > 0.f ? (sh + sl) / cnt : 0.f;
+            float d[8], ss = 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 d[u] = ne[u] ? v[u] - m : 0.f;
                 ss = fmaf(d[u], d[u], ss);
             }
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            __syncthreads();
-            if (lane == 0) S.red[prof][(warp & 1) * 3] = ss;
-            __syncthreads();
-            const float var = n > 0.f ? (S.red[prof][0] + S.red[prof][3]) / n : 0.f;
+            const float var = cnt > 0.f ? ss / cnt : 0.f;
             const float inv_sd = var > 0.f ? 1.0f / sqrtf(var) : 0.f;
+            uint32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float x = (inv_sd > 0.f && ne[u]) ? fmaf(d[u], inv_sd, m) : m;
-                S.X[prof][4 * q + u] = bf16_round(x);
+            for (int u = 0; u < 8; u += 2) {
+                const float x0 = (inv_sd > 0.f && ne[u]) ? fmaf(d[u], inv_sd, m) : m;
+                const float x1 = (inv_sd > 0.f && ne[u + 1]) ? fmaf(d[u + 1], inv_sd, m) : m;
+                w[u >> 1] = pack_bf16(x0, x1);
             }
+            *reinterpret_cast<uint4 *>(&S.X[warp][8 * lane]) = make_uint4(w[0], w[1], w[2], w[3]);
             if (p.xsave && valid) {
                 // normalised BF16 input, kept for the backward pass
 #pragma unroll
-                for (int u = 0; u < 4; ++u) p.xsave[(size_t)(k - p.k_begin) * 256 + 4 * q + u] = S.X[prof][4 * q + u];
+                for (int u = 0; u < 8; ++u)
+                    p.xsave[(size_t)kl * 256 + 8 * lane + u] =
+                        __bfloat162float(__ushort_as_bfloat16((uint16_t)(w[u >> 1] >> (16 * (u & 1)))));
             }
         }
         __syncthreads();
-        // ---- conv1 on CUDA cores: thread -> profile, pooled positions 2lp and 2lp+1
+        // ---- conv1 im2col: thread q builds row q (input positions 2q-2 .. 2q+5) of each profile
         {
-            const int prof = tid >> 6, lp = tid & 63;
-            float in[8];
+            const int q = tid;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) in[j] = S.X[prof][(4 * lp - 2 + j + 256) & 255];
-            uint16_t h[2][16];
+            for (int pp = 0; pp < kConvProfiles; ++pp) {
+                uint32_t w[4];
 #pragma unroll
-            for (int co = 0; co < 16; ++co) {
-                float a[4];
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    float acc = S.b1[co];
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) acc = fmaf(S.w1[co * 5 + k], in[l + k], acc);
-                    if (p.a1save && (k0 + prof - p.k_begin) < p.np)
-                        p.a1save[((size_t)(k0 + prof - p.k_begin) * 16 + co) * 256 + 4 * lp + l] = acc;
-                    a[l] = fmaxf(acc, 0.f);
-                }
-                h[0][co] = bf16_bits(fmaxf(a[0], a[1]));
-                h[1][co] = bf16_bits(fmaxf(a[2], a[3]));
+                for (int h = 0; h < 4; ++h)
+                    w[h] = (uint32_t)S.X[pp][(2 * q - 2 + 2 * h) & 255] |
+                           ((uint32_t)S.X[pp][(2 * q - 1 + 2 * h) & 255] << 16);
+                *reinterpret_cast<uint4 *>(S.A1[pp] + q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            uint8_t *A2 = S.A2 + prof * kA2Prof;
+        }
+        // ---- conv1: per profile M = 128 pooled positions, N = 32 (pool member, channel), K = 16
+        CONV_MMA_WAIT({
+            const uint32_t idesc = umma_idesc_bf16(128, 32);
+            const uint64_t bd = umma_desc(smem_u32(S.B1), 128, 256);
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int lq = 2 * lp + t;  // pooled position 0..127
+            for (int pp = 0; pp < kConvProfiles; ++pp) {
+                const uint32_t a = smem_u32(S.A1[pp]);
+                umma_bf16(tmem + 32 * pp, umma_desc(a, smem_u32(S.A1zero) - a, 128), bd, idesc, false);
+            }
+        });
+        // ---- conv1 epilogue: bias, ReLU, pool the two members in registers, write conv2 input
+        {
+            const int q = tid;  // pooled position 0..127
+#pragma unroll 1
+            for (int pp = 0; pp < kConvProfiles; ++pp) {
+                const int64_t kl = l0 + pp;
+                const bool valid = kl < p.np;
+                float v[32];
+                tmem_ld32(tmem + tlane + 32 * pp, v);
+                uint32_t h[8];
+#pragma unroll
+                for (int co = 0; co < 16; co += 2) {
+                    const float a00 = v[co] + S.b1[co], a01 = v[16 + co] + S.b1[co];
+                    const float a10 = v[co + 1] + S.b1[co + 1], a11 = v[17 + co] + S.b1[co + 1];
+                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                    if (p.a1save && valid) {
+                        float *a1 = p.a1save + ((size_t)kl * 16 + co) * 256 + 2 * q;
+                        a1[0] = a00;
+                        a1[1] = a01;
+                        a1[256] = a10;
+                        a1[257] = a11;
+                    }
+                }
+                if (p.h1save && valid)
+#pragma unroll
+                    for (int co = 0; co < 16; ++co)
+                        p.h1save[((size_t)kl * 16 + co) * 128 + q] = (uint16_t)(h[co >> 1] >> (16 * (co & 1)));
+                uint8_t *A2 = S.A2[pp >> 1] + (q & 1) * kA2PlaneB + (pp & 1) * 16;
+                const int row = (q >> 1) + 1;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    uint4 w;
-                    w.x = h[t][8 * c + 0] | ((uint32_t)h[t][8 * c + 1] << 16);
-                    w.y = h[t][8 * c + 2] | ((uint32_t)h[t][8 * c + 3] << 16);
-                    w.z = h[t][8 * c + 4] | ((uint32_t)h[t][8 * c + 5] << 16);
-                    w.w = h[t][8 * c + 6] | ((uint32_t)h[t][8 * c + 7] << 16);
-                    *reinterpret_cast<uint4 *>(A2 + c * kA2Chunk + (lq + 2) * 16) = w;
-                    if (lq >= 126) *reinterpret_cast<uint4 *>(A2 + c * kA2Chunk + (lq - 126) * 16) = w;
-                    if (lq <= 1) *reinterpret_cast<uint4 *>(A2 + c * kA2Chunk + (lq + 130) * 16) = w;
-                }
-                if (p.h1save) {
-                    const int64_t k = k0 + prof;
-                    if ((k - p.k_begin) < p.np)
-                        for (int co = 0; co < 16; ++co)
-                            p.h1save[((size_t)(k - p.k_begin) * 16 + co) * 128 + lq] = h[t][co];
+                    const uint4 w = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                    *reinterpret_cast<uint4 *>(A2 + c * kA2ChunkB + row * 32) = w;
+                    if (q >= 126) *reinterpret_cast<uint4 *>(A2 + c * kA2ChunkB) = w;                   // row -1
+                    if (q <= 1) *reinterpret_cast<uint4 *>(A2 + c * kA2ChunkB + (kA2Rows - 1) * 32) = w;  // row 64
                 }
             }
         }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // ---- conv2: two implicit GEMMs (one per profile), M = 128, N = 32, K = 80
-        if (tid == 0) {
+        // ---- conv2: per pair, M = 64 pooled positions x 2 profiles, N = 32, K = 80, one
+        // accumulator per pool member
+        CONV_MMA_WAIT({
             const uint32_t idesc = umma_idesc_bf16(128, 32);
 #pragma unroll
-            for (int prof = 0; prof < 2; ++prof) {
-                const uint32_t abase = smem_u32(S.A2 + prof * kA2Prof);
+            for (int g = 0; g < 2; ++g)
 #pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const int q0 = 2 * i, q1 = 2 * i + 1;
-                    const uint32_t o0 = (q0 / 5) * kA2Chunk + (q0 % 5) * 16;
-                    const uint32_t o1 = (q1 / 5) * kA2Chunk + (q1 % 5) * 16;
-                    const uint64_t ad = umma_desc(abase + o0, o1 - o0, 128);
-                    const uint64_t bd = umma_desc(smem_u32(S.B2) + i * 256, 128, 1280);
-                    umma_bf16(tmem + prof * 32, ad, bd, idesc, i > 0);
-                }
-            }
-            umma_commit(&S.bar);
-        }
-        if (!mbar_wait_bounded(&S.bar, phase)) S.abort = 1;
-        phase ^= 1u;
-        tc_fence_after();
-        // ---- conv2 epilogue: bias, ReLU, pool lanes (l, l+1), write conv3's input
+                for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                    for (int u = 0; u < 5; ++u) {
+                        const int sft = jj + u;
+                        const uint32_t a = smem_u32(S.A2[g]) + (sft & 1) * kA2PlaneB + (sft >> 1) * 32;
+                        const uint64_t ad = umma_desc(a, kA2ChunkB, 128);
+                        const uint64_t bd = umma_desc(smem_u32(S.B2) + u * 256, 128, 1280);
+                        umma_bf16(tmem + g * 64 + jj * 32, ad, bd, idesc, u > 0);
+                    }
+        });
+        // ---- conv2 epilogue: row m = (pooled position m >> 1, profile m & 1 of the pair)
         {
-            const int l = warp * 32 + lane;  // output position 0..127
+            const int m = tid, q = m >> 1, pr = m & 1;
 #pragma unroll 1
-            for (int prof = 0; prof < 2; ++prof) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + prof * 32, v);
-                uint16_t h[32];
+            for (int g = 0; g < 2; ++g) {
+                const int pp = 2 * g + pr;
+                const int64_t kl = l0 + pp;
+                const bool valid = kl < p.np;
+                float v0[32], v1[32];
+                tmem_ld32(tmem + tlane + g * 64, v0);
+                tmem_ld32(tmem + tlane + g * 64 + 32, v1);
+                uint32_t h[16];
 #pragma unroll
-                for (int co = 0; co < 32; ++co) {
-                    const float a = fmaxf(v[co] + S.b2[co], 0.f);
-                    const float o = __shfl_xor_sync(0xffffffffu, a, 1);
-                    h[co] = bf16_bits(fmaxf(a, o));
-                }
-                if ((l & 1) == 0) {
-                    const int lq = l >> 1;  // 0..63
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        uint4 w;
-                        w.x = h[8 * c + 0] | ((uint32_t)h[8 * c + 1] << 16);
-                        w.y = h[8 * c + 2] | ((uint32_t)h[8 * c + 3] << 16);
-                        w.z = h[8 * c + 4] | ((uint32_t)h[8 * c + 5] << 16);
-                        w.w = h[8 * c + 6] | ((uint32_t)h[8 * c + 7] << 16);
-                        uint8_t *A3 = S.A3 + c * kA3Chunk + prof * 16;
-                        *reinterpret_cast<uint4 *>(A3 + (lq + 2) * 32) = w;
-                        if (lq >= 62) *reinterpret_cast<uint4 *>(A3 + (lq - 62) * 32) = w;
-                        if (lq <= 1) *reinterpret_cast<uint4 *>(A3 + (lq + 66) * 32) = w;
-                    }
-                    if (p.h2save) {
-                        const int64_t k = k0 + prof;
-                        if ((k - p.k_begin) < p.np)
-                            for (int co = 0; co < 32; ++co)
-                                p.h2save[((size_t)(k - p.k_begin) * 32 + co) * 64 + lq] = h[co];
+                for (int co = 0; co < 32; co += 2) {
+                    const float a00 = v0[co] + S.b2[co], a01 = v1[co] + S.b2[co];
+                    const float a10 = v0[co + 1] + S.b2[co + 1], a11 = v1[co + 1] + S.b2[co + 1];
+                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                    if (p.a2save && valid) {
+                        float *a2 = p.a2save + ((size_t)kl * 32 + co) * 128 + 2 * q;
+                        a2[0] = a00;
+                        a2[1] = a01;
+                        a2[128] = a10;
+                        a2[129] = a11;
                     }
                 }
-                if (p.a2save) {
-                    // pre-activation of conv2 (with bias), for the ReLU/pool backward
-                    const int64_t k = k0 + prof;
-                    if ((k - p.k_begin) < p.np)
-                        for (int co = 0; co < 32; ++co)
-                            p.a2save[((size_t)(k - p.k_begin) * 32 + co) * 128 + l] = v[co] + S.b2[co];
+                if (p.h2save && valid)
+#pragma unroll
+                    for (int co = 0; co < 32; ++co)
+                        p.h2save[((size_t)kl * 32 + co) * 64 + q] = (uint16_t)(h[co >> 1] >> (16 * (co & 1)));
+                uint8_t *A3 = S.A3 + (q & 1) * kA3PlaneB + pp * 16;
+                const int row = (q >> 1) + 1;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint4 w = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                    *reinterpret_cast<uint4 *>(A3 + c * kA3ChunkB + row * 64) = w;
+                    if (q >= 62) *reinterpret_cast<uint4 *>(A3 + c * kA3ChunkB) = w;                   // row -1
+                    if (q <= 1) *reinterpret_cast<uint4 *>(A3 + c * kA3ChunkB + (kA3Rows - 1) * 64) = w;  // row 32
                 }
             }
         }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // ---- conv3: one implicit GEMM, M = 64 positions x 2 profiles, N = 64, K = 160
-        if (tid == 0) {
+        // ---- conv3: M = 32 pooled positions x 4 profiles, N = 64, K = 160, one accumulator
+        // per pool member
+        CONV_MMA_WAIT({
             const uint32_t idesc = umma_idesc_bf16(128, 64);
-            const uint32_t abase = smem_u32(S.A3);
 #pragma unroll
-            for (int i = 0; i < 10; ++i) {
-                const int q0 = 2 * i, q1 = 2 * i + 1;
-                const uint32_t o0 = (q0 / 5) * kA3Chunk + (q0 % 5) * 32;
-                const uint32_t o1 = (q1 / 5) * kA3Chunk + (q1 % 5) * 32;
-                const uint64_t ad = umma_desc(abase + o0, o1 - o0, 128);
-                const uint64_t bd = umma_desc(smem_u32(S.B3) + i * 256, 128, 2560);
-                umma_bf16(tmem + 64, ad, bd, idesc, i > 0);
-            }
-            umma_commit(&S.bar);
-        }
-        if (!mbar_wait_bounded(&S.bar, phase)) S.abort = 1;
-        phase ^= 1u;
-        tc_fence_after();
-        // ---- conv3 epilogue: row m = (position m / 2, profile m % 2); pool rows m, m ^ 2
+            for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                for (int u = 0; u < 5; ++u)
+#pragma unroll
+                    for (int cp = 0; cp < 2; ++cp) {
+                        const int sft = jj + u;
+                        const uint32_t a =
+                            smem_u32(S.A3) + (sft & 1) * kA3PlaneB + 2 * cp * kA3ChunkB + (sft >> 1) * 64;
+                        const uint64_t ad = umma_desc(a, kA3ChunkB, 128);
+                        const uint64_t bd = umma_desc(smem_u32(S.B3) + (4 * u + 2 * cp) * 128, 128, 2560);
+                        umma_bf16(tmem + jj * 64, ad, bd, idesc, u > 0 || cp > 0);
+                    }
+        });
+        // ---- conv3 epilogue: row m = (pooled position m >> 2, profile m & 3); write the fc1
+        // operand tile (feature = position * 64 + channel)
         {
-            const int m = warp * 32 + lane, l = m >> 1, prof = m & 1;
-            const int64_t k = k0 + prof;
-            const bool valid = (k - p.k_begin) < p.np;
-            uint16_t h[64];
+            const int m = tid, q = m >> 2, pp = m & 3;
+            const int64_t kl = l0 + pp;
+            const bool valid = kl < p.np;
+            uint32_t h[32];
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 64 + half * 32, v);
+                float v0[32], v1[32];
+                tmem_ld32(tmem + tlane + half * 32, v0);
+                tmem_ld32(tmem + tlane + 64 + half * 32, v1);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < 32; j += 2) {
                     const int co = half * 32 + j;
-                    const float pre = v[j] + S.b3[co];
-                    const float a = fmaxf(pre, 0.f);
-                    const float o = __shfl_xor_sync(0xffffffffu, a, 2);
-                    h[co] = bf16_bits(fmaxf(a, o));
-                    if (p.a3save && valid)
-                        p.a3save[((size_t)(k - p.k_begin) * 64 + co) * 64 + l] = pre;
+                    const float a00 = v0[j] + S.b3[co], a01 = v1[j] + S.b3[co];
+                    const float a10 = v0[j + 1] + S.b3[co + 1], a11 = v1[j + 1] + S.b3[co + 1];
+                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                    if (p.a3save && valid) {
+                        float *a3 = p.a3save + ((size_t)kl * 64 + co) * 64 + 2 * q;
+                        a3[0] = a00;
+                        a3[1] = a01;
+                        a3[64] = a10;
+                        a3[65] = a11;
+                    }
                 }
             }
-            if ((l & 1) == 0 && valid) {
-                const int lq = l >> 1;  // pooled position 0..31 = fc1 K chunk
-                const int64_t kl = k - p.k_begin;
+            if (valid) {
                 const int64_t mt = kl >> 7;
                 const int r = (int)(kl & 127);
-                uint8_t *blk = p.h3t + ((size_t)mt * 32 + lq) * kTileBytes;
+                uint8_t *blk = p.h3t + ((size_t)mt * 32 + q) * kTileBytes;
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    uint4 w;
-                    w.x = h[8 * cc + 0] | ((uint32_t)h[8 * cc + 1] << 16);
-                    w.y = h[8 * cc + 2] | ((uint32_t)h[8 * cc + 3] << 16);
-                    w.z = h[8 * cc + 4] | ((uint32_t)h[8 * cc + 5] << 16);
-                    w.w = h[8 * cc + 6] | ((uint32_t)h[8 * cc + 7] << 16);
-                    *reinterpret_cast<uint4 *>(blk + canon(r, 8 * cc, 128, 1024)) = w;
-                }
+                for (int cc = 0; cc < 8; ++cc)
+                    *reinterpret_cast<uint4 *>(blk + canon(r, 8 * cc, 128, 1024)) =
+                        make_uint4(h[4 * cc], h[4 * cc + 1], h[4 * cc + 2], h[4 * cc + 3]);
             }
         }
         tc_fence_before();
@@ -568,6 +614,7 @@ CnnDev cnn_dev_carve(void *base)
     d.bf1 = reinterpret_cast<float *>(b + CnnDevLayout::bf1);
     d.wf2 = reinterpret_cast<float *>(b + CnnDevLayout::wf2);
     d.bf2 = reinterpret_cast<float *>(b + CnnDevLayout::bf2);
+    d.B1 = b + CnnDevLayout::B1;
     d.B2 = b + CnnDevLayout::B2;
     d.B3 = b + CnnDevLayout::B3;
     d.W1t = b + CnnDevLayout::W1t;
@@ -601,9 +648,9 @@ cudaError_t launch_cnn_conv(const CnnConvParams &p, int num_sms, cudaStream_t st
 {
     cudaError_t e = cnn_register_kernels();
     if (e != cudaSuccess) return e;
-    const int64_t npairs = (p.np + 1) / 2;
-    // at most 4 blocks per SM: each holds 128 of the SM's 512 TMEM columns
-    const int grid = (int)(npairs < (int64_t)num_sms * 4 ? npairs : (int64_t)num_sms * 4);
+    const int64_t nquads = (p.np + kConvProfiles - 1) / kConvProfiles;
+    // three blocks per SM fit in shared memory (each holds 128 of the SM's 512 TMEM columns)
+    const int grid = (int)(nquads < (int64_t)num_sms * 3 ? nquads : (int64_t)num_sms * 3);
     cnn_conv_kernel<<<grid, kConvThreads, conv_smem_bytes(), st>>>(p);
     return cudaGetLastError();
 }

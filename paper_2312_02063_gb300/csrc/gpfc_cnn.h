@@ -18,6 +18,7 @@ struct CnnSrc {
 // Device copies in the layouts the kernels read (weights rounded to BF16).
 struct CnnDev {
     float *w1, *b1, *b2, *b3, *bf1, *wf2, *bf2;
+    uint8_t *B1;   // conv1 weights for both pool members, operand layout (32 x 16 BF16)
     uint8_t *B2;   // conv2 weights, tensor-core operand layout (32 x 80 BF16)
     uint8_t *B3;   // conv3 weights (64 x 160 BF16)
     uint8_t *W1t;  // fc1 weights, 32 K chunks of 256 x 64 BF16
@@ -33,6 +34,7 @@ struct CnnDevLayout {
     static constexpr size_t bf2 = 4096;
     static constexpr size_t B2 = 8192;
     static constexpr size_t B3 = B2 + 32 * 80 * 2;
+    static constexpr size_t B1 = B3 + 64 * 160 * 2;
     static constexpr size_t W1t = 65536;
     static constexpr size_t total() { return W1t + (size_t)256 * 2048 * 2; }
 };
