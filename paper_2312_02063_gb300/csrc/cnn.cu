@@ -140,6 +140,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
 }
 
+// ReLU(max(a0, a1) + b) of two channels, rounded to BF16 and packed (low half = first):
+// pooling before the bias gives the same value as pooling the biased members, and ReLU
+// commutes with the (monotone) rounding.
+__device__ __forceinline__ uint32_t pool_bias_relu2(float a00, float a01, float a10, float a11, float2 b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a00, a01) + b.x, fmaxf(a10, a11) + b.y);
+    const __nv_bfloat162 r = __hmax2(h, __float2bfloat162_rn(0.f));
+    return *reinterpret_cast<const uint32_t *>(&r);
+}
+
 // Issue the MMAs of one stage and wait for them (thread 0 issues; everyone waits).
 #define CONV_MMA_WAIT(...)                                                                         \
     do {                                                                                          \
@@ -190,6 +200,16 @@ __global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConv
 
     for (int64_t quad = blockIdx.x; quad < nquads; quad += gridDim.x) {
         const int64_t l0 = kConvProfiles * quad;  // local index of the quad's first profile
+        {
+            // pull the next quad's means and counts (8 KB) toward L2 while this quad runs
+            const int64_t ln = l0 + kConvProfiles * (int64_t)gridDim.x;
+            const int64_t pl = ln + (tid & 63) / 16;  // 16 lines of 128 bytes per 1 KB row
+            if (pl < p.np) {
+                const size_t off = (size_t)(p.k_begin + pl) * 256 + (size_t)(tid & 15) * 32;
+                if (tid < 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.folded + off));
+                else if (p.counts) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.counts + off));
+            }
+        }
         // ---- noise normalisation (Sec. 2.1): warp w takes profile w, 8 bins per lane
         {
             const int64_t kl = l0 + warp;
@@ -303,17 +323,24 @@ __global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConv
                 float v[32];
                 tmem_ld32(tmem + tlane + 32 * pp, v);
                 uint32_t h[8];
+                if (!p.a1save) {
 #pragma unroll
-                for (int co = 0; co < 16; co += 2) {
-                    const float a00 = v[co] + S.b1[co], a01 = v[16 + co] + S.b1[co];
-                    const float a10 = v[co + 1] + S.b1[co + 1], a11 = v[17 + co] + S.b1[co + 1];
-                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
-                    if (p.a1save && valid) {
-                        float *a1 = p.a1save + ((size_t)kl * 16 + co) * 256 + 2 * q;
-                        a1[0] = a00;
-                        a1[1] = a01;
-                        a1[256] = a10;
-                        a1[257] = a11;
+                    for (int co = 0; co < 16; co += 2)
+                        h[co >> 1] = pool_bias_relu2(v[co], v[16 + co], v[co + 1], v[17 + co],
+                                                     *reinterpret_cast<const float2 *>(&S.b1[co]));
+                } else {
+#pragma unroll
+                    for (int co = 0; co < 16; co += 2) {
+                        const float a00 = v[co] + S.b1[co], a01 = v[16 + co] + S.b1[co];
+                        const float a10 = v[co + 1] + S.b1[co + 1], a11 = v[17 + co] + S.b1[co + 1];
+                        h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                        if (valid) {
+                            float *a1 = p.a1save + ((size_t)kl * 16 + co) * 256 + 2 * q;
+                            a1[0] = a00;
+                            a1[1] = a01;
+                            a1[256] = a10;
+                            a1[257] = a11;
+                        }
                     }
                 }
                 if (p.h1save && valid)
@@ -360,17 +387,24 @@ __global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConv
                 tmem_ld32(tmem + tlane + g * 64, v0);
                 tmem_ld32(tmem + tlane + g * 64 + 32, v1);
                 uint32_t h[16];
+                if (!p.a2save) {
 #pragma unroll
-                for (int co = 0; co < 32; co += 2) {
-                    const float a00 = v0[co] + S.b2[co], a01 = v1[co] + S.b2[co];
-                    const float a10 = v0[co + 1] + S.b2[co + 1], a11 = v1[co + 1] + S.b2[co + 1];
-                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
-                    if (p.a2save && valid) {
-                        float *a2 = p.a2save + ((size_t)kl * 32 + co) * 128 + 2 * q;
-                        a2[0] = a00;
-                        a2[1] = a01;
-                        a2[128] = a10;
-                        a2[129] = a11;
+                    for (int co = 0; co < 32; co += 2)
+                        h[co >> 1] = pool_bias_relu2(v0[co], v1[co], v0[co + 1], v1[co + 1],
+                                                     *reinterpret_cast<const float2 *>(&S.b2[co]));
+                } else {
+#pragma unroll
+                    for (int co = 0; co < 32; co += 2) {
+                        const float a00 = v0[co] + S.b2[co], a01 = v1[co] + S.b2[co];
+                        const float a10 = v0[co + 1] + S.b2[co + 1], a11 = v1[co + 1] + S.b2[co + 1];
+                        h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                        if (valid) {
+                            float *a2 = p.a2save + ((size_t)kl * 32 + co) * 128 + 2 * q;
+                            a2[0] = a00;
+                            a2[1] = a01;
+                            a2[128] = a10;
+                            a2[129] = a11;
+                        }
                     }
                 }
                 if (p.h2save && valid)
@@ -418,18 +452,25 @@ __global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConv
                 float v0[32], v1[32];
                 tmem_ld32(tmem + tlane + half * 32, v0);
                 tmem_ld32(tmem + tlane + 64 + half * 32, v1);
+                if (!p.a3save) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const int co = half * 32 + j;
-                    const float a00 = v0[j] + S.b3[co], a01 = v1[j] + S.b3[co];
-                    const float a10 = v0[j + 1] + S.b3[co + 1], a11 = v1[j + 1] + S.b3[co + 1];
-                    h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
-                    if (p.a3save && valid) {
-                        float *a3 = p.a3save + ((size_t)kl * 64 + co) * 64 + 2 * q;
-                        a3[0] = a00;
-                        a3[1] = a01;
-                        a3[64] = a10;
-                        a3[65] = a11;
+                    for (int j = 0; j < 32; j += 2)
+                        h[(half * 32 + j) >> 1] = pool_bias_relu2(v0[j], v1[j], v0[j + 1], v1[j + 1],
+                                                                  *reinterpret_cast<const float2 *>(&S.b3[half * 32 + j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const int co = half * 32 + j;
+                        const float a00 = v0[j] + S.b3[co], a01 = v1[j] + S.b3[co];
+                        const float a10 = v0[j + 1] + S.b3[co + 1], a11 = v1[j + 1] + S.b3[co + 1];
+                        h[co >> 1] = pack_bf16(fmaxf(fmaxf(a00, a01), 0.f), fmaxf(fmaxf(a10, a11), 0.f));
+                        if (valid) {
+                            float *a3 = p.a3save + ((size_t)kl * 64 + co) * 64 + 2 * q;
+                            a3[0] = a00;
+                            a3[1] = a01;
+                            a3[64] = a10;
+                            a3[65] = a11;
+                        }
                     }
                 }
             }
@@ -461,15 +502,17 @@ __global__ void __launch_bounds__(kConvThreads, 3) cnn_conv_kernel(const CnnConv
 
 // ------------------------------------------------------------------ fc kernel
 
-constexpr int kFcStages = 3;
-constexpr int kFcStageBytes = 2 * kTileBytes + kW1Chunk;  // 64 KB
+// Pipeline stages: three of 64 KB (two activation tiles + a weight chunk) when a block
+// takes two tiles, four of 48 KB when it takes one.
+constexpr int kFcMaxStages = 4;
+constexpr int kFcStageMem = 3 * (2 * kTileBytes + kW1Chunk);  // 192 KB
 
 struct FcSmem {
-    uint8_t stage[kFcStages][kFcStageBytes];
+    uint8_t stage_mem[kFcStageMem];
     float bf1[256];
     float wf2[256];
-    uint64_t full[kFcStages];
-    uint64_t empty[kFcStages];
+    uint64_t full[kFcMaxStages];
+    uint64_t empty[kFcMaxStages];
     uint64_t done;
     uint32_t tslot;
     int abort;
@@ -487,7 +530,7 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
     }
     if (warp == 0) tmem_alloc(&S.tslot, 512);
     if (tid == 0) {
-        for (int s = 0; s < kFcStages; ++s) {
+        for (int s = 0; s < kFcMaxStages; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
@@ -503,6 +546,10 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
     const int64_t ntiles = (p.np + 127) / 128;
     const int64_t npairs = (ntiles + p.tiles_per_block - 1) / p.tiles_per_block;
     uint32_t it_prod = 0, it_mma = 0, done_phase = 0;
+    const int nst = p.tiles_per_block == 2 ? 3 : 4;
+    const uint32_t woff = (uint32_t)p.tiles_per_block * kTileBytes;  // weight chunk within a stage
+    const uint32_t sbytes = woff + kW1Chunk;
+    auto stage = [&](int st) { return S.stage_mem + (size_t)st * sbytes; };
 
     for (int64_t pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
         const int64_t mt0 = (int64_t)p.tiles_per_block * pair;
@@ -510,34 +557,34 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
         if (tid == 0) {
             // producer: stream the two activation tiles and fc1's weights, K chunk by chunk
             for (int kc = 0; kc < 32 && !S.abort; ++kc, ++it_prod) {
-                const int s = it_prod % kFcStages;
-                const uint32_t use = it_prod / kFcStages;
+                const int s = it_prod % nst;
+                const uint32_t use = it_prod / nst;
                 if (use > 0 && !mbar_wait_bounded(&S.empty[s], (use - 1) & 1u)) {
                     S.abort = 1;
                     break;
                 }
                 const uint32_t bytes = (two ? 2u : 1u) * kTileBytes + kW1Chunk;
                 mbar_arrive_expect_tx(&S.full[s], bytes);
-                bulk_g2s(S.stage[s], p.h3t + ((size_t)mt0 * 32 + kc) * kTileBytes, kTileBytes, &S.full[s]);
+                bulk_g2s(stage(s), p.h3t + ((size_t)mt0 * 32 + kc) * kTileBytes, kTileBytes, &S.full[s]);
                 if (two)
-                    bulk_g2s(S.stage[s] + kTileBytes, p.h3t + ((size_t)(mt0 + 1) * 32 + kc) * kTileBytes,
+                    bulk_g2s(stage(s) + kTileBytes, p.h3t + ((size_t)(mt0 + 1) * 32 + kc) * kTileBytes,
                              kTileBytes, &S.full[s]);
-                bulk_g2s(S.stage[s] + 2 * kTileBytes, p.w.W1t + (size_t)kc * kW1Chunk, kW1Chunk, &S.full[s]);
+                bulk_g2s(stage(s) + woff, p.w.W1t + (size_t)kc * kW1Chunk, kW1Chunk, &S.full[s]);
             }
         } else if (tid == 32) {
             // MMA issuer: 4 K steps of 16 per chunk, two M tiles sharing each weight chunk
             const uint32_t idesc = umma_idesc_bf16(128, 256);
             for (int kc = 0; kc < 32; ++kc, ++it_mma) {
-                const int s = it_mma % kFcStages;
-                const uint32_t use = it_mma / kFcStages;
+                const int s = it_mma % nst;
+                const uint32_t use = it_mma / nst;
                 if (S.abort || !mbar_wait_bounded(&S.full[s], use & 1u)) {
                     S.abort = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(S.stage[s]);
+                const uint32_t a0 = smem_u32(stage(s));
                 const uint32_t a1 = a0 + kTileBytes;
-                const uint32_t bw = a0 + 2 * kTileBytes;
+                const uint32_t bw = a0 + woff;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                     const uint64_t bd = umma_desc(bw + ks * 256, 128, 1024);
@@ -590,7 +637,7 @@ __global__ void __launch_bounds__(128, 1) cnn_fc_kernel(const CnnFcParams p)
         if (tid == 0) {
             report_error(p.status, kErrTimeout);
             for (uint32_t it = S.drain_from; it < it_prod; ++it)
-                if (!mbar_wait_bounded(&S.full[it % kFcStages], (it / kFcStages) & 1u)) break;
+                if (!mbar_wait_bounded(&S.full[it % nst], (it / nst) & 1u)) break;
         }
         if (tid == 32) mbar_wait_bounded(&S.done, done_phase ^ 1u);
     }
