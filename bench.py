@@ -38,7 +38,7 @@ SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, pe
 # DRAM bytes (read + write) of one fold_kernel<box> launch over 19,456 periods of the same
 # light curve, from the ncu capture summarised in profiles/fold_kernel_box_kepler62835.md;
 # scaled to the bench's period count (traffic grows with the number of periods).
-FOLD_DRAM_BYTES_19456 = 1.048576e6 + 24.092928e6
+FOLD_DRAM_BYTES_19456 = 1.062144e6 + 23.024640e6
 L2_FLUSH_BYTES = 256 << 20
 
 

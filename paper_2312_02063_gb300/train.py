@@ -43,29 +43,83 @@ def init_weights(device, seed: int = 1) -> dict:
     return out
 
 
+class Trainer:
+    """Adam on BCE-with-logits over the device-generated training stream, with checkpoints.
+
+    The state is the FP32 master weights, Adam's first and second moments, the number of
+    Adam steps taken and the index of the next profile of the stream (profiles are
+    generated by index, so the stream resumes exactly). Every kernel of a step is
+    deterministic, so training N + M steps equals training N steps, saving, loading and
+    training M steps, bit for bit.
+    """
+
+    def __init__(self, ctx: Context, batch: int = 4096, lr: float = 1e-3, seed: int = 1,
+                 data_seed: int = TRAIN_SEED, weights: dict | None = None):
+        self.ctx = ctx
+        self.batch = batch
+        self.lr = lr
+        self.data_seed = data_seed
+        self.params = weights if weights is not None else init_weights(ctx.device, seed)
+        self.m = {n: torch.zeros_like(p) for n, p in self.params.items()}
+        self.v = {n: torch.zeros_like(p) for n, p in self.params.items()}
+        self.steps = 0
+        self.next_index = 0
+
+    def step(self, nb: int | None = None):
+        """One Adam step on the next nb (default: batch) profiles; returns the loss tensor."""
+        nb = self.batch if nb is None else nb
+        f, c, y, _, _ = gpfc_synth_profiles(self.ctx, self.data_seed, self.next_index, nb)
+        logit, saved = gpfc_cnn_forward_train(self.ctx, f, self.params, c)
+        loss, dl = gpfc_bce_with_logits(self.ctx, logit, y)
+        grads = gpfc_cnn_backward(self.ctx, dl, self.params, saved)
+        self.steps += 1
+        for n in CNN_PARAM_NAMES:
+            gpfc_adam(self.ctx, self.params[n], grads[n], self.m[n], self.v[n], self.steps, self.lr)
+        self.next_index += nb
+        return loss
+
+    def state_dict(self) -> dict:
+        self.ctx.sync()
+        return {"params": {n: t.detach().cpu().clone() for n, t in self.params.items()},
+                "m": {n: t.detach().cpu().clone() for n, t in self.m.items()},
+                "v": {n: t.detach().cpu().clone() for n, t in self.v.items()},
+                "steps": self.steps, "next_index": self.next_index, "batch": self.batch, "lr": self.lr,
+                "data_seed": self.data_seed}
+
+    def load_state_dict(self, sd: dict):
+        dev = self.ctx.device
+        self.params = {n: t.to(dev).contiguous() for n, t in sd["params"].items()}
+        self.m = {n: t.to(dev).contiguous() for n, t in sd["m"].items()}
+        self.v = {n: t.to(dev).contiguous() for n, t in sd["v"].items()}
+        self.steps, self.next_index = int(sd["steps"]), int(sd["next_index"])
+        self.batch, self.lr, self.data_seed = int(sd["batch"]), float(sd["lr"]), int(sd["data_seed"])
+
+    def save(self, path: str):
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Trainer":
+        t = cls(ctx)
+        t.load_state_dict(torch.load(path, map_location="cpu"))
+        return t
+
+
 def train(ctx: Context, n_profiles: int, batch: int = 4096, lr: float = 1e-3, seed: int = 1,
           data_seed: int = TRAIN_SEED, first: int = 0, weights: dict | None = None, log_every: int = 50):
     """Adam on BCE-with-logits over n_profiles generated profiles (one pass, batch by batch).
 
     Returns (weights, history) where history lists (step, loss) every log_every steps.
     """
-    params = weights if weights is not None else init_weights(ctx.device, seed)
-    m = {n: torch.zeros_like(p) for n, p in params.items()}
-    v = {n: torch.zeros_like(p) for n, p in params.items()}
+    tr = Trainer(ctx, batch, lr, seed, data_seed, weights)
+    tr.next_index = first
     steps = (n_profiles + batch - 1) // batch
     hist = []
     for s in range(steps):
-        nb = min(batch, n_profiles - s * batch)
-        f, c, y, _, _ = gpfc_synth_profiles(ctx, data_seed, first + s * batch, nb)
-        logit, saved = gpfc_cnn_forward_train(ctx, f, params, c)
-        loss, dl = gpfc_bce_with_logits(ctx, logit, y)
-        grads = gpfc_cnn_backward(ctx, dl, params, saved)
-        for n in CNN_PARAM_NAMES:
-            gpfc_adam(ctx, params[n], grads[n], m[n], v[n], s + 1, lr)
+        loss = tr.step(min(batch, n_profiles - s * batch))
         if s % log_every == 0 or s == steps - 1:
             hist.append((s, float(loss.item())))
     ctx.sync()
-    return params, hist
+    return tr.params, hist
 
 
 def tpr_at_fpr(pos, neg, fpr):

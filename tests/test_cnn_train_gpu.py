@@ -105,3 +105,25 @@ def test_adam_matches_oracle(ctx):
         po, mo, vo = oracle.adam_step(po, gr, mo, vo, t, lr=1e-2)
     ctx.sync()
     np.testing.assert_allclose(p.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+
+
+def test_training_resumes_bit_for_bit_from_a_checkpoint(ctx, tmp_path):
+    """N + M steps equal N steps, a save to disk, a load into a new trainer and M steps:
+    weights, Adam moments and the data-stream position carry over exactly."""
+    from paper_2312_02063_gb300.train import Trainer
+    a = Trainer(ctx, batch=256, lr=2e-3, seed=4)
+    for _ in range(5):
+        a.step()
+    b = Trainer(ctx, batch=256, lr=2e-3, seed=4)
+    for _ in range(3):
+        b.step()
+    path = str(tmp_path / "ckpt.pt")
+    b.save(path)
+    c = Trainer.load(ctx, path)
+    for _ in range(2):
+        c.step()
+    sa, sc = a.state_dict(), c.state_dict()
+    assert sa["steps"] == sc["steps"] == 5 and sa["next_index"] == sc["next_index"] == 5 * 256
+    for part in ("params", "m", "v"):
+        for n in sa[part]:
+            assert torch.equal(sa[part][n], sc[part][n]), (part, n)
