@@ -47,6 +47,22 @@ def workload_name(n):
            f"{NBINS} bins, fold + box-SNR (w 1..{W_MAX}) + best period"
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's); the value
+    itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own replica of the workload."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
         int(os.environ.get("LOCAL_RANK", 0))
@@ -345,12 +361,10 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * n * N_PERIODS / (ms_per_step * 1e-3)
+    value = job_rate(world, n * N_PERIODS, ms_per_step)
 
     # end to end through host buffers: H2D of the step's inputs, the C-ABI call, D2H of
     # the periodogram and the best period
@@ -377,7 +391,7 @@ def run_gpu(args, rank, world, local_rank):
         if k >= 2:
             e2e_ms.append(a.elapsed_time(b))
     ctx.sync()
-    e2e_value = world * n * N_PERIODS / (statistics.mean(e2e_ms) * 1e-3)
+    e2e_value = job_rate(world, n * N_PERIODS, max_over_ranks(statistics.mean(e2e_ms), dist, dev))
     h2d = th.numel() * 8 + fh.numel() * 4 + ph.numel() * 8
     d2h = sh.numel() * 4 + 8 + 4
 

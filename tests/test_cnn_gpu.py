@@ -102,3 +102,26 @@ def test_search_with_cnn_scorer_matches_fold_then_score(ctx):
     mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods[idx], 256, lc.t0)
     _, so = oracle.cnn_score(w, mean_o.astype(np.float32), cnt_o.astype(np.int32))
     assert np.max(np.abs(sc[idx] - so)) <= SCORE_ATOL
+
+
+def test_cnn_full_size_batch_sampled(ctx):
+    """The full inference batch (262,144 profiles of 256 bins, the scoring benchmark's
+    size and launch path): 300 sampled profiles against the FP64 oracle, and the scores of
+    a repeated call identical."""
+    import paper_2312_02063_gb300 as g
+    n = 262144
+    prof, counts, _, _, _ = g.gpfc_synth_profiles(ctx, 20233204, 0, n)
+    w = scaled_weights(11, 0.25)
+    wd = dev_weights(ctx, w)
+    s = g.gpfc_score_cnn(ctx, prof, wd, counts)
+    s2 = g.gpfc_score_cnn(ctx, prof, wd, counts)
+    ctx.sync()
+    s, s2 = s.cpu().numpy(), s2.cpu().numpy()
+    assert np.array_equal(s, s2)
+    idx = np.unique(np.concatenate([np.random.default_rng(5).choice(n, 296, replace=False), [0, 1, n - 2, n - 1]]))
+    pf = prof[torch.from_numpy(idx).to(ctx.device)].cpu().numpy()
+    pc = counts[torch.from_numpy(idx).to(ctx.device)].cpu().numpy()
+    _, so = oracle.cnn_score(w, pf, pc)
+    assert np.max(np.abs(s[idx] - so)) <= SCORE_ATOL
+    flip = (s[idx] > 0.5) != (so > 0.5)
+    assert np.mean(~flip) >= 0.999 or np.all(np.abs(so[flip] - 0.5) < SCORE_ATOL)
