@@ -280,6 +280,37 @@ int gpfc_synth_profiles(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, 
                         const gpfc_synth_params *params, float *folded, int32_t *counts, float *label,
                         double *fold_period, float *flux_std);
 
+/* The paper's own training-set recipe (Sec. 2.6, Sec. 2.7): vector j (global index j =
+ * first + i) of length nbins stands for a folded light curve: Gaussian noise plus a
+ * trapezoid transit whose depth gives a target SNR alpha by Eq. 2,
+ *     alpha = (d / sigma) sqrt(n_points L / p)   =>   d = alpha sigma / sqrt(n_points q),
+ * with q = L/p the duration at half depth over the period (phase units). Even j:
+ * positive, alpha ~ U[alpha_pos_min, alpha_pos_max] (label 1). Odd j: negative (label 0),
+ * noise only when (j / 2) is even, else a transit with alpha ~ U(0, alpha_neg_max). The
+ * per-point noise sigma is log-uniform in [sigma_min, sigma_max]; a bin averages
+ * n_points / nbins points, so its noise is sigma sqrt(nbins / n_points). The trapezoid's
+ * short-to-long base ratio is r ~ U(0, 1) (long base 2q / (1 + r)), its centre phase
+ * phi0 ~ U[0, 1); it is evaluated at the bin centres (b + 1/2) / nbins. Values are
+ * 1 + noise - d * shape. Random numbers: Philox4x32-10 keyed by `seed`, counters
+ * (j, 0, 2, 2^32-1) and (j, 1, 2, 2^32-1) for the parameters, (j, m, 3, 0) for the
+ * normals of bins 4m..4m+3 (Box-Muller on u = (x >> 8) 2^-24).
+ * The paper does not give the negatives' lower SNR bound, the split between noise-only
+ * and injected negatives, the n of Eq. 2 for its 256-vectors or the trapezoid's phase:
+ * these are this library's readings. */
+typedef struct {
+    double alpha_pos_min, alpha_pos_max;
+    double alpha_neg_max;
+    double q_min, q_max;
+    double sigma_min, sigma_max;
+    int32_t n_points;
+} gpfc_vector_params;
+
+/* folded [n][nbins] float32 (every bin non-empty); label [n], alpha [n] and sigma_bin [n]
+ * float32 (the per-bin noise) may be NULL. nbins 8..1024; first + n <= 2^32. */
+int gpfc_synth_vectors(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, int32_t nbins,
+                       const gpfc_vector_params *params, float *folded, float *label, float *alpha,
+                       float *sigma_bin);
+
 /* ------------------------------------------------------------------ best period
  * argmax over score[n_periods] (NaN never wins; ties go to the smaller index), Sec. 2.1:
  * the trial period with the strongest score. best_index [1] int64 (-1 if every score is

@@ -318,3 +318,61 @@ def training_light_curve(seed: int, j: int, sp: dict = TRAINING_SET):
     elif kind == 3:
         x = x - depth * inbox(epoch) - depth2 * inbox(epoch + 0.5 * period)
     return t, 1.0 + x, float(kind == 0), fold_period
+
+
+# The paper's own training-set recipe (Sec. 2.6, Sec. 2.7): length-nbins vectors standing
+# for folded light curves, Gaussian noise plus a trapezoid transit whose depth gives a
+# target SNR alpha by Eq. 2. Positives: alpha in [6, 10]; negatives: noise only, or a
+# transit injected with alpha below 5.
+PAPER_VECTORS = dict(alpha_pos_min=6.0, alpha_pos_max=10.0, alpha_neg_max=5.0, q_min=0.04, q_max=0.12,
+                     sigma_min=1e-4, sigma_max=5e-4, n_points=65536)
+
+
+def paper_vector(seed: int, j: int, nbins: int = 256, pv: dict = PAPER_VECTORS):
+    """Vector j of the seeded paper-recipe set (the recipe of gpfc_synth_vectors).
+
+    Even j: positive (alpha ~ U[alpha_pos_min, alpha_pos_max]). Odd j: negative, noise only
+    when (j // 2) is even, else a transit with alpha ~ U(0, alpha_neg_max). Per-point noise
+    sigma log-uniform in [sigma_min, sigma_max]; a vector bin averages n_points / nbins points,
+    so its noise is sigma sqrt(nbins / n_points). Trapezoid: duration at half depth
+    q = L/p ~ U[q_min, q_max] (phase units), short-to-long base ratio r ~ U(0, 1), centre
+    phi0 ~ U[0, 1), evaluated at the bin centres (b + 1/2) / nbins. Depth d = alpha sigma /
+    sqrt(n_points q) (Eq. 2). Random numbers: Philox counters (j, 0, 2, 2^32-1) and
+    (j, 1, 2, 2^32-1) for the parameters, (j, m, 3, 0) for the normals of bins 4m..4m+3.
+    Returns (values f64 [nbins], label, alpha, sigma_bin).
+    """
+    key = (seed & _M32, (seed >> 32) & _M32)
+    a = philox4x32_10((j, 0, 2, _M32), key)
+    b = philox4x32_10((j, 1, 2, _M32), key)
+    positive = j % 2 == 0
+    inject = positive or (j // 2) % 2 == 1
+    sigma = np.exp(np.log(pv["sigma_min"]) + _u64(a[0]) * np.log(pv["sigma_max"] / pv["sigma_min"]))
+    if positive:
+        alpha = pv["alpha_pos_min"] + _u64(a[1]) * (pv["alpha_pos_max"] - pv["alpha_pos_min"])
+    else:
+        alpha = _u64(a[1]) * pv["alpha_neg_max"] if inject else 0.0
+    q = pv["q_min"] + _u64(a[2]) * (pv["q_max"] - pv["q_min"])
+    r = _u64(a[3])
+    phi0 = _u64(b[0])
+    n = pv["n_points"]
+    depth = alpha * sigma / np.sqrt(n * q)
+    sigma_bin = sigma * np.sqrt(nbins / n)
+    z = np.empty(nbins)
+    for m in range((nbins + 3) // 4):
+        rr = philox4x32_10((j, m, 3, 0), key)
+        for h in range(2):
+            u1 = 1.0 - _u64(rr[2 * h])
+            u2 = _u64(rr[2 * h + 1])
+            rad = np.sqrt(-2.0 * np.log(u1))
+            for qq, v in ((2 * h, rad * np.cos(2 * np.pi * u2)), (2 * h + 1, rad * np.sin(2 * np.pi * u2))):
+                if 4 * m + qq < nbins:
+                    z[4 * m + qq] = v
+    x = (np.arange(nbins) + 0.5) / nbins
+    dphi = x - phi0
+    dphi = np.abs(dphi - np.floor(dphi + 0.5))
+    t14 = 2.0 * q / (1.0 + r)
+    t23 = r * t14
+    shape = np.where(dphi <= 0.5 * t23, 1.0,
+                     np.where(dphi < 0.5 * t14, (0.5 * t14 - dphi) / (0.5 * (t14 - t23)), 0.0))
+    values = 1.0 + sigma_bin * z - depth * shape
+    return values, float(positive), float(alpha), float(sigma_bin)

@@ -21,7 +21,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -632,3 +632,37 @@ def gpfc_synth_profiles(ctx: Context, seed: int, first: int, n: int, nbins: int 
     ctx._check(L.gpfc_synth_profiles(ctx.handle, ctypes.c_uint64(seed), first, n, nbins, ctypes.byref(sp),
                                      _ptr(folded), _ptr(counts), _ptr(label), _ptr(period), _ptr(std)))
     return folded, counts, label, period, std
+
+
+class VectorParams(ctypes.Structure):
+    _fields_ = [("alpha_pos_min", ctypes.c_double), ("alpha_pos_max", ctypes.c_double),
+                ("alpha_neg_max", ctypes.c_double), ("q_min", ctypes.c_double), ("q_max", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double), ("n_points", ctypes.c_int32)]
+
+
+# The paper's training-set recipe (Sec. 2.6-2.7): SNR 6-10 positives, noise-only and
+# SNR < 5 negatives, trapezoids with duration/period 0.04-0.12 (Table 2), per-point noise
+# 1e-4..5e-4, 65,536-point light curves behind each 256-bin vector.
+PAPER_VECTORS = dict(alpha_pos_min=6.0, alpha_pos_max=10.0, alpha_neg_max=5.0, q_min=0.04, q_max=0.12,
+                     sigma_min=1e-4, sigma_max=5e-4, n_points=65536)
+
+
+def gpfc_synth_vectors(ctx: Context, seed: int, first: int, n: int, nbins: int = 256, params=None):
+    """Generate n paper-recipe vectors j = first..first+n-1.
+
+    Returns (folded [n][nbins], label [n], alpha [n], sigma_bin [n]) on the device.
+    """
+    L = ctx.lib
+    if not getattr(L, "_gpfc_vec_bound", False):
+        L.gpfc_synth_vectors.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.POINTER(VectorParams), _vp, _vp, _vp, _vp]
+        L._gpfc_vec_bound = True
+    vp = VectorParams(**(params or PAPER_VECTORS))
+    dev = ctx.device
+    folded = torch.empty((n, nbins), dtype=torch.float32, device=dev)
+    label = torch.empty(n, dtype=torch.float32, device=dev)
+    alpha = torch.empty(n, dtype=torch.float32, device=dev)
+    sb = torch.empty(n, dtype=torch.float32, device=dev)
+    ctx._check(L.gpfc_synth_vectors(ctx.handle, ctypes.c_uint64(seed), first, n, nbins, ctypes.byref(vp),
+                                    _ptr(folded), _ptr(label), _ptr(alpha), _ptr(sb)))
+    return folded, label, alpha, sb

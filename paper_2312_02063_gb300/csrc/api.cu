@@ -1210,6 +1210,28 @@ int gpfc_synth_profiles(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, 
     return GPFC_OK;
 }
 
+int gpfc_synth_vectors(gpfc_ctx *ctx, uint64_t seed, int64_t first, int64_t n, int32_t nbins,
+                       const gpfc_vector_params *params, float *folded, float *label, float *alpha,
+                       float *sigma_bin)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!params || !folded) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1 || first < 0 || first + n > ((int64_t)1 << 32)) return set_err(ctx, GPFC_EINVAL, "bad index range");
+    if (nbins < 8 || nbins > 1024) return set_err(ctx, GPFC_EINVAL, "nbins outside [8, 1024]");
+    const gpfc_vector_params &v = *params;
+    if (!(v.alpha_pos_min >= 0) || !(v.alpha_pos_max >= v.alpha_pos_min) || !(v.alpha_neg_max >= 0) ||
+        !(v.q_min > 0) || !(v.q_max >= v.q_min) || !(v.q_max < 1) || !(v.sigma_min > 0) ||
+        !(v.sigma_max >= v.sigma_min) || v.n_points < 1)
+        return set_err(ctx, GPFC_EINVAL, "vector parameters out of range");
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    VectorParams p{seed, first, n, nbins, v, folded, label, alpha, sigma_bin};
+    cudaError_t e = launch_paper_vectors(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "vector synthesis kernel");
+    return GPFC_OK;
+}
+
 int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods, int64_t *best_index,
                      float *best_score)
 {

@@ -23,4 +23,18 @@ struct SynthParams {
 
 cudaError_t launch_synth(const SynthParams &p, int num_sms, cudaStream_t st);
 
+struct VectorParams {
+    uint64_t seed;
+    int64_t first;
+    int64_t n;
+    int nbins;
+    gpfc_vector_params vp;
+    float *folded;          // [n][nbins]
+    float *label;           // [n] or NULL
+    float *alpha;           // [n] or NULL
+    float *sigma_bin;       // [n] or NULL
+};
+
+cudaError_t launch_paper_vectors(const VectorParams &p, int num_sms, cudaStream_t st);
+
 }  // namespace gpfc

@@ -198,6 +198,73 @@ __global__ void __launch_bounds__(kSynthWarps * 32) synth_fold_kernel(SynthParam
     }
 }
 
+// ------------------------------------------------------------------ the paper's vectors
+
+// One thread per 4 bins of a vector (the 4 normals of one Philox call), 64 per vector of
+// 256 bins; the vector's parameters are derived by every thread from the same counters.
+__global__ void paper_vectors_kernel(VectorParams P)
+{
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const int per_vec = (P.nbins + 3) / 4;
+    const int64_t total = P.n * per_vec;
+    const gpfc_vector_params &v = P.vp;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = g / per_vec;
+        const int m = (int)(g - q * per_vec);
+        const int64_t j = P.first + q;
+        const Philox4 a = philox4x32_10((uint32_t)j, 0u, 2u, 0xFFFFFFFFu, k0, k1);
+        const Philox4 b = philox4x32_10((uint32_t)j, 1u, 2u, 0xFFFFFFFFu, k0, k1);
+        const bool positive = (j & 1) == 0;
+        const bool inject = positive || ((j >> 1) & 1);
+        const double sigma = exp(log(v.sigma_min) + unif64(a.v[0]) * log(v.sigma_max / v.sigma_min));
+        double alpha = 0.0;
+        if (positive) alpha = v.alpha_pos_min + unif64(a.v[1]) * (v.alpha_pos_max - v.alpha_pos_min);
+        else if (inject) alpha = unif64(a.v[1]) * v.alpha_neg_max;
+        const double qq = v.q_min + unif64(a.v[2]) * (v.q_max - v.q_min);
+        const double r = unif64(a.v[3]);
+        const double phi0 = unif64(b.v[0]);
+        const double depth = alpha * sigma / sqrt((double)v.n_points * qq);
+        const double sigma_bin = sigma * sqrt((double)P.nbins / (double)v.n_points);
+        const double t14 = 2.0 * qq / (1.0 + r), t23 = r * t14;
+        const Philox4 rr = philox4x32_10((uint32_t)j, (uint32_t)m, 3u, 0u, k0, k1);
+        float z[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float u1 = 1.0f - unif32(rr.v[2 * h]);
+            const float u2 = unif32(rr.v[2 * h + 1]);
+            const float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cs;
+            sincospif(2.0f * u2, &sn, &cs);
+            z[2 * h] = rad * cs;
+            z[2 * h + 1] = rad * sn;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int bin = 4 * m + u;
+            if (bin >= P.nbins) break;
+            const double x = ((double)bin + 0.5) / (double)P.nbins;
+            double d = x - phi0;
+            d = fabs(d - floor(d + 0.5));
+            const double shape = d <= 0.5 * t23 ? 1.0 : (d < 0.5 * t14 ? (0.5 * t14 - d) / (0.5 * (t14 - t23)) : 0.0);
+            P.folded[q * P.nbins + bin] = (float)(1.0 + sigma_bin * (double)z[u] - depth * shape);
+        }
+        if (m == 0) {
+            if (P.label) P.label[q] = positive ? 1.f : 0.f;
+            if (P.alpha) P.alpha[q] = (float)alpha;
+            if (P.sigma_bin) P.sigma_bin[q] = (float)sigma_bin;
+        }
+    }
+}
+
+cudaError_t launch_paper_vectors(const VectorParams &p, int num_sms, cudaStream_t st)
+{
+    const int64_t total = p.n * ((p.nbins + 3) / 4);
+    const int64_t want = (total + 255) / 256;
+    const int grid = (int)(want < (int64_t)num_sms * 8 ? want : (int64_t)num_sms * 8);
+    paper_vectors_kernel<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_synth(const SynthParams &p, int num_sms, cudaStream_t st)
 {
     const int64_t want = p.n;

@@ -30,3 +30,40 @@ def test_training_light_curve_recipe():
     t, f, lab, P = lcsynth.training_light_curve(7, 1, dict(lcsynth.TRAINING_SET, n_cadences=8192, sigma_min=1e-3,
                                                            sigma_max=1e-3))
     assert 0.95 < np.std(f) / 1e-3 < 1.05
+
+
+def test_paper_vector_recipe():
+    """The paper-recipe vectors (Sec. 2.6-2.7): labels by index, alpha ranges, and the
+    injected trapezoid: its depth satisfies Eq. 2 with the per-bin noise, its width at half
+    depth is q of the phase (to one bin), and what is left after removing it is noise of
+    the stated per-bin sigma."""
+    nb, seed = 256, 7
+    pv = lcsynth.PAPER_VECTORS
+    for j in range(12):
+        v, label, alpha, sb = lcsynth.paper_vector(99, j, nb)
+        assert label == (1.0 if j % 2 == 0 else 0.0)
+        if j % 2 == 0:
+            assert pv["alpha_pos_min"] <= alpha <= pv["alpha_pos_max"]
+        elif (j // 2) % 2 == 0:
+            assert alpha == 0.0
+        else:
+            assert 0.0 <= alpha < pv["alpha_neg_max"]
+    x = (np.arange(nb) + 0.5) / nb
+    for j in (0, 2, 4, 6):
+        v, _, alpha, sb = lcsynth.paper_vector(seed, j, nb)
+        a = lcsynth.philox4x32_10((j, 0, 2, 0xFFFFFFFF), (seed, 0))
+        b = lcsynth.philox4x32_10((j, 1, 2, 0xFFFFFFFF), (seed, 0))
+        sigma = sb / np.sqrt(nb / pv["n_points"])
+        q = pv["q_min"] + lcsynth._u64(a[2]) * (pv["q_max"] - pv["q_min"])
+        r = lcsynth._u64(a[3])
+        phi0 = lcsynth._u64(b[0])
+        d = alpha * sigma / np.sqrt(pv["n_points"] * q)
+        # Eq. 2 over the vector: alpha = d / sigma_bin * sqrt(nbins * q)
+        assert abs(d / sb * np.sqrt(nb * q) - alpha) <= 1e-12 * alpha
+        dphi = np.abs((x - phi0) - np.floor(x - phi0 + 0.5))
+        t14 = 2 * q / (1 + r)
+        t23 = r * t14
+        shape = np.where(dphi <= t23 / 2, 1.0, np.where(dphi < t14 / 2, (t14 / 2 - dphi) / ((t14 - t23) / 2), 0.0))
+        assert abs(np.sum(shape >= 0.5) / nb - q) <= 1.0 / nb + 1e-12
+        noise = v - 1.0 + d * shape
+        assert abs(np.std(noise) / sb - 1.0) < 0.2

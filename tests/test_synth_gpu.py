@@ -10,6 +10,14 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2312_02063_gb300 as g
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
 def test_generated_profiles_match_oracle_fold():
     import paper_2312_02063_gb300 as g
     ctx = g.Context(0)
@@ -29,3 +37,23 @@ def test_generated_profiles_match_oracle_fold():
         assert np.max(np.abs(fo[nz] - mean_o[0][nz]) / mean_o[0][nz]) <= 1e-6
         assert abs(float(sd.item()) - np.std(flux)) <= 1e-5 * np.std(flux)
     ctx.close()
+
+
+def test_paper_recipe_vectors_match_the_reference_generator(ctx):
+    """gpfc_synth_vectors against lcsynth.paper_vector (the same Philox draws evaluated in
+    FP64 on the CPU): values within FP32 rounding of the noise, labels, alpha and the
+    per-bin noise exact to FP32."""
+    import paper_2312_02063_gb300 as g
+    seed, first, n = 4242, 1000, 64
+    f, lab, al, sb = g.gpfc_synth_vectors(ctx, seed, first, n)
+    ctx.sync()
+    f, lab, al, sb = (x.cpu().numpy() for x in (f, lab, al, sb))
+    for i in range(0, n, 3):
+        v, l, a, s = lcsynth.paper_vector(seed, first + i)
+        assert lab[i] == l
+        assert abs(al[i] - a) <= 1e-6 * max(1.0, a)
+        assert abs(sb[i] - s) <= 1e-6 * s
+        np.testing.assert_allclose(f[i].astype(np.float64), v, rtol=0, atol=2e-7)
+    # label balance and the negatives' split
+    assert lab[0::2].min() == 1.0 and lab[1::2].max() == 0.0
+    assert np.all(al[1::4] == 0.0) and np.all(al[3::4] < 5.0)
