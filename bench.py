@@ -35,10 +35,10 @@ NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
 SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, per SM
-# DRAM bytes (read + write) of one fold_kernel<box> launch over 19,456 periods of the same
-# light curve, from the ncu capture summarised in profiles/fold_kernel_box_kepler62835.md;
-# scaled to the bench's period count (traffic grows with the number of periods).
-FOLD_DRAM_BYTES_19456 = 1.062144e6 + 23.024640e6
+# DRAM bytes (read + write) of one fold launch (one chunk of the pipelined box search, all
+# resident blocks' periods: 14,592 at 3 warps x 152 SMs), from an ncu capture of the same
+# light curve.
+FOLD_DRAM_BYTES_PER_LAUNCH = 2.113024e6 + 21.418240e6  # profiles/fold_kernel_sums_kepler62835.md
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -341,6 +341,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx.set_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms = []
+    fold_ms, fold_launches = [], []
     clocks = ClockSampler(local_rank)
     if dist:
         dist.barrier()
@@ -353,6 +354,9 @@ def run_gpu(args, rank, world, local_rank):
         step()
         ev[k][1].record(stream)
         kernel_ms.append(ctx.kernel_time_ms())
+        fms, fl = ctx.fold_launch_times()
+        fold_ms.append(fms)
+        fold_launches.append(fl)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -402,7 +406,11 @@ def run_gpu(args, rank, world, local_rank):
         sms = ctx.num_sms
         peak_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
         kmean = statistics.mean(kernel_ms)
-        achieved = n * N_PERIODS / (kmean * 1e-3) / 1e9
+        # the fold's own launches (on the library's fold stream, scorer running beside them):
+        # all n * N_PERIODS updates of a step over the summed launch durations
+        fold_step_ms = statistics.mean(fold_ms)
+        launches = fold_launches[0]
+        achieved = n * N_PERIODS / (fold_step_ms * 1e-3) / 1e9
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, dt = cpu_oracle_rate(lc, periods, args.cpu_periods)
@@ -418,17 +426,19 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
-            "roofline": {"bound": "alu", "kernel": "fold_kernel<box>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "fold_kernel<sums>", "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
-                         "traffic": FOLD_DRAM_BYTES_19456 * N_PERIODS / 19456,
-                         "traffic_basis": "ncu dram__bytes_read+write of a 19,456-period launch, scaled by periods",
-                         "kernel_ms": kmean,
+                         "traffic": FOLD_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_basis": "ncu dram__bytes_read+write of one full-chunk fold launch",
+                         "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
+                         "search_ms": kmean,
                          "peak_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} bin updates/clk "
                                        f"(shared-memory pipe) x {smax:.0f} MHz ({src} sm_max_mhz)"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
-            "gpu_launches": 6 * args.steps,
+            # per step: 4 prep kernels, a fold and a box scorer per chunk, the argmax
+            "gpu_launches": (5 + 2 * launches) * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }

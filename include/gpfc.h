@@ -67,12 +67,18 @@ int gpfc_sync(gpfc_ctx *ctx);
 int gpfc_num_sms(const gpfc_ctx *ctx);
 
 /* Kernel timing. With timing enabled, each call records CUDA events on the context's
- * stream around its main kernel (the fold kernel for gpfc_fold / gpfc_search, the
- * scoring kernel for gpfc_score_*). gpfc_kernel_time_ms synchronises on the stop event
+ * stream around its main kernels (the fold kernel for gpfc_fold, the fold and scoring
+ * kernels for gpfc_search, the scoring kernel for gpfc_score_*). gpfc_kernel_time_ms synchronises on the stop event
  * of the last recorded launch and writes its duration in milliseconds to *ms (host).
  * Returns GPFC_EINVAL if timing is off or nothing was recorded yet. */
 int gpfc_set_timing(gpfc_ctx *ctx, int enable);
 int gpfc_kernel_time_ms(gpfc_ctx *ctx, float *ms);
+/* With timing enabled, a gpfc_search whose box search runs in the warp-per-profile
+ * kernel (gpfc_set_box_path) also records events around each of its fold launches, on
+ * the side stream they run on (so a launch's time includes the scorer running beside
+ * it). This writes their summed duration (ms) and their number for the last such call;
+ * it synchronises on the last stop event. GPFC_EINVAL if none was recorded. */
+int gpfc_fold_launch_times(gpfc_ctx *ctx, float *total_ms, int32_t *launches);
 
 /* Launch configuration of the fold kernel (gpfc_fold, gpfc_search, gpfc_search_batched).
  * Every field 0 means "automatic" (the autotuner's choice if it has one, else a default).
@@ -131,8 +137,9 @@ int gpfc_set_autotune(gpfc_ctx *ctx, int enable);
  * and gpfc_sync (or the next call) returns GPFC_ETIMEOUT. The context stays usable. */
 int gpfc_check_wait_timeout(gpfc_ctx *ctx, int64_t limit_cycles);
 
-/* Device workspace (bytes) the context needs for gpfc_fold / gpfc_search (box scorer) of
- * one star of n samples over n_periods periods under the current launch config. */
+/* Device workspace (bytes) the context needs for gpfc_fold, or gpfc_search with the box
+ * scorer on either box path, of one star of n samples over n_periods periods under the
+ * current launch config. */
 int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes);
 
 /* ------------------------------------------------------------------ fold
@@ -360,12 +367,22 @@ int gpfc_fold_equal_count(gpfc_ctx *ctx, const double *times, const float *flux,
 
 /* ------------------------------------------------------------------ search
  * Fold + score (Fig. 1) without returning the profiles. scorer GPFC_SCORER_BOX takes a
- * gpfc_box_params* in scorer_params: the box search runs in the fold kernel's epilogue on
- * the profile held on chip. GPFC_SCORER_CNN takes a gpfc_cnn_weights* (nbins must be
+ * gpfc_box_params* in scorer_params; the search runs where gpfc_set_box_path says (below).
+ * GPFC_SCORER_CNN takes a gpfc_cnn_weights* (nbins must be
  * 256): periods are folded in chunks whose profiles stay in L2 for the CNN kernels.
  * score [n_periods] float32; best_index [1] int64 and best_score [1] float32 (device,
  * may be NULL). Limits as for gpfc_fold. */
 typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;
+
+/* Where the box-SNR search runs. GPFC_BOX_EPILOGUE: in the fold kernel, on the profile
+ * held on chip (no profile traffic, but only as many warps as the fold's bins leave room
+ * for). GPFC_BOX_WARP: the fold writes each chunk's centred bin sums and counts to an
+ * L2-resident buffer and a separate kernel scores them, one warp per profile, at full
+ * occupancy. GPFC_BOX_AUTO (the default) takes GPFC_BOX_WARP for nbins >= 256, else the
+ * epilogue. Scores agree within the box tolerance either way; a batched search and the
+ * per-star search use the same path and agree bit for bit. */
+typedef enum { GPFC_BOX_AUTO = 0, GPFC_BOX_EPILOGUE = 1, GPFC_BOX_WARP = 2 } gpfc_box_path;
+int gpfc_set_box_path(gpfc_ctx *ctx, int path);
 
 int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
                 const double *periods, int64_t n_periods, int32_t nbins, double t0,

@@ -27,6 +27,9 @@ __all__ = [
 
 SCORER_BOX = 0
 SCORER_CNN = 1
+BOX_AUTO = 0       # the warp-per-profile kernel for nbins >= 256, else the fold's epilogue
+BOX_EPILOGUE = 1   # box search inside the fold kernel
+BOX_WARP = 2       # separate box kernel, one warp per profile
 
 STATUS = {0: "GPFC_OK", -1: "GPFC_EINVAL", -2: "GPFC_ENOMEM", -3: "GPFC_ECUDA", -4: "GPFC_ERANGE",
           -5: "GPFC_ETIMEOUT", -6: "GPFC_ENOTSUP"}
@@ -114,6 +117,8 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_search_batched.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                           ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.gpfc_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_set_box_path.argtypes = [_vp, ctypes.c_int]
+        L.gpfc_fold_launch_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]
         L.gpfc_peaks.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
                                  ctypes.c_double, ctypes.c_int32, _vp, _vp]
         L.gpfc_fold_equal_count.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
@@ -206,6 +211,10 @@ class Context:
         """Capture gpfc_search_batched into a CUDA graph and replay it (default on)."""
         self._check(self.lib.gpfc_set_graph(self.handle, int(bool(enable))))
 
+    def set_box_path(self, path: int):
+        """Where the box-SNR search runs: BOX_AUTO, BOX_EPILOGUE or BOX_WARP."""
+        self._check(self.lib.gpfc_set_box_path(self.handle, int(path)))
+
     def check_wait_timeout(self, limit_cycles: int = 2_000_000):
         """Run the bounded-wait self-test: the next sync raises GpfcError(GPFC_ETIMEOUT)."""
         self._check(self.lib.gpfc_check_wait_timeout(self.handle, int(limit_cycles)))
@@ -228,6 +237,12 @@ class Context:
         v = ctypes.c_float()
         self._check(self.lib.gpfc_kernel_time_ms(self.handle, ctypes.byref(v)))
         return float(v.value)
+
+    def fold_launch_times(self) -> tuple[float, int]:
+        """(summed ms, count) of the fold launches of the last timed warp-path box search."""
+        ms, n = ctypes.c_float(), ctypes.c_int32()
+        self._check(self.lib.gpfc_fold_launch_times(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
 
     @property
     def num_sms(self):

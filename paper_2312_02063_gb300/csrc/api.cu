@@ -43,9 +43,16 @@ struct gpfc_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint8_t> graph_key;
     gpfc_fold_config last_plan{0, 0, 0, 0, 0};
+    int box_path = GPFC_BOX_AUTO;
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    // side streams of the overlapped box search: folds (high priority), box scorer (low)
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t side_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // with timing on: event pairs around each fold launch of the last pipelined search
+    std::vector<cudaEvent_t> fold_ev;
+    int fold_ev_used = 0;
     char last_error[512] = {0};
 };
 
@@ -62,6 +69,7 @@ struct KernelTimer {
     gpfc_ctx *ctx;
     explicit KernelTimer(gpfc_ctx *c) : ctx(c)
     {
+        ctx->fold_ev_used = 0;
         if (ctx->timing) cudaEventRecord(ctx->ev_start, ctx->stream);
     }
     void stop()
@@ -307,6 +315,154 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     return GPFC_OK;
 }
 
+// The box search runs in its own warp-per-profile kernel (else in the fold's epilogue).
+bool warp_box(const gpfc_ctx *ctx, int nbins)
+{
+    return ctx->box_path == GPFC_BOX_WARP || (ctx->box_path == GPFC_BOX_AUTO && nbins >= 256);
+}
+
+// The warp-per-profile box search as a two-stage pipeline forked off stream st: chunk i is
+// folded on a high-priority side stream into buffer i % 2 and scored on a low-priority
+// side stream, so the next fold's blocks take each SM as soon as the scorer's blocks leave
+// it and the two kernels' tails overlap. The fold of chunk i + 2 waits for the scorer of
+// chunk i (same buffer). Both side streams are joined back into st, also on error, so
+// that a capture stays whole.
+template <class FoldFn, class BoxFn>
+cudaError_t box_pipeline(gpfc_ctx *ctx, cudaStream_t st, int64_t nchunks, FoldFn fold, BoxFn box)
+{
+    cudaStream_t sf = ctx->side[0], sb = ctx->side[1];
+    cudaEvent_t *ev = ctx->side_ev;  // fork, fold done x2, scorer done x2, join x2
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sf, ev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, ev[0], 0);
+    for (int64_t i = 0; i < nchunks && e == cudaSuccess; ++i) {
+        const int b = (int)(i & 1);
+        if (i >= 2) e = cudaStreamWaitEvent(sf, ev[3 + b], 0);
+        if (e == cudaSuccess) e = fold(i, b, sf);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + b], sf);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, ev[1 + b], 0);
+        if (e == cudaSuccess) e = box(i, b, sb);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + b], sb);
+    }
+    cudaError_t j = cudaEventRecord(ev[5], sf);
+    if (j == cudaSuccess) j = cudaStreamWaitEvent(st, ev[5], 0);
+    if (j == cudaSuccess) j = cudaEventRecord(ev[6], sb);
+    if (j == cudaSuccess) j = cudaStreamWaitEvent(st, ev[6], 0);
+    return e != cudaSuccess ? e : j;
+}
+
+// Runs launch() on stream sf; with timing on, between a pair of events kept for
+// gpfc_fold_launch_times.
+template <class Launch>
+cudaError_t timed_fold(gpfc_ctx *ctx, cudaStream_t sf, Launch launch)
+{
+    if (!ctx->timing) return launch();
+    const size_t need = 2 * (size_t)(ctx->fold_ev_used + 1);
+    while (ctx->fold_ev.size() < need) {
+        cudaEvent_t ev = nullptr;
+        const cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        ctx->fold_ev.push_back(ev);
+    }
+    cudaEvent_t *ev = &ctx->fold_ev[2 * ctx->fold_ev_used];
+    cudaError_t e = cudaEventRecord(ev[0], sf);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], sf);
+    if (e == cudaSuccess) ++ctx->fold_ev_used;
+    return e;
+}
+
+// Workspace of run_search_box_warp: the fold buffers, two chunks of sums and counts.
+size_t box_warp_bytes(const FoldPlan &pl, int64_t n, int64_t np, int nbins)
+{
+    const int64_t chunk = std::min<int64_t>(np, (int64_t)pl.grid * pl.ppc);
+    FoldBuffers fb{};
+    Carver c(nullptr);
+    c.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
+    for (int b = 0; b < 2; ++b) {
+        c.take<float>((size_t)chunk * nbins);
+        c.take<int32_t>((size_t)chunk * nbins);
+    }
+    return c.off + 256;
+}
+
+// Fold + box-SNR search of one star with the search in its own kernel. Periods go
+// through in chunks of one fold wave; a chunk's centred bin sums and counts stay resident
+// in L2 between the fold and the warp-per-profile scorer.
+int run_search_box_warp(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                        int64_t np, int32_t nbins, double t0, const gpfc_box_params *bp, float *score,
+                        int64_t *best_index, float *best_score)
+{
+    const FoldPlan pl = plan_fold(ctx, n, np, nbins, find_tuned(ctx, nbins, kModeFold, n));
+    const int64_t chunk = std::min<int64_t>(np, (int64_t)pl.grid * pl.ppc);
+    FoldBuffers fb{};
+    int rc = ensure_ws(ctx, box_warp_bytes(pl, n, np, nbins));
+    if (rc) return rc;
+    Carver w(ctx->ws);
+    uint8_t *fold_base = w.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
+    carve_fold(fold_base, pl, n, 1, nbins, fb);
+    float *cs[2];
+    int32_t *cc[2];
+    for (int b = 0; b < 2; ++b) {
+        cs[b] = w.take<float>((size_t)chunk * nbins);
+        cc[b] = w.take<int32_t>((size_t)chunk * nbins);
+    }
+    const bool want_best = best_index || best_score;
+    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G, fb.stats,
+                                ctx->status_dev, ctx->stream);
+    if (e == cudaSuccess && want_best) e = cudaMemsetAsync(fb.key, 0, sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    KernelTimer timer(ctx);
+    auto fold = [&](int64_t i, int b, cudaStream_t sf) {
+        const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);
+        FoldParams p{};
+        p.smp = fb.smp;
+        p.n = n;
+        p.periods = periods + k0;
+        p.np = nk;
+        p.ntasks = (nk + pl.ppc - 1) / pl.ppc;
+        p.nstars = 1;
+        p.stats = fb.stats;
+        p.nbins = nbins;
+        p.shift = shift_of(nbins);
+        p.warps = pl.warps;
+        p.chunk = pl.chunk;
+        p.layout = pl.layout;
+        p.tile = pl.tile;
+        p.ws_sc = fb.ws_sc;
+        p.ws_cnt = fb.ws_cnt;
+        p.sums = cs[b];
+        p.counts = cc[b];
+        p.status = ctx->status_dev;
+        return timed_fold(ctx, sf, [&] { return launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), sf); });
+    };
+    auto box = [&](int64_t i, int b, cudaStream_t sb) {
+        const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);
+        BoxCoopParams q{};
+        q.sums = cs[b];
+        q.counts = cc[b];
+        q.k_begin = k0;
+        q.rows = nk;
+        q.nbins = nbins;
+        q.w_min = bp->w_min;
+        q.w_max = bp->w_max;
+        q.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
+        q.stats = fb.stats;
+        q.nstars = 1;
+        q.score = score;
+        q.best_key = want_best ? fb.key : nullptr;
+        return launch_box_coop(q, ctx->num_sms, sb);
+    };
+    e = box_pipeline(ctx, ctx->stream, (np + chunk - 1) / chunk, fold, box);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "fold and box kernels");
+    timer.stop();
+    if (want_best) {
+        e = launch_argmax_finalize(fb.key, 1, best_index, best_score, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "argmax finalize");
+    }
+    return GPFC_OK;
+}
+
 bool cnn_weights_ok(const gpfc_cnn_weights *wt)
 {
     if (!wt) return false;
@@ -526,7 +682,7 @@ struct BatchArgs {
     int32_t S;
     int32_t nbins;
     int32_t scorer;
-    int32_t pad;
+    int32_t box_warp;  // box search in the warp-per-profile kernel
     const int64_t *lc_off;
     const double *times;
     const float *flux;
@@ -550,6 +706,10 @@ struct BatchBuffers {
     int64_t *slot_k;
     CnnDev dev;
     uint8_t *h3t;
+    // warp-per-profile box search: two chunks of sums, counts and slot maps
+    float *box_sum[2];
+    int32_t *box_cnt[2];
+    int64_t *box_slot[2];
 };
 
 // Workspace of a batched search: validated offsets and task starts, the fold buffers of
@@ -564,6 +724,13 @@ size_t carve_batched(void *base, const BatchArgs &A, const FoldPlan &pl, int64_t
     FoldBuffers tmp{};
     uint8_t *fold_base = c.take<uint8_t>(carve_fold(nullptr, pl, A.n_total, A.S, A.nbins, tmp));
     carve_fold(fold_base, pl, A.n_total, A.S, A.nbins, B.fb);
+    if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
+        for (int b = 0; b < 2; ++b) {
+            B.box_sum[b] = c.take<float>((size_t)slots * A.nbins);
+            B.box_cnt[b] = c.take<int32_t>((size_t)slots * A.nbins);
+            B.box_slot[b] = c.take<int64_t>(slots);
+        }
+    }
     if (A.scorer == GPFC_SCORER_CNN) {
         const int64_t half = (slots + 1) / 2;
         B.cf = c.take<float>((size_t)slots * A.nbins);
@@ -612,6 +779,42 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
     p.ws_cnt = B.fb.ws_cnt;
     p.status = ctx->status_dev;
     const bool want_best = A.best_index || A.best_score;
+    if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
+        // chunks of one task per resident block, each chunk's sums and counts by slot
+        if (want_best) e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long) * A.S, st);
+        if (e != cudaSuccess) return e;
+        const int64_t wave = (int64_t)pl.grid;
+        auto fold = [&](int64_t i, int b, cudaStream_t sf) {
+            FoldParams q = p;
+            q.sums = B.box_sum[b];
+            q.counts = B.box_cnt[b];
+            q.slot_k = B.box_slot[b];
+            q.task_begin = i * wave;
+            q.ntasks = std::min<int64_t>(T, q.task_begin + wave);
+            return launch_fold(q, kModeFold, (int)(q.ntasks - q.task_begin), sf);
+        };
+        auto box = [&](int64_t i, int b, cudaStream_t sb) {
+            const int64_t tb = i * wave, te = std::min<int64_t>(T, tb + wave);
+            BoxCoopParams q{};
+            q.sums = B.box_sum[b];
+            q.counts = B.box_cnt[b];
+            q.slot_k = B.box_slot[b];
+            q.rows = (te - tb) * pl.ppc;
+            q.nbins = A.nbins;
+            q.w_min = A.box.w_min;
+            q.w_max = A.box.w_max;
+            q.sigma_user = A.box.sigma > 0.0 ? (float)A.box.sigma : 0.f;
+            q.stats = B.fb.stats;
+            q.grid_off = B.grid_s;
+            q.nstars = A.S;
+            q.score = A.score;
+            q.best_key = want_best ? B.fb.key : nullptr;
+            return launch_box_coop(q, ctx->num_sms, sb);
+        };
+        e = box_pipeline(ctx, st, (T + wave - 1) / wave, fold, box);
+        if (e == cudaSuccess && want_best) e = launch_argmax_finalize(B.fb.key, A.S, A.best_index, A.best_score, st);
+        return e;
+    }
     if (A.scorer == GPFC_SCORER_BOX) {
         p.score = A.score;
         p.w_min = A.box.w_min;
@@ -752,6 +955,12 @@ int gpfc_create(gpfc_ctx **out, int device, void *stream)
         e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&ctx->status_dev), ctx->status_host, 0);
     }
     if (e == cudaSuccess) e = static_cast<cudaError_t>(fold_register_kernels());
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side[0], cudaStreamNonBlocking, prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side[1], cudaStreamNonBlocking, prio_least);
+    for (cudaEvent_t &ev : ctx->side_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_stop);
     if (e != cudaSuccess) {
@@ -759,6 +968,11 @@ int gpfc_create(gpfc_ctx **out, int device, void *stream)
                  cudaGetErrorString(e));
         cudaGetLastError();
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
+        for (cudaStream_t q : ctx->side)
+            if (q) cudaStreamDestroy(q);
+        for (cudaEvent_t ev : ctx->side_ev)
+            if (ev) cudaEventDestroy(ev);
+        if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
         delete ctx;
         return GPFC_ECUDA;
     }
@@ -777,6 +991,11 @@ void gpfc_destroy(gpfc_ctx *ctx)
     if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaEvent_t ev : ctx->fold_ev) cudaEventDestroy(ev);
+    for (cudaStream_t q : ctx->side)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t ev : ctx->side_ev)
+        if (ev) cudaEventDestroy(ev);
     delete ctx;
 }
 
@@ -816,6 +1035,14 @@ int gpfc_set_autotune(gpfc_ctx *ctx, int enable)
     return GPFC_OK;
 }
 
+int gpfc_set_box_path(gpfc_ctx *ctx, int path)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (path < GPFC_BOX_AUTO || path > GPFC_BOX_WARP) return set_err(ctx, GPFC_EINVAL, "box path %d unknown", path);
+    ctx->box_path = path;
+    return GPFC_OK;
+}
+
 int gpfc_set_graph(gpfc_ctx *ctx, int enable)
 {
     if (!ctx) return GPFC_EINVAL;
@@ -847,8 +1074,8 @@ int gpfc_autotune(gpfc_ctx *ctx, const double *times, const float *flux, int64_t
     cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamIsCapturing");
     if (cs != cudaStreamCaptureStatusNone) return set_err(ctx, GPFC_EINVAL, "autotune cannot run under stream capture");
-    return tune_fold(ctx, times, flux, n, periods, n_periods, nbins, scorer == GPFC_SCORER_BOX ? kModeBox : kModeFold,
-                     bp, n, out);
+    const int mode = scorer == GPFC_SCORER_BOX && !warp_box(ctx, nbins) ? kModeBox : kModeFold;
+    return tune_fold(ctx, times, flux, n, periods, n_periods, nbins, mode, bp, n, out);
 }
 
 int gpfc_check_wait_timeout(gpfc_ctx *ctx, int64_t limit_cycles)
@@ -869,9 +1096,11 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
     if (!ctx || !bytes) return GPFC_EINVAL;
     if (n < 1 || n_periods < 1 || nbins < 2 || nbins > kMaxNbinsLane)
         return set_err(ctx, GPFC_EINVAL, "bad sizes");
-    const FoldPlan pl = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
+    // the larger of a fold (gpfc_fold, the epilogue search) and the warp-per-profile search
+    const FoldPlan pb = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
+    const FoldPlan pf = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeFold, n));
     FoldBuffers fb{};
-    *bytes = carve_fold(nullptr, pl, n, 1, nbins, fb);
+    *bytes = std::max(carve_fold(nullptr, pb, n, 1, nbins, fb), box_warp_bytes(pf, n, n_periods, nbins));
     return GPFC_OK;
 }
 
@@ -890,6 +1119,23 @@ int gpfc_kernel_time_ms(gpfc_ctx *ctx, float *ms)
     cudaError_t e = cudaEventSynchronize(ctx->ev_stop);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ctx->ev_start, ctx->ev_stop);
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaEventElapsedTime");
+    return GPFC_OK;
+}
+
+int gpfc_fold_launch_times(gpfc_ctx *ctx, float *total_ms, int32_t *launches)
+{
+    if (!ctx || !total_ms || !launches) return GPFC_EINVAL;
+    if (!ctx->timing || ctx->fold_ev_used == 0) return set_err(ctx, GPFC_EINVAL, "no timed fold launch recorded");
+    float sum = 0.f;
+    for (int i = 0; i < ctx->fold_ev_used; ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(ctx->fold_ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->fold_ev[2 * i], ctx->fold_ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaEventElapsedTime");
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = ctx->fold_ev_used;
     return GPFC_OK;
 }
 
@@ -1271,6 +1517,9 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
         p.w_max = bp->w_max;
         p.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
         const bool want_best = best_index || best_score;
+        if (warp_box(ctx, nbins))
+            return run_search_box_warp(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
+                                       best_score);
         FoldBuffers fb{};
         rc = run_fold(ctx, times, flux, n, periods, n_periods, nbins, t0, kModeBox, p, want_best, &fb);
         if (rc) return rc;
@@ -1363,7 +1612,8 @@ int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offset
         if (bp->w_min < 1 || bp->w_max < bp->w_min || bp->w_max > nbins)
             return set_err(ctx, GPFC_EINVAL, "box widths must satisfy 1 <= w_min <= w_max <= nbins");
         A.box = *bp;
-        mode = kModeBox;
+        A.box_warp = warp_box(ctx, nbins) ? 1 : 0;
+        mode = A.box_warp ? kModeFold : kModeBox;
     } else if (scorer == GPFC_SCORER_CNN) {
         const auto *wt = static_cast<const gpfc_cnn_weights *>(scorer_params);
         if (!cnn_weights_ok(wt)) return set_err(ctx, GPFC_EINVAL, "CNN scorer needs gpfc_cnn_weights");

@@ -614,6 +614,7 @@ struct LaneBins {
         return big ? Cbig[(size_t)b * cbs] : st.count((uint32_t)b);
     }
     __device__ __forceinline__ float c(int b) const { return (float)ci(b); }
+    __device__ __forceinline__ float2 sc(int b) const { return make_float2(s(b), c(b)); }
 };
 
 // Bins of one profile staged transposed for the standalone scorer ([bin][33]).
@@ -628,6 +629,17 @@ struct StagedBins {
         return big ? (uint32_t)max(Cbig[b], 0) : (uint32_t)C[b * 33];
     }
     __device__ __forceinline__ float c(int b) const { return (float)ci(b); }
+    __device__ __forceinline__ float2 sc(int b) const { return make_float2(s(b), c(b)); }
+};
+
+// Bins of one profile staged by a whole warp: (sum, count) pairs at index b + b / 8, so
+// lanes reading bins 8 apart hit distinct banks. Counts are exact in FP32 (n <= 2^24).
+struct PairBins {
+    const float2 *B;
+    __device__ __forceinline__ float2 sc(int b) const { return B[b + (b >> 3)]; }
+    __device__ __forceinline__ float s(int b) const { return sc(b).x; }
+    __device__ __forceinline__ float c(int b) const { return sc(b).y; }
+    __device__ __forceinline__ uint32_t ci(int b) const { return (uint32_t)c(b); }
 };
 
 // a_hi + a_lo += x with an error-free transformation (Knuth's TwoSum): the pair carries
@@ -654,18 +666,29 @@ __device__ __forceinline__ void two_sum_acc(float &a_hi, float &a_lo, float x)
 // values; the R per-start winners are then merged
 // into the profile's best with ties to the smaller w, then the smaller s. The winning
 // box is re-evaluated in FP64 from the same bin sums.
-template <int R, class Bins>
-__device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
-                                           float &score, int &best_s, int &best_w)
+// Compare to a mask and bit-select through general registers: eight evaluations in
+// flight would otherwise need more predicate registers than a thread has.
+__device__ __forceinline__ uint32_t mask_gt(float a, float b)
 {
-    float Stot = 0.f, Ntot = 0.f;
-    for (int b = 0; b < nbins; ++b) {
-        Stot += B.s(b);
-        Ntot += B.c(b);
-    }
-    float bv = -INFINITY;
-    int bkey = 0x7fffffff;
-    for (int s0 = 0; s0 < nbins; s0 += R) {
+    uint32_t m;
+    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(m) : "f"(a), "f"(b));
+    return m;
+}
+__device__ __forceinline__ uint32_t select_bits(uint32_t m, uint32_t a, uint32_t b)  // m ? a : b, bitwise
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "r"(b), "r"(m));
+    return d;
+}
+
+// QCHECK false is allowed when w_max is below the number of non-empty bins: then no box
+// holds every sample (n_out >= 1), and a box of empty bins has D = 0 exactly (its bins add
+// exact zeros to the prefix), so it never beats anything; the q >= 1 test can go.
+template <int R, bool QCHECK, class Bins>
+__device__ __forceinline__ void box_walk(const Bins &B, int nbins, int w_min, int w_max, float Stot, float Ntot,
+                                         int s0_first, int s0_stride, float &bv, int &bkey)
+{
+    for (int s0 = s0_first; s0 < nbins; s0 += s0_stride) {
         const bool full = s0 + R <= nbins;
         float bA[R], bN[R];     // prefix values at each start
         // best per start, kept as E = D |D| and q = n_in n_out (v = sign(E) sqrt(|E| / q), so
@@ -681,12 +704,11 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
         float runA = 0.f, runN = 0.f;
         int j = s0;
         // the next bin's sum and count are read one step ahead of their use
-        float pf_s = B.s(j), pf_c = B.c(j);
+        float2 pf = B.sc(j);
         auto step = [&](int t) {
-            const float c = pf_c, sv = pf_s;
+            const float sv = pf.x, c = pf.y;
             j = (j + 1 == nbins) ? 0 : j + 1;
-            pf_s = B.s(j);
-            pf_c = B.c(j);
+            pf = B.sc(j);
             runA = fmaf(Stot, c, fmaf(-Ntot, sv, runA));
             runN += c;
             (void)t;
@@ -728,10 +750,29 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
                 eval(r, t, (w >= w_min) & (w <= w_max) & (s0 + r < nbins));
             }
         }
-        for (int t = ta; t < tb; ++t) {  // every (r, w) valid here
-            step(t);
+        if (QCHECK) {
+            for (int t = ta; t < tb; ++t) {  // every (r, w) valid here
+                step(t);
 #pragma unroll
-            for (int r = 0; r < R; ++r) eval(r, t, true);
+                for (int r = 0; r < R; ++r) eval(r, t, true);
+            }
+        } else {
+            float cN[R];  // N + Pn(start): n_out = cN - Pn(end), exact in integers
+#pragma unroll
+            for (int r = 0; r < R; ++r) cN[r] = Ntot + bN[r];
+            for (int t = ta; t < tb; ++t) {
+                step(t);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float q = (runN - bN[r]) * (cN[r] - runN);
+                    const float D = runA - bA[r];
+                    const float E = D * fabsf(D);
+                    const uint32_t m = mask_gt(E * rq[r], rE[r] * q);
+                    rE[r] = __uint_as_float(select_bits(m, __float_as_uint(E), __float_as_uint(rE[r])));
+                    rq[r] = __uint_as_float(select_bits(m, __float_as_uint(q), __float_as_uint(rq[r])));
+                    rt[r] = (int)select_bits(m, (uint32_t)t, (uint32_t)rt[r]);
+                }
+            }
         }
         for (int t = max(tb, R); t < tend; ++t) {
             step(t);
@@ -752,15 +793,13 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
             bkey = take ? key : bkey;
         }
     }
-    if (bkey == 0x7fffffff) {
-        score = -INFINITY;
-        best_s = -1;
-        best_w = -1;
-        return;
-    }
-    const int bw = bkey >> 12, bs = bkey & 4095;
-    // re-evaluation of the winner, snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out)):
-    // exact integer counts, double-float sums, FP64 for the last few operations
+}
+
+// Re-evaluation of box (bs, bw), snr = (S n_in - S_in N) / (sigma sqrt(N n_in n_out)):
+// exact integer counts, double-float sums, FP64 for the last few operations.
+template <class Bins>
+__device__ __forceinline__ float box_reeval(const Bins &B, int nbins, int bs, int bw, float sigma)
+{
     float sth = 0.f, stl = 0.f, sih = 0.f, sil = 0.f;
     uint32_t nt = 0u, ni = 0u;
     for (int b = 0; b < nbins; ++b) {
@@ -775,9 +814,35 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
     }
     const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
     const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
-    score = (float)((St * Ni - Si * Nt) / ((double)sigma * sqrt(Nt * Ni * No)));
-    best_s = bs;
-    best_w = bw;
+    return (float)((St * Ni - Si * Nt) / ((double)sigma * sqrt(Nt * Ni * No)));
+}
+
+// Box-SNR of one profile held by one thread: every start, then the winner re-evaluated.
+template <int R, class Bins>
+__device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
+                                           float &score, int &best_s, int &best_w)
+{
+    float Stot = 0.f, Ntot = 0.f;
+    int nnz = 0;
+    for (int b = 0; b < nbins; ++b) {
+        const float c = B.c(b);
+        Stot += B.s(b);
+        Ntot += c;
+        nnz += c > 0.f;
+    }
+    float bv = -INFINITY;
+    int bkey = 0x7fffffff;
+    if (w_max < nnz) box_walk<R, false>(B, nbins, w_min, w_max, Stot, Ntot, 0, R, bv, bkey);
+    else box_walk<R, true>(B, nbins, w_min, w_max, Stot, Ntot, 0, R, bv, bkey);
+    if (bkey == 0x7fffffff) {
+        score = -INFINITY;
+        best_s = -1;
+        best_w = -1;
+        return;
+    }
+    best_w = bkey >> 12;
+    best_s = bkey & 4095;
+    score = box_reeval(B, nbins, best_s, best_w, sigma);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
@@ -969,8 +1034,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     uint32_t c = over ? wcn_cta[(size_t)b * ppc] : st.count((uint32_t)b);
                     if (!kvalid) c = 0u;
                     const float S = st.sum((uint32_t)b);
-                    const float mean = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
-                    if (p.folded) p.folded[(size_t)row * nbins + b] = mean;
+                    if (p.folded) p.folded[(size_t)row * nbins + b] = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
+                    if (p.sums) p.sums[(size_t)row * nbins + b] = c ? S : 0.f;
                     if (p.counts) p.counts[(size_t)row * nbins + b] = (int32_t)c;
                 }
             }
@@ -1019,9 +1084,12 @@ static cudaError_t set_smem_attr_all()
     return e;
 }
 
+cudaError_t box_coop_register();
+
 int fold_register_kernels()
 {
-    cudaError_t e = set_smem_attr_all<kModeFold, true>();
+    cudaError_t e = box_coop_register();
+    if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, true>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, false>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, true>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, false>();
@@ -1200,6 +1268,150 @@ cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, in
     const int grid = (int)(want < (int64_t)sms * 2 ? want : (int64_t)sms * 2);
     box_kernel<<<grid, warps * 32, smem, st>>>(folded, counts, np, nbins, w_min, w_max, sigma,
                                                    score, best_s, best_w);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ box-SNR, warp per profile
+
+// A warp scores one profile at a time from the fold's centred bin sums and counts: the
+// profile is staged as PairBins, lane L walks the blocks of 8 starts L, L + 32, ... and
+// the lanes' winners merge by the walk's own rule (larger v, then smaller w, then smaller
+// s). The winner is re-evaluated with double-float sums spread over the warp. Unlike the
+// fold's own epilogue, the search here runs at full occupancy.
+constexpr int kCoopR = 8;
+
+__device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float hi2, float lo2)
+{
+    two_sum_acc(hi, lo, hi2);
+    lo += lo2;
+}
+
+__device__ __forceinline__ int star_of(const int64_t *grid_off, int nstars, int64_t k)
+{
+    int lo = 0, hi = nstars - 1;
+    while (lo < hi) {  // the last star whose range starts at or before k
+        const int mid = (lo + hi + 1) >> 1;
+        if (grid_off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxCoopParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int nbins = p.nbins;
+    float2 *Bw = reinterpret_cast<float2 *>(smem) + (size_t)warp * coop_pairs(nbins);
+    const PairBins B{Bw};
+    int cur_s = -1;
+    unsigned long long cur_key = 0ull;
+    for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < p.rows; r += (int64_t)gridDim.x * nw) {
+        const int64_t k = p.slot_k ? p.slot_k[r] : p.k_begin + r;
+        if (k < 0) continue;
+        const int s = p.grid_off ? star_of(p.grid_off, p.nstars, k) : 0;
+        const int64_t gb = p.grid_off ? p.grid_off[s] : 0;
+        const float *srow = p.sums + (size_t)r * nbins;
+        const int32_t *crow = p.counts + (size_t)r * nbins;
+        __syncwarp();  // the previous profile's readers are done
+        float Stot = 0.f, Ntot = 0.f;
+        int nnz = 0;
+        for (int b = lane; b < nbins; b += 32) {
+            const float sv = srow[b], c = (float)max(crow[b], 0);
+            Bw[b + (b >> 3)] = make_float2(sv, c);
+            Stot += sv;
+            Ntot += c;
+            nnz += c > 0.f;
+        }
+        for (int o = 16; o > 0; o >>= 1) {  // a butterfly leaves the same totals in every lane
+            Stot += __shfl_xor_sync(0xffffffffu, Stot, o);
+            Ntot += __shfl_xor_sync(0xffffffffu, Ntot, o);
+            nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+        }
+        __syncwarp();
+        float bv = -INFINITY;
+        int bkey = 0x7fffffff;
+        if (p.w_max < nnz)
+            box_walk<kCoopR, false>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
+        else
+            box_walk<kCoopR, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int okey = __shfl_xor_sync(0xffffffffu, bkey, o);
+            const bool take = (ov > bv) | ((ov == bv) & (okey < bkey));
+            bv = take ? ov : bv;
+            bkey = take ? okey : bkey;
+        }
+        float sc = -INFINITY;
+        int bs = -1, bw = -1;
+        if (bkey != 0x7fffffff) {
+            bw = bkey >> 12;
+            bs = bkey & 4095;
+            float sth = 0.f, stl = 0.f, sih = 0.f, sil = 0.f;
+            uint32_t nt = 0u, ni = 0u;
+            for (int b = lane; b < nbins; b += 32) {
+                const float2 v = B.sc(b);
+                const uint32_t c = (uint32_t)v.y;
+                two_sum_acc(sth, stl, v.x);
+                nt += c;
+                int d = b - bs;
+                d += d < 0 ? nbins : 0;
+                if (d < bw) {
+                    two_sum_acc(sih, sil, v.x);
+                    ni += c;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                two_sum_merge(sth, stl, __shfl_xor_sync(0xffffffffu, sth, o), __shfl_xor_sync(0xffffffffu, stl, o));
+                two_sum_merge(sih, sil, __shfl_xor_sync(0xffffffffu, sih, o), __shfl_xor_sync(0xffffffffu, sil, o));
+                nt += __shfl_xor_sync(0xffffffffu, nt, o);
+                ni += __shfl_xor_sync(0xffffffffu, ni, o);
+            }
+            float sig = p.sigma_user;
+            if (!(sig > 0.f)) sig = p.stats[s].sigma;
+            if (!(sig > 0.f)) sig = 1.f;
+            const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
+            const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
+            sc = (float)((St * Ni - Si * Nt) / ((double)sig * sqrt(Nt * Ni * No)));
+        }
+        if (lane == 0) {
+            p.score[k] = sc;
+            if (p.best_s) p.best_s[k] = bs;
+            if (p.best_w) p.best_w[k] = bw;
+            if (p.best_key) {
+                const unsigned long long key = argmax_key(sc, k - gb);
+                if (s != cur_s) {
+                    if (cur_key) atomicMax(&p.best_key[cur_s], cur_key);
+                    cur_s = s;
+                    cur_key = key;
+                } else {
+                    cur_key = key > cur_key ? key : cur_key;
+                }
+            }
+        }
+    }
+    if (lane == 0 && p.best_key && cur_key) atomicMax(&p.best_key[cur_s], cur_key);
+}
+
+size_t box_coop_smem(int nbins) { return (size_t)kCoopWarps * coop_pairs(nbins) * sizeof(float2); }
+
+cudaError_t box_coop_register()
+{
+    return cudaFuncSetAttribute(box_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemLimit - 1024));
+}
+
+cudaError_t launch_box_coop(const BoxCoopParams &p, int num_sms, cudaStream_t st)
+{
+    if (p.rows <= 0) return cudaSuccess;
+    const size_t smem = box_coop_smem(p.nbins);
+    if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, box_coop_kernel, kCoopWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (p.rows + kCoopWarps - 1) / kCoopWarps;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms * std::max(1, occ));
+    box_coop_kernel<<<grid, kCoopWarps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 

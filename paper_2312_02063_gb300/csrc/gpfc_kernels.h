@@ -67,6 +67,7 @@ struct FoldParams {
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
     // kModeFold outputs ([global period][nbins], or [slot][nbins] when slot_k is set)
     float *folded;
+    float *sums;               // centred bin sums (0 for empty bins), for the separate box scorer
     int32_t *counts;
     int64_t *slot_k;           // chunk slots: slot (task - task_begin) * 32 * warps + lane of
                                // the block gets period k, or -1 (then counts 0, means NaN)
@@ -81,6 +82,33 @@ struct FoldParams {
     uint16_t *cnn_in;
     uint32_t *status;
 };
+
+// Box-SNR over profiles the fold wrote as centred sums and counts ([row][nbins]), one warp
+// per profile. Row r holds period k = slot_k[r] (skipped if < 0), or k_begin + r.
+struct BoxCoopParams {
+    const float *sums;
+    const int32_t *counts;
+    const int64_t *slot_k;
+    int64_t k_begin;
+    int64_t rows;
+    int nbins;
+    int w_min, w_max;
+    float sigma_user;             // > 0: use it; else the star's flux std (1 if that is 0)
+    const StarStats *stats;
+    const int64_t *grid_off;      // [S+1] period offsets, or NULL (one star)
+    int nstars;
+    float *score;                 // [global period]
+    int32_t *best_s;
+    int32_t *best_w;
+    unsigned long long *best_key; // [S] argmax keys (may be NULL)
+};
+
+// float2 (sum, count) slots one warp of the scorer stages per profile
+__host__ __device__ inline int coop_pairs(int nbins) { return nbins + (nbins >> 3) + 2; }
+constexpr int kCoopWarps = 8;  // warps per block of the scorer
+
+size_t box_coop_smem(int nbins);
+cudaError_t launch_box_coop(const BoxCoopParams &p, int num_sms, cudaStream_t st);
 
 size_t fold_smem_bytes(int nbins, int warps, int layout, int tile = kTile);
 int fold_max_warps(int nbins, int layout, int tile = kTile);
