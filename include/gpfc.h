@@ -155,14 +155,18 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
  * times   [n]            float64, days, any order
  * flux    [n]            float32
  * periods [n_periods]    float64, days, finite and > 0 (else GPFC_ERANGE, latched)
- * nbins                  2..1024
+ * nbins                  2..4096
  * t0                     phase origin in days; NaN means t0 = times[0]
  * folded  [n_periods][nbins] float32 row-major, per-bin mean flux, NaN for an empty bin;
  *                        may be NULL (not written)
  * counts  [n_periods][nbins] int32 row-major, samples per bin; may be NULL
  * Sums are accumulated as (flux - mean flux) in FP32 with Kahan compensation (chunk
  * partials in shared memory, compensated across chunks); counts are exact integers.
- * Limits: 1 <= n <= 2^24, 1 <= n_periods <= 2^31 - 1, |tau| < 2^62, F < 2^63. */
+ * Above 1024 bins (more than a lane's shared-memory share) the fold adds each sample
+ * with one 64-bit shared-memory atomic per period into count << 40 plus the flux sum in
+ * fixed point (quantum 2^-k with n max|flux - mean| 2^k < 2^38): exact sums, rounded once.
+ * Limits: 1 <= n <= 2^24 (n < 2^24 above 1024 bins), 1 <= n_periods <= 2^31 - 1,
+ * |tau| < 2^62, F < 2^63. */
 int gpfc_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
               const double *periods, int64_t n_periods, int32_t nbins, double t0,
               float *folded, int32_t *counts);
@@ -183,8 +187,9 @@ typedef struct {
 
 /* folded [n_periods][nbins] float32 means (NaN or count 0 marks an empty bin);
  * counts [n_periods][nbins] int32 (required); score [n_periods] float32;
- * best_s / best_w [n_periods] int32, may be NULL. Limits: nbins 2..1024,
- * per-profile sample count N <= 2^24. */
+ * best_s / best_w [n_periods] int32, may be NULL. Limits: nbins 2..4096,
+ * per-profile sample count N <= 2^24. Each profile is centred on its count-weighted
+ * mean (FP64) and scored by one warp (the search kernel of gpfc_set_box_path). */
 int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts,
                    int64_t n_periods, int32_t nbins, const gpfc_box_params *params,
                    float *score, int32_t *best_s, int32_t *best_w);
@@ -444,6 +449,8 @@ int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t
  *   best_index   [n_stars] int64 (may be NULL): argmax of the star's scores as an index
  *                into ITS grid (0 .. grid length - 1), ties to the smallest, -1 if none
  *   best_score   [n_stars] float32 (may be NULL)
+ * nbins 2..1024 (GPFC_ENOTSUP above: the fixed-point fold of larger bin counts runs one
+ * star at a time through gpfc_search).
  * scorer / scorer_params as for gpfc_search. Every score equals the one gpfc_search gives
  * for that star alone (bit for bit).
  * The offsets are validated on the device (no host synchronisation): a violation is

@@ -246,6 +246,10 @@ size_t carve_fold(void *base, const FoldPlan &pl, int64_t n_total, int nstars, i
     return c.off + 256;
 }
 
+// Bin counts above the lane-private fold's limit go through the fine-bin stage of the
+// two-tier kernel (exact fixed-point shared atomics, twotier.cu).
+bool wide_bins(int nbins) { return nbins > kMaxNbinsLane || fold_max_warps(nbins, kLayoutPaired16) < 1; }
+
 int check_fold_args(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
                     const double *periods, int64_t np, int32_t nbins)
 {
@@ -254,9 +258,9 @@ int check_fold_args(gpfc_ctx *ctx, const double *times, const float *flux, int64
     if (n < 1 || n > (int64_t)1 << 24) return set_err(ctx, GPFC_EINVAL, "n = %lld outside [1, 2^24]", (long long)n);
     if (np < 1 || np > (int64_t)INT32_MAX)
         return set_err(ctx, GPFC_EINVAL, "n_periods = %lld outside [1, 2^31-1]", (long long)np);
-    if (nbins < 2) return set_err(ctx, GPFC_EINVAL, "nbins = %d < 2", nbins);
-    if (nbins > kMaxNbinsLane || fold_max_warps(nbins, kLayoutPaired16) < 1)
-        return set_err(ctx, GPFC_ENOTSUP, "nbins = %d > %d", nbins, kMaxNbinsLane);
+    if (nbins < 2 || nbins > kEqMaxFine) return set_err(ctx, GPFC_EINVAL, "nbins = %d outside [2, %d]", nbins, kEqMaxFine);
+    if (wide_bins(nbins) && n >= ((int64_t)1 << 24))
+        return set_err(ctx, GPFC_EINVAL, "n = %lld: above %d bins n must be below 2^24", (long long)n, kMaxNbinsLane);
     return GPFC_OK;
 }
 
@@ -266,6 +270,154 @@ int shift_of(int nbins)
     int l = 0;
     while ((1 << l) < nbins) ++l;
     return 32 - l;
+}
+
+// Buffers of the fixed-point fold of one star: prep outputs and the quantised flux.
+struct WideBuffers {
+    double *partial;
+    StarStats *stats;
+    SampleScratch smp;
+    long long *q;
+    unsigned int *maxbits;
+    int *kscale;
+};
+
+int prep_groups(int64_t n) { return (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 8191) / 8192)); }
+
+size_t carve_wide(void *base, int64_t n, WideBuffers &w)
+{
+    Carver c(base);
+    w.partial = c.take<double>((size_t)3 * prep_groups(n));
+    w.stats = c.take<StarStats>(1);
+    const int64_t se = scratch_elems(n, 1);
+    w.smp.tau_lo = c.take<uint32_t>(se);
+    w.smp.tau_hi = c.take<int32_t>(se);
+    w.smp.x = c.take<float>(se);
+    w.smp.flags = c.take<uint8_t>(se / 16 + 64);
+    w.q = c.take<long long>(n);
+    w.maxbits = c.take<unsigned int>(1);
+    w.kscale = c.take<int>(1);
+    return c.off;
+}
+
+cudaError_t prep_wide(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, double t0,
+                      const WideBuffers &w)
+{
+    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, w.smp, w.partial, prep_groups(n), w.stats,
+                                ctx->status_dev, ctx->stream);
+    if (e == cudaSuccess) e = launch_eq_prep(w.smp.x, n, w.maxbits, w.q, w.kscale, ctx->num_sms, ctx->stream);
+    return e;
+}
+
+EqParams eq_params(gpfc_ctx *ctx, const WideBuffers &w, int64_t n, const double *periods, int64_t np, int nfine,
+                   int nbins)
+{
+    EqParams p{};
+    p.tau_lo = w.smp.tau_lo;
+    p.tau_hi = w.smp.tau_hi;
+    p.q = w.q;
+    p.n = n;
+    p.periods = periods;
+    p.np = np;
+    p.nfine = nfine;
+    p.nbins = nbins;
+    p.fshift = shift_of(nfine);
+    p.ppb = eq_periods_per_block(nfine);
+    p.kscale = w.kscale;
+    p.stats = w.stats;
+    p.status = ctx->status_dev;
+    return p;
+}
+
+// Equal-width fold above the lane-private limit (means and/or counts out).
+int run_fold_wide(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                  int64_t np, int32_t nbins, double t0, float *folded, int32_t *counts)
+{
+    WideBuffers w{};
+    int rc = ensure_ws(ctx, carve_wide(nullptr, n, w) + 256);
+    if (rc) return rc;
+    carve_wide(ctx->ws, n, w);
+    cudaError_t e = prep_wide(ctx, times, flux, n, t0, w);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    EqParams p = eq_params(ctx, w, n, periods, np, nbins, nbins);
+    p.width_only = 1;
+    p.folded = folded;
+    p.counts = counts;
+    KernelTimer timer(ctx);
+    e = launch_eq_fold(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "fold kernel");
+    timer.stop();
+    return GPFC_OK;
+}
+
+// Chunk of the wide box search: one block pass of periods per SM.
+int64_t wide_chunk(const gpfc_ctx *ctx, int64_t np, int nbins)
+{
+    return std::min<int64_t>(np, (int64_t)ctx->num_sms * eq_periods_per_block(nbins));
+}
+
+size_t box_wide_bytes(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins)
+{
+    WideBuffers w{};
+    Carver c(nullptr);
+    c.take<uint8_t>(carve_wide(nullptr, n, w));
+    const int64_t chunk = wide_chunk(ctx, np, nbins);
+    c.take<float>((size_t)chunk * nbins);
+    c.take<int32_t>((size_t)chunk * nbins);
+    c.take<unsigned long long>(1);
+    return c.off + 256;
+}
+
+// Box-SNR search above the lane-private limit: chunks of the equal-width fixed-point fold,
+// each scored by the warp-per-profile kernel from its centred sums.
+int run_search_box_wide(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                        int64_t np, int32_t nbins, double t0, const gpfc_box_params *bp, float *score,
+                        int64_t *best_index, float *best_score)
+{
+    int rc = ensure_ws(ctx, box_wide_bytes(ctx, n, np, nbins));
+    if (rc) return rc;
+    const int64_t chunk = wide_chunk(ctx, np, nbins);
+    Carver c(ctx->ws);
+    WideBuffers w{};
+    carve_wide(c.take<uint8_t>(carve_wide(nullptr, n, w)), n, w);
+    float *cs = c.take<float>((size_t)chunk * nbins);
+    int32_t *cc = c.take<int32_t>((size_t)chunk * nbins);
+    unsigned long long *key = c.take<unsigned long long>(1);
+    const bool want_best = best_index || best_score;
+    cudaError_t e = prep_wide(ctx, times, flux, n, t0, w);
+    if (e == cudaSuccess && want_best) e = cudaMemsetAsync(key, 0, sizeof(*key), ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    KernelTimer timer(ctx);
+    for (int64_t k0 = 0; k0 < np && e == cudaSuccess; k0 += chunk) {
+        const int64_t nk = std::min<int64_t>(chunk, np - k0);
+        EqParams p = eq_params(ctx, w, n, periods + k0, nk, nbins, nbins);
+        p.width_only = 1;
+        p.sums = cs;
+        p.counts = cc;
+        e = launch_eq_fold(p, ctx->num_sms, ctx->stream);
+        if (e != cudaSuccess) break;
+        BoxCoopParams q{};
+        q.sums = cs;
+        q.counts = cc;
+        q.k_begin = k0;
+        q.rows = nk;
+        q.nbins = nbins;
+        q.w_min = bp->w_min;
+        q.w_max = bp->w_max;
+        q.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
+        q.stats = w.stats;
+        q.nstars = 1;
+        q.score = score;
+        q.best_key = want_best ? key : nullptr;
+        e = launch_box_coop(q, ctx->num_sms, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "fold and box kernels");
+    timer.stop();
+    if (want_best) {
+        e = launch_argmax_finalize(key, 1, best_index, best_score, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "argmax finalize");
+    }
+    return GPFC_OK;
 }
 
 // Quantise + fold one star in `mode`; fills p.* outputs set by the caller.
@@ -1094,8 +1246,12 @@ int gpfc_check_wait_timeout(gpfc_ctx *ctx, int64_t limit_cycles)
 int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbins, size_t *bytes)
 {
     if (!ctx || !bytes) return GPFC_EINVAL;
-    if (n < 1 || n_periods < 1 || nbins < 2 || nbins > kMaxNbinsLane)
+    if (n < 1 || n_periods < 1 || nbins < 2 || nbins > kEqMaxFine)
         return set_err(ctx, GPFC_EINVAL, "bad sizes");
+    if (wide_bins(nbins)) {
+        *bytes = box_wide_bytes(ctx, n, n_periods, nbins);
+        return GPFC_OK;
+    }
     // the larger of a fold (gpfc_fold, the epilogue search) and the warp-per-profile search
     const FoldPlan pb = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
     const FoldPlan pf = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeFold, n));
@@ -1168,6 +1324,7 @@ int gpfc_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, 
     if (rc) return rc;
     cudaSetDevice(ctx->device);
     if ((rc = take_latched(ctx))) return rc;
+    if (wide_bins(nbins)) return run_fold_wide(ctx, times, flux, n, periods, n_periods, nbins, t0, folded, counts);
     FoldParams p{};
     p.folded = folded;
     p.counts = counts;
@@ -1189,50 +1346,14 @@ int gpfc_fold_equal_count(gpfc_ctx *ctx, const double *times, const float *flux,
     cudaSetDevice(ctx->device);
     int rc = take_latched(ctx);
     if (rc) return rc;
-    const int G = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 8191) / 8192));
-    auto carve = [&](void *base, double **partial, StarStats **stats, SampleScratch *smp, long long **q,
-                     unsigned int **maxbits, int **kscale) {
-        Carver c(base);
-        *partial = c.take<double>((size_t)3 * G);
-        *stats = c.take<StarStats>(1);
-        const int64_t se = scratch_elems(n, 1);
-        smp->tau_lo = c.take<uint32_t>(se);
-        smp->tau_hi = c.take<int32_t>(se);
-        smp->x = c.take<float>(se);
-        smp->flags = c.take<uint8_t>(se / 16 + 64);
-        *q = c.take<long long>(n);
-        *maxbits = c.take<unsigned int>(1);
-        *kscale = c.take<int>(1);
-        return c.off + 256;
-    };
-    double *partial;
-    StarStats *stats;
-    SampleScratch smp{};
-    long long *q;
-    unsigned int *maxbits;
-    int *kscale;
-    rc = ensure_ws(ctx, carve(nullptr, &partial, &stats, &smp, &q, &maxbits, &kscale));
+    WideBuffers w{};
+    rc = ensure_ws(ctx, carve_wide(nullptr, n, w) + 256);
     if (rc) return rc;
-    carve(ctx->ws, &partial, &stats, &smp, &q, &maxbits, &kscale);
-    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, smp, partial, G, stats,
-                                ctx->status_dev, ctx->stream);
-    if (e == cudaSuccess) e = launch_eq_prep(smp.x, n, maxbits, q, kscale, ctx->num_sms, ctx->stream);
+    carve_wide(ctx->ws, n, w);
+    cudaError_t e = prep_wide(ctx, times, flux, n, t0, w);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
-    EqParams p{};
-    p.tau_lo = smp.tau_lo;
-    p.tau_hi = smp.tau_hi;
-    p.q = q;
-    p.n = n;
-    p.periods = periods;
-    p.np = n_periods;
-    p.nfine = nfine;
-    p.nbins = nbins;
-    p.fshift = shift_of(nfine);
-    p.ppb = ppb;
-    p.kscale = kscale;
-    p.stats = stats;
+    EqParams p = eq_params(ctx, w, n, periods, n_periods, nfine, nbins);
     p.folded = folded;
-    p.status = ctx->status_dev;
     KernelTimer timer(ctx);
     e = launch_eq_fold(p, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "two-tier fold kernel");
@@ -1247,17 +1368,26 @@ int gpfc_score_box(gpfc_ctx *ctx, const float *folded, const int32_t *counts, in
     if (!ctx) return GPFC_EINVAL;
     if (!folded || !counts || !score || !params) return set_err(ctx, GPFC_EINVAL, "NULL argument");
     if (n_periods < 1 || n_periods > (int64_t)INT32_MAX) return set_err(ctx, GPFC_EINVAL, "bad n_periods");
-    if (nbins < 2 || nbins > kMaxNbinsLane) return set_err(ctx, GPFC_EINVAL, "nbins outside [2, 1024]");
-    if ((size_t)nbins * 33 * 6 > kSmemLimit - 1024) return set_err(ctx, GPFC_ENOTSUP, "nbins too large for the box kernel");
+    if (nbins < 2 || nbins > kEqMaxFine) return set_err(ctx, GPFC_EINVAL, "nbins outside [2, %d]", kEqMaxFine);
     if (params->w_min < 1 || params->w_max < params->w_min || params->w_max > nbins)
         return set_err(ctx, GPFC_EINVAL, "box widths must satisfy 1 <= w_min <= w_max <= nbins");
     cudaSetDevice(ctx->device);
     int rc = take_latched(ctx);
     if (rc) return rc;
-    const float sigma = params->sigma > 0.0 ? (float)params->sigma : 1.0f;
+    BoxCoopParams q{};
+    q.means = folded;
+    q.counts = counts;
+    q.rows = n_periods;
+    q.nbins = nbins;
+    q.w_min = params->w_min;
+    q.w_max = params->w_max;
+    q.sigma_user = params->sigma > 0.0 ? (float)params->sigma : 1.0f;
+    q.nstars = 1;
+    q.score = score;
+    q.best_s = best_s;
+    q.best_w = best_w;
     KernelTimer timer(ctx);
-    cudaError_t e = launch_box_standalone(folded, counts, n_periods, nbins, params->w_min, params->w_max,
-                                          sigma, score, best_s, best_w, ctx->stream);
+    cudaError_t e = launch_box_coop(q, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "box kernel");
     timer.stop();
     return GPFC_OK;
@@ -1517,6 +1647,9 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
         p.w_max = bp->w_max;
         p.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
         const bool want_best = best_index || best_score;
+        if (wide_bins(nbins))
+            return run_search_box_wide(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
+                                       best_score);
         if (warp_box(ctx, nbins))
             return run_search_box_warp(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
                                        best_score);

@@ -617,21 +617,6 @@ struct LaneBins {
     __device__ __forceinline__ float2 sc(int b) const { return make_float2(s(b), c(b)); }
 };
 
-// Bins of one profile staged transposed for the standalone scorer ([bin][33]).
-struct StagedBins {
-    const float *S;
-    const uint16_t *C;
-    const int32_t *Cbig;   // the caller's counts row when a count exceeds 65535
-    bool big;
-    __device__ __forceinline__ float s(int b) const { return S[b * 33]; }
-    __device__ __forceinline__ uint32_t ci(int b) const
-    {
-        return big ? (uint32_t)max(Cbig[b], 0) : (uint32_t)C[b * 33];
-    }
-    __device__ __forceinline__ float c(int b) const { return (float)ci(b); }
-    __device__ __forceinline__ float2 sc(int b) const { return make_float2(s(b), c(b)); }
-};
-
 // Bins of one profile staged by a whole warp: (sum, count) pairs at index b + b / 8, so
 // lanes reading bins 8 apart hit distinct banks. Counts are exact in FP32 (n <= 2^24).
 struct PairBins {
@@ -1169,108 +1154,6 @@ cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ standalone box-SNR
-
-// Each warp scores 32 profiles, one per lane. The profiles are staged transposed into
-// shared memory ([bin][33] so both the coalesced staging writes and the lane-per-
-// profile reads are conflict-free), as centred sums (mean - m_ref) * count in FP32 with
-// m_ref the count-weighted mean of the profile (FP64), plus 16-bit counts.
-constexpr int kBoxWarps = 4;
-
-__global__ void __launch_bounds__(kBoxWarps * 32) box_kernel(const float *__restrict__ folded,
-                                                             const int32_t *__restrict__ counts,
-                                                             int64_t np, int nbins, int w_min,
-                                                             int w_max, float sigma, float *score,
-                                                             int32_t *best_s, int32_t *best_w)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    float *Sw = reinterpret_cast<float *>(smem) + (size_t)warp * nbins * 33;
-    uint16_t *Cw = reinterpret_cast<uint16_t *>(reinterpret_cast<float *>(smem) +
-                                                 (size_t)nwarps * nbins * 33) +
-                   (size_t)warp * nbins * 33;
-    const int64_t nblocks = (np + 31) / 32;
-    for (int64_t blk = (int64_t)blockIdx.x * nwarps + warp; blk < nblocks;
-         blk += (int64_t)gridDim.x * nwarps) {
-        const int64_t k0 = blk * 32;
-        const int nk = (int)min((int64_t)32, np - k0);
-        bool big_lane = false;
-        // stage: for each profile j, lanes walk its bins (coalesced row reads)
-        for (int j = 0; j < 32; ++j) {
-            double num = 0.0, den = 0.0;
-            if (j < nk) {
-                const float *row = folded + (size_t)(k0 + j) * nbins;
-                const int32_t *crow = counts + (size_t)(k0 + j) * nbins;
-                for (int b = lane; b < nbins; b += 32) {
-                    const int32_t c = crow[b];
-                    if (c > 0) {
-                        num += (double)row[b] * (double)c;
-                        den += (double)c;
-                    }
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                num += __shfl_xor_sync(0xffffffffu, num, o);
-                den += __shfl_xor_sync(0xffffffffu, den, o);
-            }
-            const float mref = den > 0.0 ? (float)(num / den) : 0.f;
-            bool big = false;
-            for (int b = lane; b < nbins; b += 32) {
-                float sv = 0.f;
-                uint32_t c = 0;
-                if (j < nk) {
-                    const int32_t ci = counts[(size_t)(k0 + j) * nbins + b];
-                    c = ci > 0 ? (uint32_t)ci : 0u;
-                    if (c) sv = (folded[(size_t)(k0 + j) * nbins + b] - mref) * (float)c;
-                }
-                big |= c > 65535u;
-                Sw[b * 33 + j] = sv;
-                Cw[b * 33 + j] = (uint16_t)min(c, 65535u);
-            }
-            if (__any_sync(0xffffffffu, big) && lane == j) big_lane = true;
-        }
-        __syncwarp();
-        if (lane < nk) {
-            const int64_t k = k0 + lane;
-            float sc;
-            int bs, bw;
-            const StagedBins B{Sw + lane, Cw + lane, counts + (size_t)k * nbins, big_lane};
-            box_search<8>(B, nbins, w_min, w_max, sigma, sc, bs, bw);
-            score[k] = sc;
-            if (best_s) best_s[k] = bs;
-            if (best_w) best_w[k] = bw;
-        }
-        __syncwarp();
-    }
-}
-
-cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, int64_t np, int nbins,
-                                  int w_min, int w_max, float sigma, float *score, int32_t *best_s,
-                                  int32_t *best_w, cudaStream_t st)
-{
-    static bool attr = false;
-    int warps = kBoxWarps;
-    while (warps > 1 && (size_t)warps * nbins * 33 * 6 > kSmemLimit - 1024) --warps;
-    const size_t smem = (size_t)warps * nbins * 33 * 6;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kSmemLimit - 1024));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t nblocks = (np + 31) / 32;
-    const int64_t want = (nblocks + warps - 1) / warps;
-    const int grid = (int)(want < (int64_t)sms * 2 ? want : (int64_t)sms * 2);
-    box_kernel<<<grid, warps * 32, smem, st>>>(folded, counts, np, nbins, w_min, w_max, sigma,
-                                                   score, best_s, best_w);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ box-SNR, warp per profile
 
 // A warp scores one profile at a time from the fold's centred bin sums and counts: the
@@ -1312,13 +1195,31 @@ __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxC
         if (k < 0) continue;
         const int s = p.grid_off ? star_of(p.grid_off, p.nstars, k) : 0;
         const int64_t gb = p.grid_off ? p.grid_off[s] : 0;
-        const float *srow = p.sums + (size_t)r * nbins;
+        const float *srow = p.sums ? p.sums + (size_t)r * nbins : nullptr;
+        const float *mrow = p.means ? p.means + (size_t)r * nbins : nullptr;
         const int32_t *crow = p.counts + (size_t)r * nbins;
+        float mref = 0.f;
+        if (mrow) {  // means in: centre them on the profile's count-weighted mean (FP64)
+            double num = 0.0, den = 0.0;
+            for (int b = lane; b < nbins; b += 32) {
+                const int32_t c = crow[b];
+                if (c > 0) {
+                    num += (double)mrow[b] * (double)c;
+                    den += (double)c;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                num += __shfl_xor_sync(0xffffffffu, num, o);
+                den += __shfl_xor_sync(0xffffffffu, den, o);
+            }
+            mref = den > 0.0 ? (float)(num / den) : 0.f;
+        }
         __syncwarp();  // the previous profile's readers are done
         float Stot = 0.f, Ntot = 0.f;
         int nnz = 0;
         for (int b = lane; b < nbins; b += 32) {
-            const float sv = srow[b], c = (float)max(crow[b], 0);
+            const float c = (float)max(crow[b], 0);
+            const float sv = mrow ? (c > 0.f ? (mrow[b] - mref) * c : 0.f) : srow[b];
             Bw[b + (b >> 3)] = make_float2(sv, c);
             Stot += sv;
             Ntot += c;
@@ -1369,7 +1270,7 @@ __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxC
                 ni += __shfl_xor_sync(0xffffffffu, ni, o);
             }
             float sig = p.sigma_user;
-            if (!(sig > 0.f)) sig = p.stats[s].sigma;
+            if (!(sig > 0.f) && p.stats) sig = p.stats[s].sigma;
             if (!(sig > 0.f)) sig = 1.f;
             const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
             const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
@@ -1394,7 +1295,15 @@ __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxC
     if (lane == 0 && p.best_key && cur_key) atomicMax(&p.best_key[cur_s], cur_key);
 }
 
-size_t box_coop_smem(int nbins) { return (size_t)kCoopWarps * coop_pairs(nbins) * sizeof(float2); }
+// Warps per block of the scorer: 8, fewer when 8 profiles do not fit shared memory.
+int box_coop_warps(int nbins)
+{
+    int w = kCoopWarps;
+    while (w > 1 && (size_t)w * coop_pairs(nbins) * sizeof(float2) > kSmemLimit - 1024) --w;
+    return w;
+}
+
+size_t box_coop_smem(int nbins) { return (size_t)box_coop_warps(nbins) * coop_pairs(nbins) * sizeof(float2); }
 
 cudaError_t box_coop_register()
 {
@@ -1406,12 +1315,13 @@ cudaError_t launch_box_coop(const BoxCoopParams &p, int num_sms, cudaStream_t st
     if (p.rows <= 0) return cudaSuccess;
     const size_t smem = box_coop_smem(p.nbins);
     if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
+    const int warps = box_coop_warps(p.nbins);
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, box_coop_kernel, kCoopWarps * 32, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, box_coop_kernel, warps * 32, smem);
     if (e != cudaSuccess) return e;
-    const int64_t want = (p.rows + kCoopWarps - 1) / kCoopWarps;
+    const int64_t want = (p.rows + warps - 1) / warps;
     const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms * std::max(1, occ));
-    box_coop_kernel<<<grid, kCoopWarps * 32, smem, st>>>(p);
+    box_coop_kernel<<<grid, warps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 

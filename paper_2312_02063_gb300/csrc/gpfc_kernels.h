@@ -86,15 +86,16 @@ struct FoldParams {
 // Box-SNR over profiles the fold wrote as centred sums and counts ([row][nbins]), one warp
 // per profile. Row r holds period k = slot_k[r] (skipped if < 0), or k_begin + r.
 struct BoxCoopParams {
-    const float *sums;
+    const float *sums;            // centred bin sums, or NULL when means are given
+    const float *means;           // bin means (used only where the count is > 0), or NULL
     const int32_t *counts;
     const int64_t *slot_k;
     int64_t k_begin;
     int64_t rows;
     int nbins;
     int w_min, w_max;
-    float sigma_user;             // > 0: use it; else the star's flux std (1 if that is 0)
-    const StarStats *stats;
+    float sigma_user;             // > 0: use it; else the star's flux std (1 if that is 0 or stats is NULL)
+    const StarStats *stats;       // may be NULL
     const int64_t *grid_off;      // [S+1] period offsets, or NULL (one star)
     int nstars;
     float *score;                 // [global period]
@@ -119,9 +120,6 @@ cudaError_t launch_prep(const double *times, const float *flux, const int64_t *l
                         int nstars, int64_t max_len, const double *t0s, double t0, SampleScratch smp,
                         double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st);
 cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st);
-cudaError_t launch_box_standalone(const float *folded, const int32_t *counts, int64_t np, int nbins,
-                                  int w_min, int w_max, float sigma, float *score, int32_t *best_s,
-                                  int32_t *best_w, cudaStream_t st);
 cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *key, cudaStream_t st);
 cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, int nstars, int64_t n_total,
                               int64_t np_total, int ppc, int64_t *lc_s, int64_t *grid_s, int64_t *task_off,

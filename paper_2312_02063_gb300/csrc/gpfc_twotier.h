@@ -24,7 +24,11 @@ struct EqParams {
     int ppb;                  // periods per block pass (<= kEqMaxPeriods)
     const int *kscale;        // k (device)
     const StarStats *stats;
-    float *folded;            // [np][nbins] means
+    int width_only;           // 1: equal-width fold into nfine (= nbins) bins, no merge
+    float *folded;            // [np][nbins] means (may be NULL when width_only)
+    // width_only outputs, [np][nfine] (each may be NULL)
+    int32_t *counts;          // samples per bin
+    float *sums;              // sum of (flux - f_ref) per bin
     uint32_t *status;
 };
 

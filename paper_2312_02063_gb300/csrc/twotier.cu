@@ -10,6 +10,8 @@
 //     G(u) = S(f-1) + s_f (u - C(f-1) nbins) / (c_f nbins),   C(f-1) nbins < u <= C(f) nbins,
 // S the cumulative flux sum.
 // Step 5: mean = f_ref + sum / (n / nbins).
+// With width_only set the kernel stops after step 3 and returns the fine bins themselves
+// (count, sum, mean): the equal-width fold for bin counts above the lane-private fold's.
 //
 // Design. A fine bin is one 64-bit word, count << 40 plus the flux sum (flux - f_ref) in
 // signed fixed point with a per-star quantum 2^-k, chosen so that n max|x| 2^k < 2^38:
@@ -150,6 +152,21 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
             }
         }
         __syncthreads();
+        if (p.width_only) {
+            // the fine bins are the result: counts, exact sums rounded once, means
+            for (int idx = threadIdx.x; idx < nper * nfine; idx += kEqThreads) {
+                const int pp = idx / nfine, f = idx - pp * nfine;
+                const unsigned long long w = bins[idx];
+                const int64_t c = eq_count(w);
+                const double S = (double)eq_sum(w) * quantum;
+                const size_t o = (size_t)(k0 + pp) * nfine + f;
+                if (p.folded) p.folded[o] = c ? (float)(f_ref + S / (double)c) : __int_as_float(0x7fc00000);
+                if (p.counts) p.counts[o] = (int32_t)c;
+                if (p.sums) p.sums[o] = (float)S;
+            }
+            __syncthreads();
+            continue;
+        }
         // step 4a: inclusive prefix sums of each period's fine bins (exact integers)
         for (int pp = 0; pp < nper; ++pp) {
             unsigned long long *B = bins + (size_t)pp * nfine;
