@@ -190,8 +190,10 @@ __global__ void prep_sigma_kernel(const double *partial, const long long *pmin, 
 }
 
 // Pass 4: one flag byte per group of 16 samples: 1 if every step inside the group lies in
-// [dtau0, dtau0 + 2] (a regular cadence up to the 2^-24 d rounding of tau). The fold
-// skips its per-group bin-collision check on flagged groups when the period allows it.
+// [dtau0, dtau0 + 2] (a regular cadence up to the 2^-24 d rounding of tau) and the high
+// word of tau is the same for all 16 (it changes every 2^32 units, ~256 d). The fold
+// skips its per-group bin-collision check on flagged groups when the period allows it,
+// and forms their phases with one th * F_lo product per group.
 // grid = (G, stars).
 __global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratch smp,
                                   const StarStats *stats)
@@ -208,11 +210,13 @@ __global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratc
         const int64_t j0 = q * 16;
         bool reg = d0 > 0 && j0 + 16 <= len;
         if (reg) {
-            long long prev = ((long long)smp.tau_hi[base + j0] << 32) | smp.tau_lo[base + j0];
+            const int32_t th0 = smp.tau_hi[base + j0];
+            long long prev = ((long long)th0 << 32) | smp.tau_lo[base + j0];
             for (int k = 1; k < 16; ++k) {
-                const long long cur = ((long long)smp.tau_hi[base + j0 + k] << 32) | smp.tau_lo[base + j0 + k];
+                const int32_t th = smp.tau_hi[base + j0 + k];
+                const long long cur = ((long long)th << 32) | smp.tau_lo[base + j0 + k];
                 const long long d = cur - prev;
-                reg &= (d >= d0) & (d <= d0 + 2);
+                reg &= (d >= d0) & (d <= d0 + 2) & (th == th0);
                 prev = cur;
             }
         }
@@ -315,6 +319,59 @@ __device__ __forceinline__ void load_tile_regs(uint32_t stl, uint32_t sth, uint3
         T.a[q] = lds_u32x4(stl + o);
         T.h[q] = lds_u32x4(sth + o);
         T.f[q] = lds_f32x4(sx + o);
+    }
+}
+
+// Tile data of U consecutive samples of a regular group. The prep pass flags a group
+// regular only if the high word of tau is the same for all its samples, so only the
+// first one is read, and th * F_lo is formed once per group.
+template <int U>
+struct TileRegsR {
+    uint4 a[U / 4];   // tau low words
+    float4 f[U / 4];  // flux - f_ref
+    uint32_t th;      // tau high word of the group
+};
+
+template <int U>
+__device__ __forceinline__ void load_tile_regs_r(uint32_t stl, uint32_t sth, uint32_t sx, int i, TileRegsR<U> &T)
+{
+#pragma unroll
+    for (int q = 0; q < U / 4; ++q) {
+        const uint32_t o = 4u * (uint32_t)(i + 4 * q);
+        T.a[q] = lds_u32x4(stl + o);
+        T.f[q] = lds_f32x4(sx + o);
+    }
+    T.th = lds_u32(sth + 4u * (uint32_t)i);
+}
+
+// phase_bin with the th * F_lo term of the phase's high word given
+template <bool POW2>
+__device__ __forceinline__ uint32_t phase_bin_th(uint32_t tl, uint32_t thF, uint32_t Fl, uint32_t Fh,
+                                                 uint32_t nbins, int shift)
+{
+    const uint32_t hi = __umulhi(tl, Fl) + thF + tl * Fh;
+    if (POW2) return hi >> shift;
+    const uint32_t lo = tl * Fl;
+    const unsigned long long t =
+        (unsigned long long)hi * nbins + (unsigned long long)__umulhi(lo, nbins);
+    return (uint32_t)(t >> 32);
+}
+
+template <bool POW2, int U>
+__device__ __forceinline__ void bins_from_regs_r(const TileRegsR<U> &T, uint32_t Fl, uint32_t Fh, uint32_t nbins,
+                                                 int shift, uint32_t (&b)[U], float (&x)[U])
+{
+    const uint32_t thF = T.th * Fl;
+#pragma unroll
+    for (int q = 0; q < U / 4; ++q) {
+        b[4 * q + 0] = phase_bin_th<POW2>(T.a[q].x, thF, Fl, Fh, nbins, shift);
+        b[4 * q + 1] = phase_bin_th<POW2>(T.a[q].y, thF, Fl, Fh, nbins, shift);
+        b[4 * q + 2] = phase_bin_th<POW2>(T.a[q].z, thF, Fl, Fh, nbins, shift);
+        b[4 * q + 3] = phase_bin_th<POW2>(T.a[q].w, thF, Fl, Fh, nbins, shift);
+        x[4 * q + 0] = T.f[q].x;
+        x[4 * q + 1] = T.f[q].y;
+        x[4 * q + 2] = T.f[q].z;
+        x[4 * q + 3] = T.f[q].w;
     }
 }
 
@@ -441,23 +498,23 @@ __device__ __forceinline__ void fold_run_regular(uint32_t stl, uint32_t sth, uin
     // the tile data of group `fetch` into Tn, compute the next group's bins from Tc into
     // (nb, nx), then write the current group back. Two stages per iteration with the
     // register roles swapped, so nothing is copied between iterations.
-    auto stage = [&](const uint32_t (&cb)[U], const float (&cx)[U], const TileRegs<U> &Tc, TileRegs<U> &Tn,
+    auto stage = [&](const uint32_t (&cb)[U], const float (&cx)[U], const TileRegsR<U> &Tc, TileRegsR<U> &Tn,
                      uint32_t (&nb)[U], float (&nx)[U], int fetch) {
         float sm[U];
         uint32_t c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) st.load(cb[u], sm[u], c[u]);
-        load_tile_regs<U>(stl, sth, sx, U * fetch, Tn);
-        bins_from_regs<POW2, U>(Tc, Fl, Fh, nbins, shift, nb, nx);
+        load_tile_regs_r<U>(stl, sth, sx, U * fetch, Tn);
+        bins_from_regs_r<POW2, U>(Tc, Fl, Fh, nbins, shift, nb, nx);
 #pragma unroll
         for (int u = 0; u < U; ++u) st.put(cb[u], sm[u] + cx[u], c[u] + 1u);
     };
     uint32_t b0[U], b1[U];
     float x0[U], x1[U];
-    TileRegs<U> T0, T1;
-    load_tile_regs<U>(stl, sth, sx, 0, T0);
-    bins_from_regs<POW2, U>(T0, Fl, Fh, nbins, shift, b0, x0);  // group 0
-    load_tile_regs<U>(stl, sth, sx, ng > 1 ? U : 0, T1);        // group 1
+    TileRegsR<U> T0, T1;
+    load_tile_regs_r<U>(stl, sth, sx, 0, T0);
+    bins_from_regs_r<POW2, U>(T0, Fl, Fh, nbins, shift, b0, x0);  // group 0
+    load_tile_regs_r<U>(stl, sth, sx, ng > 1 ? U : 0, T1);        // group 1
     int g = 0;
 #pragma unroll 1
     for (; g + 1 < ng; g += 2) {
@@ -666,16 +723,43 @@ __device__ __forceinline__ uint32_t select_bits(uint32_t m, uint32_t a, uint32_t
     return d;
 }
 
+// Two FP32 lanes in one 64-bit register pair, and element-wise IEEE round-to-nearest
+// add and multiply on both (one instruction for two boxes).
+__device__ __forceinline__ unsigned long long f2pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // QCHECK false is allowed when w_max is below the number of non-empty bins: then no box
 // holds every sample (n_out >= 1), and a box of empty bins has D = 0 exactly (its bins add
 // exact zeros to the prefix), so it never beats anything; the q >= 1 test can go.
-template <int R, bool QCHECK, class Bins>
+// PACKED: the steady state of the unchecked walk evaluates starts in pairs with f32x2
+// arithmetic (the same IEEE operations, so the same results).
+template <int R, bool QCHECK, class Bins, bool PACKED = false>
 __device__ __forceinline__ void box_walk(const Bins &B, int nbins, int w_min, int w_max, float Stot, float Ntot,
                                          int s0_first, int s0_stride, float &bv, int &bkey)
 {
     for (int s0 = s0_first; s0 < nbins; s0 += s0_stride) {
         const bool full = s0 + R <= nbins;
-        float bA[R], bN[R];     // prefix values at each start
+        float bA[R] = {}, bN[R] = {};  // prefix values at each start (set as the walk enters it)
         // best per start, kept as E = D |D| and q = n_in n_out (v = sign(E) sqrt(|E| / q), so
         // E1 q2 > E2 q1 orders two boxes as v does without a square root)
         float rE[R], rq[R];
@@ -740,6 +824,40 @@ __device__ __forceinline__ void box_walk(const Bins &B, int nbins, int w_min, in
                 step(t);
 #pragma unroll
                 for (int r = 0; r < R; ++r) eval(r, t, true);
+            }
+        } else if (PACKED) {
+            unsigned long long nbN2[R / 2], cN2[R / 2], nbA2[R / 2];
+#pragma unroll
+            for (int h = 0; h < R / 2; ++h) {
+                nbN2[h] = f2pack(-bN[2 * h], -bN[2 * h + 1]);
+                cN2[h] = f2pack(Ntot + bN[2 * h], Ntot + bN[2 * h + 1]);
+                nbA2[h] = f2pack(-bA[2 * h], -bA[2 * h + 1]);
+            }
+            for (int t = ta; t < tb; ++t) {
+                step(t);
+                const unsigned long long RN2 = f2pack(runN, runN), nRN2 = f2pack(-runN, -runN);
+                const unsigned long long RA2 = f2pack(runA, runA);
+#pragma unroll
+                for (int h = 0; h < R / 2; ++h) {
+                    const unsigned long long q2 = f2mul(f2add(RN2, nbN2[h]), f2add(cN2[h], nRN2));
+                    float D0, D1;
+                    f2unpack(f2add(RA2, nbA2[h]), D0, D1);
+                    const unsigned long long E2 = f2pack(D0 * fabsf(D0), D1 * fabsf(D1));
+                    float l0, l1, g0, g1, q0, q1, E0, E1;
+                    f2unpack(f2mul(E2, f2pack(rq[2 * h], rq[2 * h + 1])), l0, l1);
+                    f2unpack(f2mul(f2pack(rE[2 * h], rE[2 * h + 1]), q2), g0, g1);
+                    f2unpack(q2, q0, q1);
+                    f2unpack(E2, E0, E1);
+                    const uint32_t m0 = mask_gt(l0, g0), m1 = mask_gt(l1, g1);
+                    rE[2 * h] = __uint_as_float(select_bits(m0, __float_as_uint(E0), __float_as_uint(rE[2 * h])));
+                    rq[2 * h] = __uint_as_float(select_bits(m0, __float_as_uint(q0), __float_as_uint(rq[2 * h])));
+                    rt[2 * h] = (int)select_bits(m0, (uint32_t)t, (uint32_t)rt[2 * h]);
+                    rE[2 * h + 1] =
+                        __uint_as_float(select_bits(m1, __float_as_uint(E1), __float_as_uint(rE[2 * h + 1])));
+                    rq[2 * h + 1] =
+                        __uint_as_float(select_bits(m1, __float_as_uint(q1), __float_as_uint(rq[2 * h + 1])));
+                    rt[2 * h + 1] = (int)select_bits(m1, (uint32_t)t, (uint32_t)rt[2 * h + 1]);
+                }
             }
         } else {
             float cN[R];  // N + Pn(start): n_out = cN - Pn(end), exact in integers
@@ -1182,7 +1300,7 @@ __device__ __forceinline__ int star_of(const int64_t *grid_off, int nstars, int6
 
 __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxCoopParams p)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int nbins = p.nbins;
@@ -1234,7 +1352,8 @@ __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxC
         float bv = -INFINITY;
         int bkey = 0x7fffffff;
         if (p.w_max < nnz)
-            box_walk<kCoopR, false>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
+            box_walk<kCoopR, false, PairBins, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR,
+                                                   bv, bkey);
         else
             box_walk<kCoopR, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
         for (int o = 16; o > 0; o >>= 1) {
