@@ -38,7 +38,7 @@ SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, pe
 # DRAM bytes (read + write) of one fold launch (one chunk of the pipelined box search, all
 # resident blocks' periods: 14,592 at 3 warps x 152 SMs), from an ncu capture of the same
 # light curve.
-FOLD_DRAM_BYTES_PER_LAUNCH = 2.113024e6 + 21.418240e6  # profiles/fold_kernel_sums_kepler62835.md
+FOLD_DRAM_BYTES_PER_LAUNCH = 1.979392e6 + 21.214464e6  # profiles/fold_kernel_sums_kepler62835.md
 L2_FLUSH_BYTES = 256 << 20
 
 
