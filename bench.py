@@ -35,10 +35,10 @@ NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
 SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, per SM
-# DRAM bytes (read + write) of one fold launch (one chunk of the pipelined box search, all
-# resident blocks' periods: 14,592 at 3 warps x 152 SMs), from an ncu capture of the same
-# light curve.
-FOLD_DRAM_BYTES_PER_LAUNCH = 1.979392e6 + 21.214464e6  # profiles/fold_kernel_sums_kepler62835.md
+# DRAM bytes (read + write) per period of the one-kernel search (fold + box-SNR) of the same
+# light curve, from an ncu capture of a 58,368-period search; the search's traffic grows
+# with the number of periods (ring writes, one light-curve pass per task).
+SEARCH_DRAM_BYTES_PER_PERIOD = (38.126080e6 + 206.458624e6) / 58368  # profiles/fold_kernel_search_kepler62835.md
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -332,6 +332,8 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    ctx.set_box_path(g.BOX_FUSED)  # fold and box-SNR in one kernel (the default for one star)
+
     def step():
         g.gpfc_search(ctx, t_d, f_d, p_d, NBINS, lc.t0, g.SCORER_BOX, 1, W_MAX, 0.0, score, bi, bs)
 
@@ -406,8 +408,8 @@ def run_gpu(args, rank, world, local_rank):
         sms = ctx.num_sms
         peak_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
         kmean = statistics.mean(kernel_ms)
-        # the fold's own launches (on the library's fold stream, scorer running beside them):
-        # all n * N_PERIODS updates of a step over the summed launch durations
+        # the search kernel's own launch (fold + box-SNR): all n * N_PERIODS updates of a step
+        # over its duration
         fold_step_ms = statistics.mean(fold_ms)
         launches = fold_launches[0]
         achieved = n * N_PERIODS / (fold_step_ms * 1e-3) / 1e9
@@ -426,10 +428,11 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
-            "roofline": {"bound": "alu", "kernel": "fold_kernel<sums>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "fold_kernel<search> (fold + box-SNR)", "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
-                         "traffic": FOLD_DRAM_BYTES_PER_LAUNCH,
-                         "traffic_basis": "ncu dram__bytes_read+write of one full-chunk fold launch",
+                         "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None
+                         else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS,
+                         "traffic_basis": "ncu dram__bytes_read+write of a 58,368-period search, scaled by periods",
                          "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
                          "search_ms": kmean,
                          "peak_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} bin updates/clk "
@@ -437,8 +440,8 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
-            # per step: 4 prep kernels, a fold and a box scorer per chunk, the argmax
-            "gpu_launches": (5 + 2 * launches) * args.steps,
+            # per step: 4 prep kernels, the search kernel, the argmax
+            "gpu_launches": (5 + launches) * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }

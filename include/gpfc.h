@@ -383,10 +383,15 @@ typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;
  * held on chip (no profile traffic, but only as many warps as the fold's bins leave room
  * for). GPFC_BOX_WARP: the fold writes each chunk's centred bin sums and counts to an
  * L2-resident buffer and a separate kernel scores them, one warp per profile, at full
- * occupancy. GPFC_BOX_AUTO (the default) takes GPFC_BOX_WARP for nbins >= 256, else the
- * epilogue. Scores agree within the box tolerance either way; a batched search and the
- * per-star search use the same path and agree bit for bit. */
-typedef enum { GPFC_BOX_AUTO = 0, GPFC_BOX_EPILOGUE = 1, GPFC_BOX_WARP = 2 } gpfc_box_path;
+ * occupancy. GPFC_BOX_FUSED: one kernel; each fold block has one more warp that scores
+ * the block's previous task, one profile at a time, from a two-slot ring of sums and
+ * counts in L2, and the fold warps take leftover profiles when they would otherwise wait
+ * for a slot (single-star gpfc_search only; when the extra warp's shared memory does not
+ * fit, GPFC_BOX_WARP is used). GPFC_BOX_AUTO (the default) takes GPFC_BOX_FUSED for a
+ * single star and GPFC_BOX_WARP for a batch from nbins >= 256, else the epilogue. The box
+ * scores of the warp and fused paths are bit-identical; a batched search and the per-star
+ * search agree bit for bit whatever the path. */
+typedef enum { GPFC_BOX_AUTO = 0, GPFC_BOX_EPILOGUE = 1, GPFC_BOX_WARP = 2, GPFC_BOX_FUSED = 3 } gpfc_box_path;
 int gpfc_set_box_path(gpfc_ctx *ctx, int path);
 
 int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,

@@ -27,9 +27,10 @@ __all__ = [
 
 SCORER_BOX = 0
 SCORER_CNN = 1
-BOX_AUTO = 0       # the warp-per-profile kernel for nbins >= 256, else the fold's epilogue
+BOX_AUTO = 0       # from 256 bins the one-kernel search (a batch: the separate kernel), else the epilogue
 BOX_EPILOGUE = 1   # box search inside the fold kernel
 BOX_WARP = 2       # separate box kernel, one warp per profile
+BOX_FUSED = 3      # one kernel: an extra warp per fold block scores the block's previous task
 
 STATUS = {0: "GPFC_OK", -1: "GPFC_EINVAL", -2: "GPFC_ENOMEM", -3: "GPFC_ECUDA", -4: "GPFC_ERANGE",
           -5: "GPFC_ETIMEOUT", -6: "GPFC_ENOTSUP"}

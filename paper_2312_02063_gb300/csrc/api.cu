@@ -470,7 +470,8 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
 // The box search runs in its own warp-per-profile kernel (else in the fold's epilogue).
 bool warp_box(const gpfc_ctx *ctx, int nbins)
 {
-    return ctx->box_path == GPFC_BOX_WARP || (ctx->box_path == GPFC_BOX_AUTO && nbins >= 256);
+    return ctx->box_path == GPFC_BOX_WARP || ctx->box_path == GPFC_BOX_FUSED ||
+           (ctx->box_path == GPFC_BOX_AUTO && nbins >= 256);
 }
 
 // The warp-per-profile box search as a two-stage pipeline forked off stream st: chunk i is
@@ -522,6 +523,91 @@ cudaError_t timed_fold(gpfc_ctx *ctx, cudaStream_t sf, Launch launch)
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], sf);
     if (e == cudaSuccess) ++ctx->fold_ev_used;
     return e;
+}
+
+// Plan of the one-kernel search (grid of resident search blocks), or false if its block
+// does not fit.
+bool fused_plan(gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, FoldPlan &pl)
+{
+    pl = plan_fold(ctx, n, np, nbins, find_tuned(ctx, nbins, kModeFold, n));
+    const int bps = search_blocks_per_sm(nbins, pl.warps, pl.layout, pl.tile);
+    if (bps < 1) return false;
+    pl.bps = bps;
+    pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms * bps);
+    return true;
+}
+
+struct FusedBuffers {
+    FoldBuffers fb;
+    float *ring_s;
+    int32_t *ring_c;
+    int64_t *ring_k;
+};
+
+size_t carve_fused(void *base, const FoldPlan &pl, int64_t n, int nbins, FusedBuffers &B)
+{
+    Carver c(base);
+    FoldBuffers tmp{};
+    uint8_t *fold_base = c.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, tmp));
+    if (base) carve_fold(fold_base, pl, n, 1, nbins, B.fb);
+    const size_t rows = (size_t)pl.grid * 2 * pl.ppc;
+    B.ring_s = c.take<float>(rows * nbins);
+    B.ring_c = c.take<int32_t>(rows * nbins);
+    B.ring_k = c.take<int64_t>(rows);
+    return c.off + 256;
+}
+
+// Fold + box-SNR search of one star in one kernel (kModeSearch). Returns 1 (nothing
+// enqueued) when the search block does not fit.
+int run_search_box_fused(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
+                         int64_t np, int32_t nbins, double t0, const gpfc_box_params *bp, float *score,
+                         int64_t *best_index, float *best_score)
+{
+    FoldPlan pl{};
+    if (!fused_plan(ctx, n, np, nbins, pl)) return 1;
+    FusedBuffers B{};
+    int rc = ensure_ws(ctx, carve_fused(nullptr, pl, n, nbins, B));
+    if (rc) return rc;
+    carve_fused(ctx->ws, pl, n, nbins, B);
+    const bool want_best = best_index || best_score;
+    cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, B.fb.smp, B.fb.partial, pl.G,
+                                B.fb.stats, ctx->status_dev, ctx->stream);
+    if (e == cudaSuccess && want_best) e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
+    FoldParams p{};
+    p.smp = B.fb.smp;
+    p.n = n;
+    p.periods = periods;
+    p.np = np;
+    p.ntasks = pl.ntasks;
+    p.nstars = 1;
+    p.stats = B.fb.stats;
+    p.nbins = nbins;
+    p.shift = shift_of(nbins);
+    p.warps = pl.warps;
+    p.chunk = pl.chunk;
+    p.layout = pl.layout;
+    p.tile = pl.tile;
+    p.ws_sc = B.fb.ws_sc;
+    p.ws_cnt = B.fb.ws_cnt;
+    p.sums = B.ring_s;
+    p.counts = B.ring_c;
+    p.slot_k = B.ring_k;
+    p.score = score;
+    p.w_min = bp->w_min;
+    p.w_max = bp->w_max;
+    p.sigma_user = bp->sigma > 0.0 ? (float)bp->sigma : 0.f;
+    p.best_key = want_best ? B.fb.key : nullptr;
+    p.status = ctx->status_dev;
+    KernelTimer timer(ctx);
+    e = timed_fold(ctx, ctx->stream, [&] { return launch_fold(p, kModeSearch, pl.grid, ctx->stream); });
+    if (e != cudaSuccess) return cuda_err(ctx, e, "search kernel");
+    timer.stop();
+    if (want_best) {
+        e = launch_argmax_finalize(B.fb.key, 1, best_index, best_score, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "argmax finalize");
+    }
+    return GPFC_OK;
 }
 
 // Workspace of run_search_box_warp: the fold buffers, two chunks of sums and counts.
@@ -1190,7 +1276,7 @@ int gpfc_set_autotune(gpfc_ctx *ctx, int enable)
 int gpfc_set_box_path(gpfc_ctx *ctx, int path)
 {
     if (!ctx) return GPFC_EINVAL;
-    if (path < GPFC_BOX_AUTO || path > GPFC_BOX_WARP) return set_err(ctx, GPFC_EINVAL, "box path %d unknown", path);
+    if (path < GPFC_BOX_AUTO || path > GPFC_BOX_FUSED) return set_err(ctx, GPFC_EINVAL, "box path %d unknown", path);
     ctx->box_path = path;
     return GPFC_OK;
 }
@@ -1252,11 +1338,17 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
         *bytes = box_wide_bytes(ctx, n, n_periods, nbins);
         return GPFC_OK;
     }
-    // the larger of a fold (gpfc_fold, the epilogue search) and the warp-per-profile search
+    // the largest of a fold (gpfc_fold, the epilogue search), the warp-per-profile search
+    // and the one-kernel search
     const FoldPlan pb = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
     const FoldPlan pf = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeFold, n));
     FoldBuffers fb{};
     *bytes = std::max(carve_fold(nullptr, pb, n, 1, nbins, fb), box_warp_bytes(pf, n, n_periods, nbins));
+    FoldPlan ps{};
+    if (fused_plan(ctx, n, n_periods, nbins, ps)) {
+        FusedBuffers B{};
+        *bytes = std::max(*bytes, carve_fused(nullptr, ps, n, nbins, B));
+    }
     return GPFC_OK;
 }
 
@@ -1650,9 +1742,15 @@ int gpfc_search(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n
         if (wide_bins(nbins))
             return run_search_box_wide(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
                                        best_score);
-        if (warp_box(ctx, nbins))
+        if (warp_box(ctx, nbins)) {
+            if (ctx->box_path != GPFC_BOX_WARP) {
+                rc = run_search_box_fused(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
+                                          best_score);
+                if (rc != 1) return rc;
+            }
             return run_search_box_warp(ctx, times, flux, n, periods, n_periods, nbins, t0, bp, score, best_index,
                                        best_score);
+        }
         FoldBuffers fb{};
         rc = run_fold(ctx, times, flux, n, periods, n_periods, nbins, t0, kModeBox, p, want_best, &fb);
         if (rc) return rc;

@@ -957,16 +957,261 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// ------------------------------------------------------------------ box-SNR, warp per profile
+
+// A warp scores one profile at a time from the fold's centred bin sums and counts: the
+// profile is staged as PairBins, lane L walks the blocks of 8 starts L, L + 32, ... and
+// the lanes' winners merge by the walk's own rule (larger v, then smaller w, then smaller
+// s). The winner is re-evaluated with double-float sums spread over the warp. Unlike the
+// fold's own epilogue, the search here runs at full occupancy.
+constexpr int kCoopR = 8;
+
+__device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float hi2, float lo2)
+{
+    two_sum_acc(hi, lo, hi2);
+    lo += lo2;
+}
+
+__device__ __forceinline__ int star_of(const int64_t *grid_off, int nstars, int64_t k)
+{
+    int lo = 0, hi = nstars - 1;
+    while (lo < hi) {  // the last star whose range starts at or before k
+        const int mid = (lo + hi + 1) >> 1;
+        if (grid_off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Box-SNR of row r of p's profile buffer (period k >= 0) by the calling warp, staged in Bw
+// as PairBins: lane L walks the blocks of 8 starts L, L + 32, ..., the lanes' winners merge
+// by the walk's own rule (larger v, then smaller w, then smaller s), and the winner is
+// re-evaluated with double-float sums spread over the warp. Lane 0 writes the outputs and
+// folds the period's argmax key into (cur_s, cur_key).
+__device__ __noinline__ void score_row(const BoxCoopParams &p, int64_t r, int64_t k, float2 *Bw, int lane,
+                                       int &cur_s, unsigned long long &cur_key)
+{
+    const int nbins = p.nbins;
+    const PairBins B{Bw};
+    const int s = p.grid_off ? star_of(p.grid_off, p.nstars, k) : 0;
+    const int64_t gb = p.grid_off ? p.grid_off[s] : 0;
+    const float *srow = p.sums ? p.sums + (size_t)r * nbins : nullptr;
+    const float *mrow = p.means ? p.means + (size_t)r * nbins : nullptr;
+    const int32_t *crow = p.counts + (size_t)r * nbins;
+    float mref = 0.f;
+    if (mrow) {  // means in: centre them on the profile's count-weighted mean (FP64)
+        double num = 0.0, den = 0.0;
+        for (int b = lane; b < nbins; b += 32) {
+            const int32_t c = crow[b];
+            if (c > 0) {
+                num += (double)mrow[b] * (double)c;
+                den += (double)c;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        mref = den > 0.0 ? (float)(num / den) : 0.f;
+    }
+    __syncwarp();  // the previous profile's readers are done
+    float Stot = 0.f, Ntot = 0.f;
+    int nnz = 0;
+    // 256 bins at a time, every load issued before any is used: one L2 round trip per
+    // 256 bins (a lone warp per scheduler cannot hide eight in a row)
+    for (int b0 = 0; b0 < nbins; b0 += 256) {
+        float vv[8];
+        int32_t cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + 32 * u + lane;
+            cv[u] = b < nbins ? crow[b] : 0;
+            vv[u] = b < nbins ? (mrow ? mrow[b] : srow[b]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + 32 * u + lane;
+            if (b < nbins) {
+                const float c = (float)max(cv[u], 0);
+                const float sv = mrow ? (c > 0.f ? (vv[u] - mref) * c : 0.f) : vv[u];
+                Bw[b + (b >> 3)] = make_float2(sv, c);
+                Stot += sv;
+                Ntot += c;
+                nnz += c > 0.f;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // a butterfly leaves the same totals in every lane
+        Stot += __shfl_xor_sync(0xffffffffu, Stot, o);
+        Ntot += __shfl_xor_sync(0xffffffffu, Ntot, o);
+        nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+    }
+    __syncwarp();
+    float bv = -INFINITY;
+    int bkey = 0x7fffffff;
+    if (p.w_max < nnz)
+        box_walk<kCoopR, false, PairBins, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR,
+                                               bv, bkey);
+    else
+        box_walk<kCoopR, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int okey = __shfl_xor_sync(0xffffffffu, bkey, o);
+        const bool take = (ov > bv) | ((ov == bv) & (okey < bkey));
+        bv = take ? ov : bv;
+        bkey = take ? okey : bkey;
+    }
+    float sc = -INFINITY;
+    int bs = -1, bw = -1;
+    if (bkey != 0x7fffffff) {
+        bw = bkey >> 12;
+        bs = bkey & 4095;
+        float sth = 0.f, stl = 0.f, sih = 0.f, sil = 0.f;
+        uint32_t nt = 0u, ni = 0u;
+        for (int b = lane; b < nbins; b += 32) {
+            const float2 v = B.sc(b);
+            const uint32_t c = (uint32_t)v.y;
+            two_sum_acc(sth, stl, v.x);
+            nt += c;
+            int d = b - bs;
+            d += d < 0 ? nbins : 0;
+            if (d < bw) {
+                two_sum_acc(sih, sil, v.x);
+                ni += c;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            two_sum_merge(sth, stl, __shfl_xor_sync(0xffffffffu, sth, o), __shfl_xor_sync(0xffffffffu, stl, o));
+            two_sum_merge(sih, sil, __shfl_xor_sync(0xffffffffu, sih, o), __shfl_xor_sync(0xffffffffu, sil, o));
+            nt += __shfl_xor_sync(0xffffffffu, nt, o);
+            ni += __shfl_xor_sync(0xffffffffu, ni, o);
+        }
+        float sig = p.sigma_user;
+        if (!(sig > 0.f) && p.stats) sig = p.stats[s].sigma;
+        if (!(sig > 0.f)) sig = 1.f;
+        const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
+        const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
+        sc = (float)((St * Ni - Si * Nt) / ((double)sig * sqrt(Nt * Ni * No)));
+    }
+    if (lane == 0) {
+        p.score[k] = sc;
+        if (p.best_s) p.best_s[k] = bs;
+        if (p.best_w) p.best_w[k] = bw;
+        if (p.best_key) {
+            const unsigned long long key = argmax_key(sc, k - gb);
+            if (s != cur_s) {
+                if (cur_key) atomicMax(&p.best_key[cur_s], cur_key);
+                cur_s = s;
+                cur_key = key;
+            } else {
+                cur_key = key > cur_key ? key : cur_key;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fold + box-SNR in one kernel
+
+// Work of the box-SNR scorer inside a search block. Tickets number the rows of the block's
+// tasks in order (ticket t = row t % ppc of the block's task t / ppc); a warp takes the next
+// ticket with a compare-and-swap, never one at or past `limit`.
+__device__ __forceinline__ int take_ticket(int *ticket, int limit)
+{
+    int t = *reinterpret_cast<volatile int *>(ticket);
+    while (t < limit) {
+        const int old = atomicCAS(ticket, t, t + 1);
+        if (old == t) return t;
+        t = old;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Named barrier that returns the OR of the participants' predicates (the same for all).
+__device__ __forceinline__ bool named_bar_or(int id, int threads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+// Shared state of a search block: the task each ring slot last received (-1: none yet),
+// the rows scored in each slot since the start (slot b is free for task i once
+// done[b] >= (i / 2) * ppc), and the next ticket. All three only grow.
+struct SearchShared {
+    int pub[2];
+    int done[2];
+    int ticket;
+};
+
+// Score the row of ticket t (its task already published) with the calling warp; the ring
+// slot's done count goes up once the row's staging reads are over.
+__device__ __forceinline__ void score_ticket(const FoldParams &p, SearchShared &sh, int t, int ppc, float2 *Bw,
+                                             int lane, int &cur_s, unsigned long long &cur_key)
+{
+    const int task_i = t / ppc, row = t - task_i * ppc, b = task_i & 1;
+    const size_t base = ((size_t)blockIdx.x * 2 + b) * ppc;
+    const int64_t k = p.slot_k[base + row];
+    if (k >= 0) {
+        BoxCoopParams q{};
+        q.sums = p.sums + base * p.nbins;
+        q.counts = p.counts + base * p.nbins;
+        q.nbins = p.nbins;
+        q.w_min = p.w_min;
+        q.w_max = p.w_max;
+        q.sigma_user = p.sigma_user;
+        q.stats = p.stats;
+        q.grid_off = p.grid_off;
+        q.nstars = p.nstars;
+        q.score = p.score;
+        q.best_s = p.best_s;
+        q.best_w = p.best_w;
+        q.best_key = p.best_key;
+        score_row(q, row, k, Bw, lane, cur_s, cur_key);
+    }
+    __syncwarp();
+    if (lane == 0) atomicAdd(&sh.done[b], 1);
+}
+
+// Wait (bounded, giving up on abort) until `*flag` >= `want`; one lane reads it.
+__device__ __forceinline__ bool wait_flag(const int *flag, int want, const int *abort_flag, uint32_t *status)
+{
+    const long long start = clock64();
+    while (*reinterpret_cast<const volatile int *>(flag) < want) {
+        if (*reinterpret_cast<const volatile int *>(abort_flag)) return false;
+        if (clock64() - start > kWaitLimitCycles) {
+            report_error(status, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
 template <int MODE, bool POW2, int LAYOUT, int MAXW>
 __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort;
+    __shared__ SearchShared sh;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nbins = p.nbins;
     const int ppc = 32 * p.warps;
     const int tile = p.tile;
+    // block barrier of the fold warps (in kModeSearch the scorer warp is not among them)
+    auto fold_sync = [&]() {
+        if (MODE == kModeSearch) named_bar_sync(1, 32 * p.warps);
+        else __syncthreads();
+    };
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     uint32_t *tl_buf = reinterpret_cast<uint32_t *>(smem + 128);
@@ -991,6 +1236,9 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         mbar_init(&bars[1], 1);
         fence_mbar_init();
         s_abort = 0;
+        sh.pub[0] = sh.pub[1] = -1;
+        sh.done[0] = sh.done[1] = 0;
+        sh.ticket = 0;
     }
     __syncthreads();
     uint32_t parity_bits = 0u;  // bit b: phase parity of buffer b
@@ -1002,7 +1250,30 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         const int64_t t = *p.ntasks_dev;
         task_end = t < task_end ? t : task_end;
     }
-    for (int64_t task = p.task_begin + blockIdx.x; task < task_end; task += gridDim.x) {
+    // kModeSearch: this block's tasks, their rows as tickets, and the warps' scorer staging
+    const int64_t first_task = p.task_begin + blockIdx.x;
+    const int my_tasks = first_task < task_end ? (int)((task_end - first_task + gridDim.x - 1) / gridDim.x) : 0;
+    float2 *Bw = reinterpret_cast<float2 *>(smem + p.stage_off) + (size_t)warp * coop_pairs(nbins);
+    int cur_s = -1;
+    unsigned long long cur_key = 0ull;
+    if (MODE == kModeSearch && warp == p.warps) {
+        // the scorer warp: take tickets in order, wait for each one's task to be published
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = take_ticket(&sh.ticket, my_tasks * ppc);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t < 0) break;
+            bool ok = true;
+            if (lane == 0) ok = wait_flag(&sh.pub[(t / ppc) & 1], t / ppc, &s_abort, p.status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;  // the fold warps aborted, or a timeout
+            __threadfence_block();
+            score_ticket(p, sh, t, ppc, Bw, lane, cur_s, cur_key);
+        }
+        if (lane == 0 && p.best_key && cur_key) atomicMax(&p.best_key[cur_s], cur_key);
+        return;
+    }
+    int iter = 0;  // index of the task within this block's sequence
+    for (int64_t task = first_task; task < task_end; task += gridDim.x, ++iter) {
         // resolve the star of this task and its period block
         int s = 0;
         int64_t tbase = 0;
@@ -1055,7 +1326,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
-        __syncthreads();  // previous task's readers are done with both buffers
+        fold_sync();  // previous task's readers are done with both buffers
         if (threadIdx.x == 0 && ntiles > 0) {  // a star without samples issues nothing
             issue(0, 0);
             if (ntiles > 1) issue(1, 1);
@@ -1114,8 +1385,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     }
                 }
             }
-            __syncthreads();
-            if (s_abort) {
+            fold_sync();
+            if (*reinterpret_cast<volatile int *>(&s_abort)) {
                 if (threadIdx.x == 0) {
                     // let this block's bulk copies in flight (tiles t and t + 1) land first
                     mbar_wait_bounded(&bars[buf], ((parity_bits >> buf) & 1u) ^ 1u);
@@ -1134,13 +1405,59 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             if (kvalid || p.slot_k) {
                 const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
                 for (int b = 0; b < nbins; ++b) {
-                    uint32_t c = over ? wcn_cta[(size_t)b * ppc] : st.count((uint32_t)b);
+                    float S;
+                    uint32_t c;
+                    st.load((uint32_t)b, S, c);
+                    if (over) c = wcn_cta[(size_t)b * ppc];
                     if (!kvalid) c = 0u;
-                    const float S = st.sum((uint32_t)b);
                     if (p.folded) p.folded[(size_t)row * nbins + b] = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
                     if (p.sums) p.sums[(size_t)row * nbins + b] = c ? S : 0.f;
                     if (p.counts) p.counts[(size_t)row * nbins + b] = (int32_t)c;
                 }
+            }
+        } else if (MODE == kModeSearch) {
+            const int b = iter & 1;
+            const int need = (iter >> 1) * ppc;  // rows of slot b that must be scored first
+            bool ok = true;
+            if (iter >= 2) {
+                // slot b still holds task iter - 2: score leftover rows of the published tasks
+                // (tickets below iter * ppc) until all of iter - 2's rows are done
+                for (;;) {
+                    int t = -1;
+                    if (lane == 0) t = *reinterpret_cast<volatile int *>(&sh.done[b]) >= need
+                                           ? -2 : take_ticket(&sh.ticket, iter * ppc);
+                    t = __shfl_sync(0xffffffffu, t, 0);
+                    if (t == -2) break;
+                    if (t >= 0) {
+                        score_ticket(p, sh, t, ppc, Bw, lane, cur_s, cur_key);
+                    } else {
+                        if (lane == 0) ok = wait_flag(&sh.done[b], need, &s_abort, p.status);
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        break;
+                    }
+                }
+            }
+            if (ok) {
+                const size_t base = ((size_t)blockIdx.x * 2 + b) * ppc + warp * 32 + lane;
+                p.slot_k[base] = kvalid ? k : -1;
+                for (int bb = 0; bb < nbins; ++bb) {
+                    float S;
+                    uint32_t c;
+                    st.load((uint32_t)bb, S, c);
+                    if (over) c = wcn_cta[(size_t)bb * ppc];
+                    if (!kvalid) c = 0u;
+                    p.sums[base * nbins + bb] = c ? S : 0.f;
+                    p.counts[base * nbins + bb] = (int32_t)c;
+                }
+            }
+            // every row of the task is written; all fold warps leave together on a failure
+            if (named_bar_or(1, 32 * p.warps, !ok)) {
+                if (threadIdx.x == 0) *reinterpret_cast<volatile int *>(&s_abort) = 1;
+                return;
+            }
+            if (threadIdx.x == 0) {
+                __threadfence_block();
+                *reinterpret_cast<volatile int *>(&sh.pub[b]) = iter;
             }
         } else if (MODE == kModeBox) {
             float sc = -INFINITY;
@@ -1161,6 +1478,18 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 if (lane == 0 && key) atomicMax(&p.best_key[s], key);
             }
         }
+    }
+    if (MODE == kModeSearch) {
+        // all tasks published: score whatever rows are left, then leave
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = take_ticket(&sh.ticket, my_tasks * ppc);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t < 0) break;
+            __threadfence_block();
+            score_ticket(p, sh, t, ppc, Bw, lane, cur_s, cur_key);
+        }
+        if (lane == 0 && p.best_key && cur_key) atomicMax(&p.best_key[cur_s], cur_key);
     }
     if (MODE == kModeFold && p.slot_k) {
         // slots of tasks in this launch's range that lie past the device task count
@@ -1192,6 +1521,10 @@ cudaError_t box_coop_register();
 int fold_register_kernels()
 {
     cudaError_t e = box_coop_register();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, true, kLayoutPacked64, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, false, kLayoutPacked64, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, true, kLayoutPaired16, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, false, kLayoutPaired16, 4>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, true>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, false>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, true>();
@@ -1227,6 +1560,15 @@ static int occupancy_of(int threads, size_t smem)
     return n;
 }
 
+int search_blocks_per_sm(int nbins, int warps, int layout, int tile)
+{
+    const size_t smem = search_smem_bytes(nbins, warps, layout, tile);
+    if (smem == 0) return 0;
+    const int threads = 32 * (warps + 1);
+    return layout == kLayoutPacked64 ? occupancy_of<kModeSearch, true, kLayoutPacked64, 4>(threads, smem)
+                                     : occupancy_of<kModeSearch, true, kLayoutPaired16, 4>(threads, smem);
+}
+
 int fold_blocks_per_sm(int nbins, int warps, int layout, int tile)
 {
     const size_t smem = fold_smem_bytes(nbins, warps, layout, tile);
@@ -1253,9 +1595,36 @@ static void launch_variant(const FoldParams &p, int grid, int threads, size_t sm
     }
 }
 
-cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st)
+size_t search_smem_bytes(int nbins, int warps, int layout, int tile)
 {
+    if (warps + 1 > 4) return 0;
+    const size_t off = (fold_smem_bytes(nbins, warps, layout, tile) + 15) & ~(size_t)15;
+    const size_t bytes = off + (size_t)(warps + 1) * coop_pairs(nbins) * sizeof(float2);
+    return bytes <= kSmemLimit - 1024 ? bytes : 0;
+}
+
+// One fold block of `warps` warps plus the scorer warp (the 128-thread instantiation).
+template <bool POW2>
+static void launch_search_variant(const FoldParams &p, int grid, size_t smem, cudaStream_t st)
+{
+    const int threads = 32 * (p.warps + 1);
+    if (p.layout == kLayoutPacked64) fold_kernel<kModeSearch, POW2, kLayoutPacked64, 4><<<grid, threads, smem, st>>>(p);
+    else fold_kernel<kModeSearch, POW2, kLayoutPaired16, 4><<<grid, threads, smem, st>>>(p);
+}
+
+cudaError_t launch_fold(const FoldParams &p_in, int mode, int grid, cudaStream_t st)
+{
+    const FoldParams &p = p_in;
     if (p.tile != 512 && p.tile != 1024 && p.tile != 2048) return cudaErrorInvalidValue;
+    if (mode == kModeSearch) {
+        const size_t smem = search_smem_bytes(p.nbins, p.warps, p.layout, p.tile);
+        if (smem == 0 || !p.sums || !p.counts || !p.slot_k || !p.score) return cudaErrorInvalidValue;
+        FoldParams q = p;
+        q.stage_off = (fold_smem_bytes(p.nbins, p.warps, p.layout, p.tile) + 15) & ~(size_t)15;
+        if (q.shift >= 0) launch_search_variant<true>(q, grid, smem, st);
+        else launch_search_variant<false>(q, grid, smem, st);
+        return cudaGetLastError();
+    }
     const size_t smem = fold_smem_bytes(p.nbins, p.warps, p.layout, p.tile);
     if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
     const int threads = 32 * p.warps;
@@ -1272,144 +1641,17 @@ cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ box-SNR, warp per profile
-
-// A warp scores one profile at a time from the fold's centred bin sums and counts: the
-// profile is staged as PairBins, lane L walks the blocks of 8 starts L, L + 32, ... and
-// the lanes' winners merge by the walk's own rule (larger v, then smaller w, then smaller
-// s). The winner is re-evaluated with double-float sums spread over the warp. Unlike the
-// fold's own epilogue, the search here runs at full occupancy.
-constexpr int kCoopR = 8;
-
-__device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float hi2, float lo2)
-{
-    two_sum_acc(hi, lo, hi2);
-    lo += lo2;
-}
-
-__device__ __forceinline__ int star_of(const int64_t *grid_off, int nstars, int64_t k)
-{
-    int lo = 0, hi = nstars - 1;
-    while (lo < hi) {  // the last star whose range starts at or before k
-        const int mid = (lo + hi + 1) >> 1;
-        if (grid_off[mid] <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kCoopWarps * 32, 2) box_coop_kernel(const BoxCoopParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    const int nbins = p.nbins;
-    float2 *Bw = reinterpret_cast<float2 *>(smem) + (size_t)warp * coop_pairs(nbins);
-    const PairBins B{Bw};
+    float2 *Bw = reinterpret_cast<float2 *>(smem) + (size_t)warp * coop_pairs(p.nbins);
     int cur_s = -1;
     unsigned long long cur_key = 0ull;
     for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < p.rows; r += (int64_t)gridDim.x * nw) {
         const int64_t k = p.slot_k ? p.slot_k[r] : p.k_begin + r;
-        if (k < 0) continue;
-        const int s = p.grid_off ? star_of(p.grid_off, p.nstars, k) : 0;
-        const int64_t gb = p.grid_off ? p.grid_off[s] : 0;
-        const float *srow = p.sums ? p.sums + (size_t)r * nbins : nullptr;
-        const float *mrow = p.means ? p.means + (size_t)r * nbins : nullptr;
-        const int32_t *crow = p.counts + (size_t)r * nbins;
-        float mref = 0.f;
-        if (mrow) {  // means in: centre them on the profile's count-weighted mean (FP64)
-            double num = 0.0, den = 0.0;
-            for (int b = lane; b < nbins; b += 32) {
-                const int32_t c = crow[b];
-                if (c > 0) {
-                    num += (double)mrow[b] * (double)c;
-                    den += (double)c;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                num += __shfl_xor_sync(0xffffffffu, num, o);
-                den += __shfl_xor_sync(0xffffffffu, den, o);
-            }
-            mref = den > 0.0 ? (float)(num / den) : 0.f;
-        }
-        __syncwarp();  // the previous profile's readers are done
-        float Stot = 0.f, Ntot = 0.f;
-        int nnz = 0;
-        for (int b = lane; b < nbins; b += 32) {
-            const float c = (float)max(crow[b], 0);
-            const float sv = mrow ? (c > 0.f ? (mrow[b] - mref) * c : 0.f) : srow[b];
-            Bw[b + (b >> 3)] = make_float2(sv, c);
-            Stot += sv;
-            Ntot += c;
-            nnz += c > 0.f;
-        }
-        for (int o = 16; o > 0; o >>= 1) {  // a butterfly leaves the same totals in every lane
-            Stot += __shfl_xor_sync(0xffffffffu, Stot, o);
-            Ntot += __shfl_xor_sync(0xffffffffu, Ntot, o);
-            nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
-        }
-        __syncwarp();
-        float bv = -INFINITY;
-        int bkey = 0x7fffffff;
-        if (p.w_max < nnz)
-            box_walk<kCoopR, false, PairBins, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR,
-                                                   bv, bkey);
-        else
-            box_walk<kCoopR, true>(B, nbins, p.w_min, p.w_max, Stot, Ntot, lane * kCoopR, 32 * kCoopR, bv, bkey);
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int okey = __shfl_xor_sync(0xffffffffu, bkey, o);
-            const bool take = (ov > bv) | ((ov == bv) & (okey < bkey));
-            bv = take ? ov : bv;
-            bkey = take ? okey : bkey;
-        }
-        float sc = -INFINITY;
-        int bs = -1, bw = -1;
-        if (bkey != 0x7fffffff) {
-            bw = bkey >> 12;
-            bs = bkey & 4095;
-            float sth = 0.f, stl = 0.f, sih = 0.f, sil = 0.f;
-            uint32_t nt = 0u, ni = 0u;
-            for (int b = lane; b < nbins; b += 32) {
-                const float2 v = B.sc(b);
-                const uint32_t c = (uint32_t)v.y;
-                two_sum_acc(sth, stl, v.x);
-                nt += c;
-                int d = b - bs;
-                d += d < 0 ? nbins : 0;
-                if (d < bw) {
-                    two_sum_acc(sih, sil, v.x);
-                    ni += c;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                two_sum_merge(sth, stl, __shfl_xor_sync(0xffffffffu, sth, o), __shfl_xor_sync(0xffffffffu, stl, o));
-                two_sum_merge(sih, sil, __shfl_xor_sync(0xffffffffu, sih, o), __shfl_xor_sync(0xffffffffu, sil, o));
-                nt += __shfl_xor_sync(0xffffffffu, nt, o);
-                ni += __shfl_xor_sync(0xffffffffu, ni, o);
-            }
-            float sig = p.sigma_user;
-            if (!(sig > 0.f) && p.stats) sig = p.stats[s].sigma;
-            if (!(sig > 0.f)) sig = 1.f;
-            const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
-            const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
-            sc = (float)((St * Ni - Si * Nt) / ((double)sig * sqrt(Nt * Ni * No)));
-        }
-        if (lane == 0) {
-            p.score[k] = sc;
-            if (p.best_s) p.best_s[k] = bs;
-            if (p.best_w) p.best_w[k] = bw;
-            if (p.best_key) {
-                const unsigned long long key = argmax_key(sc, k - gb);
-                if (s != cur_s) {
-                    if (cur_key) atomicMax(&p.best_key[cur_s], cur_key);
-                    cur_s = s;
-                    cur_key = key;
-                } else {
-                    cur_key = key > cur_key ? key : cur_key;
-                }
-            }
-        }
+        if (k >= 0) score_row(p, r, k, Bw, lane, cur_s, cur_key);
     }
     if (lane == 0 && p.best_key && cur_key) atomicMax(&p.best_key[cur_s], cur_key);
 }

@@ -39,7 +39,10 @@ struct SampleScratch {
     uint8_t *flags;     // one byte per 16 samples: regular-cadence group (see prep)
 };
 
-enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeCnnPrep = 2 };
+// kModeSearch: fold warps write each task's centred sums and counts to a per-block
+// two-slot ring (sums, counts, slot_k) and one extra warp scores them (box-SNR), with the
+// fold warps taking leftover profiles when they would otherwise wait for a slot.
+enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeCnnPrep = 2, kModeSearch = 3 };
 
 // Shared-memory layout of the lane-private bins (see fold.cu).
 enum FoldLayout : int { kLayoutPaired16 = 1, kLayoutPacked64 = 2 };
@@ -65,7 +68,8 @@ struct FoldParams {
     int tile;                  // samples per bulk-copy tile: 512, 1024 or 2048
     float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
-    // kModeFold outputs ([global period][nbins], or [slot][nbins] when slot_k is set)
+    // kModeFold outputs ([global period][nbins], or [slot][nbins] when slot_k is set);
+    // kModeSearch uses sums, counts and slot_k as its ring, [grid][2][32 * warps] rows
     float *folded;
     float *sums;               // centred bin sums (0 for empty bins), for the separate box scorer
     int32_t *counts;
@@ -78,6 +82,7 @@ struct FoldParams {
     unsigned long long *best_key;  // [S] argmax keys (may be NULL)
     int w_min, w_max;
     float sigma_user;          // > 0: use it; else the star's flux std (1 if that is 0)
+    size_t stage_off;          // kModeSearch: byte offset of the scorer staging in shared memory
     // kModeCnnPrep output: normalised profiles, bf16 [global period][256]
     uint16_t *cnn_in;
     uint32_t *status;
@@ -120,6 +125,9 @@ cudaError_t launch_prep(const double *times, const float *flux, const int64_t *l
                         int nstars, int64_t max_len, const double *t0s, double t0, SampleScratch smp,
                         double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st);
 cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st);
+// Shared memory of a kModeSearch block (0 if it does not fit or warps + 1 > 4).
+size_t search_smem_bytes(int nbins, int warps, int layout, int tile);
+int search_blocks_per_sm(int nbins, int warps, int layout, int tile);
 cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *key, cudaStream_t st);
 cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, int nstars, int64_t n_total,
                               int64_t np_total, int ppc, int64_t *lc_s, int64_t *grid_s, int64_t *task_off,

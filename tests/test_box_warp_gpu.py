@@ -1,8 +1,9 @@
-"""GPU parity of the two places the box-SNR search can run: the fold kernel's epilogue
-and the separate warp-per-profile kernel fed by the fold's centred bin sums. Both are
-checked against the FP64 oracle (box-SNR within 1e-5 relative, the score's own scale as
-floor when |score| < 1); batched searches must equal per-star ones bit for bit on either
-path.
+"""GPU parity of the places the box-SNR search can run: the fold kernel's epilogue, the
+separate warp-per-profile kernel fed by the fold's centred bin sums, and the one-kernel
+search whose extra warp per fold block scores the block's previous task. All are checked
+against the FP64 oracle (box-SNR within 1e-5 relative, the score's own scale as floor when
+|score| < 1); the warp and one-kernel paths must agree bit for bit, and batched searches
+must equal per-star ones bit for bit.
 """
 import numpy as np
 import pytest
@@ -54,18 +55,23 @@ def test_both_box_paths_match_the_oracle(ctx, nbins, w_min, w_max):
     periods = lcsynth.freq_grid(517)
     _, cnt_o, sum_o = oracle.fold(lc.times, lc.flux, periods, nbins, lc.t0)
     sc_o, _, _ = oracle.box_snr(sum_o, cnt_o, w_min, w_max, 2e-4)
-    for path in (g.BOX_EPILOGUE, g.BOX_WARP):
+    got = {}
+    for path in (g.BOX_EPILOGUE, g.BOX_WARP, g.BOX_FUSED):
         sc, k, v = search(ctx, path, lc.times, lc.flux, periods, nbins, lc.t0, w_min, w_max, 2e-4)
         check_box(sc, sc_o)
         assert k == oracle.argmax(sc) and v == sc[k]
+        got[path] = sc
+    np.testing.assert_array_equal(got[g.BOX_WARP], got[g.BOX_FUSED])
 
 
-def test_box_warp_path_over_several_chunks(ctx):
-    """More periods than one fold wave holds, so the scorer runs on several chunks."""
+@pytest.mark.parametrize("path_name", ["BOX_WARP", "BOX_FUSED"])
+def test_box_warp_path_over_several_chunks(ctx, path_name):
+    """More periods than one fold wave holds: the scorer runs on several chunks, and in the
+    one-kernel search every block goes round its two-slot ring more than once."""
     import paper_2312_02063_gb300 as g
     lc = lcsynth.light_curve_tiny(3)
     periods = lcsynth.freq_grid(40000)
-    sc, k, v = search(ctx, g.BOX_WARP, lc.times, lc.flux, periods, 256, lc.t0, 1, 108, 0.0)
+    sc, k, v = search(ctx, getattr(g, path_name), lc.times, lc.flux, periods, 256, lc.t0, 1, 108, 0.0)
     idx = np.unique(np.concatenate([np.random.default_rng(5).choice(len(periods), 40, replace=False),
                                     [0, len(periods) - 1, k]]))
     sigma = float(np.std(lc.flux.astype(np.float64)))
@@ -83,6 +89,20 @@ def test_box_warp_degenerate_star(ctx):
     sc, k, v = search(ctx, g.BOX_WARP, *args)
     assert np.all(sc == -np.inf) and k == oracle.argmax(sc) and v == -np.inf
     assert search(ctx, g.BOX_EPILOGUE, *args)[1] == k
+    sc2, k2, _ = search(ctx, g.BOX_FUSED, *args)
+    assert np.all(sc2 == -np.inf) and k2 == k
+
+
+def test_fused_search_equals_the_two_kernel_path_at_full_size(ctx):
+    """The 250,000-period Kepler-like search: the one-kernel path gives the two-kernel
+    path's scores bit for bit (same fold sums, same scorer), and its best period."""
+    import paper_2312_02063_gb300 as g
+    lc = lcsynth.light_curve_kepler()
+    periods = lcsynth.freq_grid(250000)
+    a, ka, va = search(ctx, g.BOX_WARP, lc.times, lc.flux, periods, 256, lc.t0, 1, 108, 0.0)
+    b, kb, vb = search(ctx, g.BOX_FUSED, lc.times, lc.flux, periods, 256, lc.t0, 1, 108, 0.0)
+    np.testing.assert_array_equal(a, b)
+    assert ka == kb and va == vb
 
 
 @pytest.mark.parametrize("nbins", [128, 256])
