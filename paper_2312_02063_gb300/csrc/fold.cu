@@ -988,7 +988,7 @@ __device__ __forceinline__ int star_of(const int64_t *grid_off, int nstars, int6
 // by the walk's own rule (larger v, then smaller w, then smaller s), and the winner is
 // re-evaluated with double-float sums spread over the warp. Lane 0 writes the outputs and
 // folds the period's argmax key into (cur_s, cur_key).
-__device__ __noinline__ void score_row(const BoxCoopParams &p, int64_t r, int64_t k, float2 *Bw, int lane,
+__device__ __forceinline__ void score_row(const BoxCoopParams &p, int64_t r, int64_t k, float2 *Bw, int lane,
                                        int &cur_s, unsigned long long &cur_key)
 {
     const int nbins = p.nbins;
