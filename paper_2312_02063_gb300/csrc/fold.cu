@@ -1086,12 +1086,14 @@ __device__ __forceinline__ void score_row(const BoxCoopParams &p, int64_t r, int
             nt += __shfl_xor_sync(0xffffffffu, nt, o);
             ni += __shfl_xor_sync(0xffffffffu, ni, o);
         }
-        float sig = p.sigma_user;
-        if (!(sig > 0.f) && p.stats) sig = p.stats[s].sigma;
-        if (!(sig > 0.f)) sig = 1.f;
-        const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
-        const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
-        sc = (float)((St * Ni - Si * Nt) / ((double)sig * sqrt(Nt * Ni * No)));
+        if (lane == 0) {  // the FP64 tail once per profile (only lane 0 writes the outputs)
+            float sig = p.sigma_user;
+            if (!(sig > 0.f) && p.stats) sig = p.stats[s].sigma;
+            if (!(sig > 0.f)) sig = 1.f;
+            const double St = (double)sth + (double)stl, Si = (double)sih + (double)sil;
+            const double Nt = (double)nt, Ni = (double)ni, No = (double)(nt - ni);
+            sc = (float)((St * Ni - Si * Nt) / ((double)sig * sqrt(Nt * Ni * No)));
+        }
     }
     if (lane == 0) {
         p.score[k] = sc;
