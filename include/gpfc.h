@@ -386,11 +386,11 @@ typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;
  * occupancy. GPFC_BOX_FUSED: one kernel; each fold block has one more warp that scores
  * the block's previous task, one profile at a time, from a two-slot ring of sums and
  * counts in L2, and the fold warps take leftover profiles when they would otherwise wait
- * for a slot (single-star gpfc_search only; when the extra warp's shared memory does not
- * fit, GPFC_BOX_WARP is used). GPFC_BOX_AUTO (the default) takes GPFC_BOX_FUSED for a
- * single star and GPFC_BOX_WARP for a batch from nbins >= 256, else the epilogue. The box
- * scores of the warp and fused paths are bit-identical; a batched search and the per-star
- * search agree bit for bit whatever the path. */
+ * for a slot (when the extra warp's shared memory does not fit, GPFC_BOX_WARP is used; a
+ * batched search whose tuned fold block leaves no room takes the default fold block).
+ * GPFC_BOX_AUTO (the default) takes GPFC_BOX_FUSED from nbins >= 256, else the epilogue.
+ * The box scores of the warp and fused paths are bit-identical; a batched search and the
+ * per-star search agree bit for bit whatever the path. */
 typedef enum { GPFC_BOX_AUTO = 0, GPFC_BOX_EPILOGUE = 1, GPFC_BOX_WARP = 2, GPFC_BOX_FUSED = 3 } gpfc_box_path;
 int gpfc_set_box_path(gpfc_ctx *ctx, int path);
 

@@ -27,7 +27,7 @@ __all__ = [
 
 SCORER_BOX = 0
 SCORER_CNN = 1
-BOX_AUTO = 0       # from 256 bins the one-kernel search (a batch: the separate kernel), else the epilogue
+BOX_AUTO = 0       # from 256 bins the one-kernel search, else the fold's epilogue
 BOX_EPILOGUE = 1   # box search inside the fold kernel
 BOX_WARP = 2       # separate box kernel, one warp per profile
 BOX_FUSED = 3      # one kernel: an extra warp per fold block scores the block's previous task

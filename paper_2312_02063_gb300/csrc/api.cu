@@ -920,7 +920,7 @@ struct BatchArgs {
     int32_t S;
     int32_t nbins;
     int32_t scorer;
-    int32_t box_warp;  // box search in the warp-per-profile kernel
+    int32_t box_warp;  // box search: 0 in the fold's epilogue, 1 separate kernel, 2 one kernel
     const int64_t *lc_off;
     const double *times;
     const float *flux;
@@ -948,6 +948,10 @@ struct BatchBuffers {
     float *box_sum[2];
     int32_t *box_cnt[2];
     int64_t *box_slot[2];
+    // one-kernel box search: the blocks' two-slot rings
+    float *ring_s;
+    int32_t *ring_c;
+    int64_t *ring_k;
 };
 
 // Workspace of a batched search: validated offsets and task starts, the fold buffers of
@@ -962,7 +966,12 @@ size_t carve_batched(void *base, const BatchArgs &A, const FoldPlan &pl, int64_t
     FoldBuffers tmp{};
     uint8_t *fold_base = c.take<uint8_t>(carve_fold(nullptr, pl, A.n_total, A.S, A.nbins, tmp));
     carve_fold(fold_base, pl, A.n_total, A.S, A.nbins, B.fb);
-    if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
+    if (A.scorer == GPFC_SCORER_BOX && A.box_warp == 2) {
+        const size_t rows = (size_t)pl.grid * 2 * pl.ppc;
+        B.ring_s = c.take<float>(rows * A.nbins);
+        B.ring_c = c.take<int32_t>(rows * A.nbins);
+        B.ring_k = c.take<int64_t>(rows);
+    } else if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
         for (int b = 0; b < 2; ++b) {
             B.box_sum[b] = c.take<float>((size_t)slots * A.nbins);
             B.box_cnt[b] = c.take<int32_t>((size_t)slots * A.nbins);
@@ -1017,6 +1026,24 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
     p.ws_cnt = B.fb.ws_cnt;
     p.status = ctx->status_dev;
     const bool want_best = A.best_index || A.best_score;
+    if (A.scorer == GPFC_SCORER_BOX && A.box_warp == 2) {
+        // one kernel over every task: fold warps and a scorer warp per block
+        if (want_best) e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long) * A.S, st);
+        if (e != cudaSuccess) return e;
+        p.sums = B.ring_s;
+        p.counts = B.ring_c;
+        p.slot_k = B.ring_k;
+        p.score = A.score;
+        p.w_min = A.box.w_min;
+        p.w_max = A.box.w_max;
+        p.sigma_user = A.box.sigma > 0.0 ? (float)A.box.sigma : 0.f;
+        p.best_key = want_best ? B.fb.key : nullptr;
+        p.task_begin = 0;
+        p.ntasks = T;
+        e = launch_fold(p, kModeSearch, (int)std::min<int64_t>(T, pl.grid), st);
+        if (e == cudaSuccess && want_best) e = launch_argmax_finalize(B.fb.key, A.S, A.best_index, A.best_score, st);
+        return e;
+    }
     if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
         // chunks of one task per resident block, each chunk's sums and counts by slot
         if (want_best) e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long) * A.S, st);
@@ -1876,7 +1903,23 @@ int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offset
             tuned = find_tuned(ctx, nbins, mode, n_avg);
         }
     }
-    const FoldPlan pl = plan_fold(ctx, n_avg, n_periods_total, nbins, tuned);
+    FoldPlan pl = plan_fold(ctx, n_avg, n_periods_total, nbins, tuned);
+    if (A.box_warp && ctx->box_path != GPFC_BOX_WARP) {
+        // the one-kernel search, with the tuned fold config if its block fits, else the
+        // default one
+        FoldPlan ps = pl;
+        int bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile);
+        if (bps < 1) {
+            ps = plan_fold(ctx, n_avg, n_periods_total, nbins, nullptr);
+            bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile);
+        }
+        if (bps >= 1) {
+            ps.bps = bps;
+            ps.grid = ctx->num_sms * bps;
+            pl = ps;
+            A.box_warp = 2;
+        }
+    }
     BatchBuffers B{};
     const int64_t slots = (int64_t)pl.grid * pl.ppc;
     rc = ensure_ws(ctx, carve_batched(nullptr, A, pl, slots, B));
