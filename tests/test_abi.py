@@ -86,9 +86,11 @@ def test_struct_layouts_match_the_header(tmp_path):
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "gpfc.h"\n'
         'int main(void) {\n'
-        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gpfc_fold_config), sizeof(gpfc_box_params),\n'
-        '         sizeof(gpfc_cnn_weights), offsetof(gpfc_fold_config, blocks_per_sm),\n'
-        '         sizeof(gpfc_star_summary), sizeof(gpfc_peak));\n'
+        '  printf("%zu %zu %zu %zu %zu %zu %d %d %d %d %d %d\\n", sizeof(gpfc_fold_config),\n'
+        '         sizeof(gpfc_box_params), sizeof(gpfc_cnn_weights),\n'
+        '         offsetof(gpfc_fold_config, blocks_per_sm), sizeof(gpfc_star_summary), sizeof(gpfc_peak),\n'
+        '         (int)GPFC_BOX_AUTO, (int)GPFC_BOX_EPILOGUE, (int)GPFC_BOX_WARP, (int)GPFC_BOX_FUSED,\n'
+        '         (int)GPFC_SCORER_BOX, (int)GPFC_SCORER_CNN);\n'
         '  return 0;\n}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -97,6 +99,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert int(out[1]) == ctypes.sizeof(g.BoxParams)
     assert int(out[2]) == ctypes.sizeof(g.CnnWeights)
     assert int(out[3]) == g.FoldConfig.blocks_per_sm.offset
+    assert [int(v) for v in out[6:12]] == [g.BOX_AUTO, g.BOX_EPILOGUE, g.BOX_WARP, g.BOX_FUSED, g.SCORER_BOX,
+                                           g.SCORER_CNN]
     assert int(out[4]) == g.STAR_SUMMARY_DTYPE.itemsize
     assert int(out[5]) == g.PEAK_DTYPE.itemsize
 
@@ -111,3 +115,8 @@ def test_batched_entry_rejects_null_context_without_gpu():
     assert lib.gpfc_check_wait_timeout(None, 10000) == -1
     assert lib.gpfc_peaks(None, None, None, 1, None, 1, 3.0, 4, 1e-3, 8, None, None) == -1
     assert lib.gpfc_fold_equal_count(None, None, None, 1, None, 1, 4096, 256, 0.0, None) == -1
+    assert lib.gpfc_set_box_path(None, g.BOX_FUSED) == -1
+    import ctypes
+    ms, nl = ctypes.c_float(), ctypes.c_int32()
+    assert lib.gpfc_fold_launch_times(None, ctypes.byref(ms), ctypes.byref(nl)) == -1
+
