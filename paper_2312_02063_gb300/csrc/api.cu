@@ -467,7 +467,8 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     return GPFC_OK;
 }
 
-// The box search runs in its own warp-per-profile kernel (else in the fold's epilogue).
+// The box search runs outside the fold's epilogue: in the one-kernel search, or in the
+// separate warp-per-profile kernel.
 bool warp_box(const gpfc_ctx *ctx, int nbins)
 {
     return ctx->box_path == GPFC_BOX_WARP || ctx->box_path == GPFC_BOX_FUSED ||

@@ -6,20 +6,26 @@
 //
 // Design. One lane owns one trial period for the whole light curve, so no two threads
 // ever update the same bin and no atomics are needed. Each warp keeps the bins of its
-// 32 periods in shared memory laid out [bin][lane]: lane l's bin b sits in bank l, so a
-// warp's 32 read-modify-writes never conflict whatever bins the lanes hit. Light-curve
-// tiles (tau split in two 32-bit words, flux - f_ref) are staged into shared memory by
-// the bulk-copy (TMA) engine, double-buffered behind an mbarrier, and every lane reads
-// the same sample (a broadcast). Each lane processes 4 consecutive samples at once; if
-// two of them fall in the same bin it takes a sequential path.
+// 32 periods in shared memory laid out [bin][lane], so a warp's 32 read-modify-writes never
+// conflict whatever bins the lanes hit: either 8-byte words (FP32 partial sum, 32-bit
+// count; the default from 256 bins) or FP32 sums with paired 16-bit counts (6 bytes a
+// bin, four warps' worth at 256 bins). Light-curve tiles (tau split in two 32-bit words,
+// flux - f_ref, one regular-cadence flag byte per 16 samples) are staged into shared
+// memory by the bulk-copy (TMA) engine, double-buffered behind an mbarrier, and every lane
+// reads the same sample (a broadcast). Groups of 16 (or 8) regular samples that can never
+// put two samples into one bin at the warp's periods go through a software-pipelined loop
+// without collision checks; other groups take a checked path.
 //
-// Shared memory holds per (bin, lane) an FP32 partial sum and a 16-bit count over a
-// chunk of samples (<= 65535 samples, so the count cannot overflow). At the end of each
-// chunk the partials are added into a per-block workspace with Kahan compensation
-// (sum, compensation) and exact 32-bit counts; the workspace stays resident in L2.
+// The partial sums cover a chunk of 64 * nbins samples; at the end of each chunk they
+// are added into a per-block workspace with Kahan compensation (sum, compensation) and
+// exact 32-bit counts, which stays resident in L2.
 //
-// Epilogues, same kernel: write means + counts (gpfc_fold), or run the box-SNR search
-// over the finished profile of each lane's period (gpfc_search, box scorer).
+// Epilogues (kernel modes): write means and counts (gpfc_fold) or centred sums and counts
+// (the separate box scorer); run the box-SNR search over each lane's finished profile
+// (kModeBox, below 256 bins); or kModeSearch, where each block has one more warp that
+// scores the block's previous task from a two-slot ring in L2 (the one-kernel search).
+// box_coop_kernel scores profiles one warp per profile (the separate scorer, and
+// gpfc_score_box).
 #include <algorithm>
 #include <climits>
 #include <cmath>
