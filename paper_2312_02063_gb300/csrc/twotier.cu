@@ -42,6 +42,11 @@ __device__ __forceinline__ int64_t eq_sum(unsigned long long P)
     return (int64_t)(P - ((unsigned long long)eq_count(P) << kCountShift));
 }
 
+// Word of fine bin f in a period's row: the low 4 bits of f XORed with bits 4-7 (rows of
+// a multiple of 16 bins), so lanes whose bins are a regular stride apart spread over the
+// banks instead of piling onto a few.
+__device__ __forceinline__ int eq_word(int f, bool swz) { return swz ? f ^ ((f >> 4) & 15) : f; }
+
 // max |x| over the star (as float bits: order-preserving for values >= 0)
 __global__ void eq_absmax_kernel(const float *__restrict__ x, int64_t n, unsigned int *maxbits)
 {
@@ -108,6 +113,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
     const double f_ref = p.stats->f_ref;
     const int64_t n = p.n;
     const int per_thread = (nfine + kEqThreads - 1) / kEqThreads;
+    const bool swz = (nfine & 15) == 0;
     const int64_t ngroups = (p.np + ppb - 1) / ppb;
 
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
                         f = (uint32_t)(((unsigned long long)hi * (uint32_t)nfine +
                                         (unsigned long long)__umulhi(lo, (uint32_t)nfine)) >> 32);
                     }
-                    atomicAdd(&bins[pp * nfine + f], v);
+                    atomicAdd(&bins[pp * nfine + eq_word((int)f, swz)], v);
                 }
             }
         }
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
             // the fine bins are the result: counts, exact sums rounded once, means
             for (int idx = threadIdx.x; idx < nper * nfine; idx += kEqThreads) {
                 const int pp = idx / nfine, f = idx - pp * nfine;
-                const unsigned long long w = bins[idx];
+                const unsigned long long w = bins[pp * nfine + eq_word(f, swz)];
                 const int64_t c = eq_count(w);
                 const double S = (double)eq_sum(w) * quantum;
                 const size_t o = (size_t)(k0 + pp) * nfine + f;
@@ -172,12 +178,12 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
             unsigned long long *B = bins + (size_t)pp * nfine;
             const int f0 = threadIdx.x * per_thread;
             unsigned long long loc = 0ull;
-            for (int f = f0; f < min(nfine, f0 + per_thread); ++f) loc += B[f];
+            for (int f = f0; f < min(nfine, f0 + per_thread); ++f) loc += B[eq_word(f, swz)];
             const unsigned long long incl = eq_block_scan(loc, warp_tot);
             unsigned long long run = incl - loc;
             for (int f = f0; f < min(nfine, f0 + per_thread); ++f) {
-                run += B[f];
-                B[f] = run;
+                run += B[eq_word(f, swz)];
+                B[eq_word(f, swz)] = run;
             }
             __syncthreads();
         }
@@ -197,12 +203,12 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
                 int lo = 0, hi = nfine - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (eq_count(B[mid]) * nbins >= u) hi = mid;
+                    if (eq_count(B[eq_word(mid, swz)]) * nbins >= u) hi = mid;
                     else lo = mid + 1;
                 }
-                const unsigned long long Pp = lo > 0 ? B[lo - 1] : 0ull;
+                const unsigned long long Pp = lo > 0 ? B[eq_word(lo - 1, swz)] : 0ull;
                 const int64_t Cp = eq_count(Pp), Sp = eq_sum(Pp);
-                const int64_t cf = eq_count(B[lo]) - Cp, sf = eq_sum(B[lo]) - Sp;
+                const int64_t cf = eq_count(B[eq_word(lo, swz)]) - Cp, sf = eq_sum(B[eq_word(lo, swz)]) - Sp;
                 whole[side] = Sp;
                 part[side] = (double)sf * ((double)(u - Cp * nbins) / ((double)cf * nbins));
             }
