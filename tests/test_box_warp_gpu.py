@@ -48,7 +48,7 @@ def search(ctx, path, times, flux, periods, nbins, t0, w_min, w_max, sigma):
 
 
 @pytest.mark.parametrize("nbins,w_min,w_max", [(256, 1, 108), (256, 5, 256), (100, 3, 17), (512, 2, 200),
-                                               (1024, 1, 40), (37, 2, 37), (2, 1, 2), (9, 1, 1)])
+                                               (300, 2, 120), (1024, 1, 40), (37, 2, 37), (2, 1, 2), (9, 1, 1)])
 def test_both_box_paths_match_the_oracle(ctx, nbins, w_min, w_max):
     import paper_2312_02063_gb300 as g
     lc = lcsynth.light_curve_tiny(nbins)
@@ -132,3 +132,22 @@ def test_batched_equals_per_star_on_both_paths(ctx, nbins):
             one, k, v = search(ctx, path, times[a:b], flux[a:b], periods[c:d], nbins, float(t0s[s]), 2, 40, 0.0)
             np.testing.assert_array_equal(sc[c:d], one)
             assert bi[s] == k and bs[s] == v
+
+
+def test_one_kernel_search_with_the_paired16_layout(ctx):
+    """The one-kernel search with 6-byte bins (FP32 sums, paired 16-bit counts) and three
+    fold warps, against the default 8-byte layout: the same fold sums, so the same scores."""
+    import paper_2312_02063_gb300 as g
+    lc = lcsynth.light_curve_tiny(17)
+    periods = lcsynth.freq_grid(3000)
+    a, ka, _ = search(ctx, g.BOX_FUSED, lc.times, lc.flux, periods, 256, lc.t0, 1, 40, 2e-4)
+    try:
+        ctx.set_fold_config(warps=3, layout=g.LAYOUT_PAIRED16)
+        b, kb, _ = search(ctx, g.BOX_FUSED, lc.times, lc.flux, periods, 256, lc.t0, 1, 40, 2e-4)
+        assert ctx.last_fold_plan()["layout"] == g.LAYOUT_PAIRED16
+    finally:
+        ctx.reset_fold_config()
+    _, cnt_o, sum_o = oracle.fold(lc.times, lc.flux, periods, 256, lc.t0)
+    sc_o, _, _ = oracle.box_snr(sum_o, cnt_o, 1, 40, 2e-4)
+    check_box(b, sc_o)
+    assert kb == oracle.argmax(b)
