@@ -38,7 +38,7 @@ SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, pe
 # DRAM bytes (read + write) per period of the one-kernel search (fold + box-SNR) of the same
 # light curve, from an ncu capture of a 58,368-period search; the search's traffic grows
 # with the number of periods (ring writes, one light-curve pass per task).
-SEARCH_DRAM_BYTES_PER_PERIOD = (33.926144e6 + 202.215168e6) / 58368  # profiles/fold_kernel_search_kepler62835.md
+SEARCH_DRAM_BYTES_PER_PERIOD = (34.224128e6 + 196.570112e6) / 58368  # profiles/fold_kernel_search_kepler62835.md
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -192,9 +192,11 @@ FoldPlan plan_with(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const 
     int64_t per_sm = (np + (int64_t)32 * ctx->num_sms - 1) / ((int64_t)32 * ctx->num_sms);
     int w = (int)std::min<int64_t>(maxw, std::max<int64_t>(1, per_sm));
     if (cfg.warps > 0) w = std::min(cfg.warps, maxw);
-    // ~64 samples per bin per chunk keeps the plain FP32 partials short; the chunk
-    // partials are then added with Kahan compensation
-    int64_t chunk = cfg.chunk > 0 ? cfg.chunk : (int64_t)64 * nbins;
+    // ~128 samples per bin per chunk keeps the plain FP32 partials short; the chunk
+    // partials are then added with Kahan compensation. Each flush costs a few L2 round
+    // trips that one warp per scheduler cannot hide, so chunks are as long as precision
+    // allows (the C2 search: 18.3 / 17.3 / 16.7 ms at 32 / 64 / 128 samples per bin).
+    int64_t chunk = cfg.chunk > 0 ? cfg.chunk : (int64_t)128 * nbins;
     pl.chunk = (int)std::min<int64_t>(65520, std::max<int64_t>(256, chunk)) & ~15;
     pl.warps = w;
     pl.ppc = 32 * w;

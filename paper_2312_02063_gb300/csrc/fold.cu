@@ -16,7 +16,7 @@
 // put two samples into one bin at the warp's periods go through a software-pipelined loop
 // without collision checks; other groups take a checked path.
 //
-// The partial sums cover a chunk of 64 * nbins samples; at the end of each chunk they
+// The partial sums cover a chunk of 128 * nbins samples; at the end of each chunk they
 // are added into a per-block workspace with Kahan compensation (sum, compensation) and
 // exact 32-bit counts, which stays resident in L2.
 //
