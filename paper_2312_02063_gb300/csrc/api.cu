@@ -537,7 +537,8 @@ bool fused_plan(gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, FoldPlan &pl)
     if (bps < 1) return false;
     pl.bps = bps;
     pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms * bps);
-    return true;
+    // a block numbers the rows of its tasks in 32-bit tickets
+    return (pl.ntasks + pl.grid - 1) / pl.grid * pl.ppc < ((int64_t)1 << 31);
 }
 
 struct FusedBuffers {
@@ -1916,7 +1917,9 @@ int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offset
             ps = plan_fold(ctx, n_avg, n_periods_total, nbins, nullptr);
             bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile);
         }
-        if (bps >= 1) {
+        // a block numbers the rows of its tasks in 32-bit tickets
+        const int64_t rows_per_block = (task_bound(A, ps.ppc) + ctx->num_sms - 1) / ctx->num_sms * ps.ppc;
+        if (bps >= 1 && rows_per_block < ((int64_t)1 << 31)) {
             ps.bps = bps;
             ps.grid = ctx->num_sms * bps;
             pl = ps;
