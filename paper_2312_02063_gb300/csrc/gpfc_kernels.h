@@ -42,7 +42,7 @@ struct SampleScratch {
 // kModeSearch: fold warps write each task's centred sums and counts to a per-block
 // two-slot ring (sums, counts, slot_k) and one extra warp scores them (box-SNR), with the
 // fold warps taking leftover profiles when they would otherwise wait for a slot.
-enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeCnnPrep = 2, kModeSearch = 3 };
+enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeSearch = 3 };
 
 // Shared-memory layout of the lane-private bins (see fold.cu).
 enum FoldLayout : int { kLayoutPaired16 = 1, kLayoutPacked64 = 2 };
@@ -83,8 +83,6 @@ struct FoldParams {
     int w_min, w_max;
     float sigma_user;          // > 0: use it; else the star's flux std (1 if that is 0)
     size_t stage_off;          // kModeSearch: byte offset of the scorer staging in shared memory
-    // kModeCnnPrep output: normalised profiles, bf16 [global period][256]
-    uint16_t *cnn_in;
     uint32_t *status;
 };
 
