@@ -8,15 +8,19 @@
 // activations are BF16; every product is accumulated in FP32.
 //
 // Kernels:
-//  * cnn_conv_kernel: a block takes two profiles at a time. Noise normalisation (Sec. 2.1:
-//    std scaled to 1, mean kept) and conv1 run on CUDA cores. conv2 and conv3 are implicit
-//    GEMMs on tcgen05: activations sit in shared memory as [channel chunk of 8][position
-//    with a circular halo][8 channels] BF16, so the im2col matrix row of output position l
-//    for tap k is the 16-byte row at position l + k: the MMA's A descriptor walks those rows
-//    directly (core-matrix K step = one tap), no im2col copy. conv2: M = 128 positions of one
-//    profile, N = 32, K = 80; conv3: M = 64 positions x 2 profiles interleaved, N = 64, K = 160.
-//    Accumulators live in TMEM; the epilogue adds the bias, applies ReLU, pools neighbouring
-//    TMEM lanes with warp shuffles and writes the next layer's input.
+//  * cnn_conv_kernel: a block takes four profiles at a time. Noise normalisation (Sec. 2.1:
+//    std scaled to 1, mean kept) runs on CUDA cores. conv1, conv2 and conv3 are implicit
+//    GEMMs on tcgen05: conv1 from one 16-byte im2col row per pooled position (8 taps, K
+//    padded to 16), conv2 and conv3 straight from the activations, which sit in shared
+//    memory as even and odd position planes with a circular halo row, [channel chunk of
+//    8][row][profile][8 channels] BF16, so the A window of pooled output q for pool member
+//    j and tap u starts 16-byte rows apart whatever j and u are (core-matrix K step = one
+//    tap), no im2col copy. conv1: M = 128 pooled positions per profile, N = 32 (pool
+//    member x 16 channels), K = 16; conv2: M = 64 pooled positions x 2 profiles, N = 32,
+//    K = 80; conv3: M = 32 pooled positions x 4 profiles, N = 64, K = 160; conv2 and conv3
+//    keep one accumulator per pool member. Accumulators live in TMEM; the epilogue pools
+//    the two members in registers (the same TMEM lane), adds the bias, applies ReLU on
+//    packed BF16 pairs and writes the next layer's input.
 //    The pooled conv3 output (flattened position-major, feature = position * 64 + channel,
 //    with fc1's weights permuted to match) is written to global memory pre-tiled in the
 //    tensor-core operand layout, 128 profiles x 64 features per 16 KB block.
