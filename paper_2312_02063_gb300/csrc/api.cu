@@ -477,12 +477,12 @@ bool warp_box(const gpfc_ctx *ctx, int nbins)
            (ctx->box_path == GPFC_BOX_AUTO && nbins >= 256);
 }
 
-// The warp-per-profile box search as a two-stage pipeline forked off stream st: chunk i is
-// folded on a high-priority side stream into buffer i % 2 and scored on a low-priority
-// side stream, so the next fold's blocks take each SM as soon as the scorer's blocks leave
-// it and the two kernels' tails overlap. The fold of chunk i + 2 waits for the scorer of
-// chunk i (same buffer). Both side streams are joined back into st, also on error, so
-// that a capture stays whole.
+// A fold-then-score search as a two-stage pipeline forked off stream st (the two-kernel
+// box search, the CNN search): chunk i is folded on a high-priority side stream into
+// buffer i % 2 and scored on a low-priority side stream, so the next fold's blocks take
+// each SM as soon as the scorer's blocks leave it and the two stages' tails overlap. The
+// fold of chunk i + 2 waits for the scoring of chunk i (same buffer). Both side streams
+// are joined back into st, also on error, so that a capture stays whole.
 template <class FoldFn, class BoxFn>
 cudaError_t box_pipeline(gpfc_ctx *ctx, cudaStream_t st, int64_t nchunks, FoldFn fold, BoxFn box)
 {
@@ -735,8 +735,10 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
     FoldBuffers fb{};
     Carver c(nullptr);
     c.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
-    c.take<float>((size_t)chunk * nbins);
-    c.take<int32_t>((size_t)chunk * nbins);
+    for (int b = 0; b < 2; ++b) {
+        c.take<float>((size_t)chunk * nbins);
+        c.take<int32_t>((size_t)chunk * nbins);
+    }
     c.take<uint8_t>(cnn_dev_bytes());
     c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
     c.take<unsigned long long>(1);
@@ -745,8 +747,12 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
     Carver w(ctx->ws);
     uint8_t *fold_base = w.take<uint8_t>(carve_fold(nullptr, pl, n, 1, nbins, fb));
     carve_fold(fold_base, pl, n, 1, nbins, fb);
-    float *cf = w.take<float>((size_t)chunk * nbins);
-    int32_t *cc = w.take<int32_t>((size_t)chunk * nbins);
+    float *cf[2];
+    int32_t *cc[2];
+    for (int b = 0; b < 2; ++b) {
+        cf[b] = w.take<float>((size_t)chunk * nbins);
+        cc[b] = w.take<int32_t>((size_t)chunk * nbins);
+    }
     const CnnDev dev = cnn_dev_carve(w.take<uint8_t>(cnn_dev_bytes()));
     uint8_t *h3t = w.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
     unsigned long long *key = w.take<unsigned long long>(1);
@@ -756,8 +762,11 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
     if (e == cudaSuccess) e = launch_cnn_prep(cnn_src(wt), dev, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
     KernelTimer timer(ctx);
-    for (int64_t k0 = 0; k0 < np; k0 += chunk) {
-        const int64_t nk = std::min<int64_t>(chunk, np - k0);
+    // the same two-stream pipeline as the box search: chunk i folds on the high-priority
+    // stream into buffer i % 2 while the CNN scores chunk i - 1 on the low-priority one
+    // (its fc1 operand tiles are used on that stream only)
+    auto fold = [&](int64_t i, int b, cudaStream_t sf) {
+        const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);
         FoldParams p{};
         p.smp = fb.smp;
         p.n = n;
@@ -774,23 +783,26 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
-        p.folded = cf;
-        p.counts = cc;
+        p.folded = cf[b];
+        p.counts = cc[b];
         p.status = ctx->status_dev;
-        e = launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), ctx->stream);
-        if (e != cudaSuccess) return cuda_err(ctx, e, "fold kernel");
-        for (int64_t h0 = 0; h0 < nk; h0 += half) {
+        return launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), sf);
+    };
+    auto cnn = [&](int64_t i, int b, cudaStream_t sb) {
+        const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);
+        cudaError_t ec = cudaSuccess;
+        for (int64_t h0 = 0; h0 < nk && ec == cudaSuccess; h0 += half) {
             const int64_t nh = std::min<int64_t>(half, nk - h0);
             CnnConvParams cp{};
-            cp.folded = cf;
-            cp.counts = cc;
+            cp.folded = cf[b];
+            cp.counts = cc[b];
             cp.k_begin = h0;
             cp.np = nh;
             cp.w = dev;
             cp.h3t = h3t;
             cp.status = ctx->status_dev;
-            e = launch_cnn_conv(cp, ctx->num_sms, ctx->stream);
-            if (e != cudaSuccess) return cuda_err(ctx, e, "CNN conv kernel");
+            ec = launch_cnn_conv(cp, ctx->num_sms, sb);
+            if (ec != cudaSuccess) break;
             CnnFcParams fp{};
             fp.h3t = h3t;
             fp.k_begin = h0;
@@ -798,10 +810,12 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
             fp.w = dev;
             fp.score = score + k0;
             fp.status = ctx->status_dev;
-            e = launch_cnn_fc(fp, ctx->num_sms, ctx->stream);
-            if (e != cudaSuccess) return cuda_err(ctx, e, "CNN fc kernel");
+            ec = launch_cnn_fc(fp, ctx->num_sms, sb);
         }
-    }
+        return ec;
+    };
+    e = box_pipeline(ctx, ctx->stream, (np + chunk - 1) / chunk, fold, cnn);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "fold and CNN kernels");
     timer.stop();
     if (best_index || best_score) {
         e = cudaMemsetAsync(key, 0, sizeof(*key), ctx->stream);
