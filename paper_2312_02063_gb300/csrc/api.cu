@@ -957,15 +957,13 @@ struct BatchArgs {
 struct BatchBuffers {
     int64_t *lc_s, *grid_s, *task_off;
     FoldBuffers fb;
-    float *cf;
-    int32_t *cc;
-    int64_t *slot_k;
     CnnDev dev;
     uint8_t *h3t;
-    // warp-per-profile box search: two chunks of sums, counts and slot maps
-    float *box_sum[2];
-    int32_t *box_cnt[2];
-    int64_t *box_slot[2];
+    // two chunks of profiles (box: centred sums; CNN: means), counts and slot maps, for the
+    // fold/score pipeline
+    float *chunk_f[2];
+    int32_t *chunk_c[2];
+    int64_t *chunk_k[2];
     // one-kernel box search: the blocks' two-slot rings
     float *ring_s;
     int32_t *ring_c;
@@ -989,18 +987,15 @@ size_t carve_batched(void *base, const BatchArgs &A, const FoldPlan &pl, int64_t
         B.ring_s = c.take<float>(rows * A.nbins);
         B.ring_c = c.take<int32_t>(rows * A.nbins);
         B.ring_k = c.take<int64_t>(rows);
-    } else if (A.scorer == GPFC_SCORER_BOX && A.box_warp) {
+    } else if (A.scorer == GPFC_SCORER_CNN || A.box_warp) {
         for (int b = 0; b < 2; ++b) {
-            B.box_sum[b] = c.take<float>((size_t)slots * A.nbins);
-            B.box_cnt[b] = c.take<int32_t>((size_t)slots * A.nbins);
-            B.box_slot[b] = c.take<int64_t>(slots);
+            B.chunk_f[b] = c.take<float>((size_t)slots * A.nbins);
+            B.chunk_c[b] = c.take<int32_t>((size_t)slots * A.nbins);
+            B.chunk_k[b] = c.take<int64_t>(slots);
         }
     }
     if (A.scorer == GPFC_SCORER_CNN) {
         const int64_t half = (slots + 1) / 2;
-        B.cf = c.take<float>((size_t)slots * A.nbins);
-        B.cc = c.take<int32_t>((size_t)slots * A.nbins);
-        B.slot_k = c.take<int64_t>(slots);
         uint8_t *d = c.take<uint8_t>(cnn_dev_bytes());
         B.dev = base ? cnn_dev_carve(d) : CnnDev{};
         B.h3t = c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
@@ -1069,9 +1064,9 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
         const int64_t wave = (int64_t)pl.grid;
         auto fold = [&](int64_t i, int b, cudaStream_t sf) {
             FoldParams q = p;
-            q.sums = B.box_sum[b];
-            q.counts = B.box_cnt[b];
-            q.slot_k = B.box_slot[b];
+            q.sums = B.chunk_f[b];
+            q.counts = B.chunk_c[b];
+            q.slot_k = B.chunk_k[b];
             q.task_begin = i * wave;
             q.ntasks = std::min<int64_t>(T, q.task_begin + wave);
             return launch_fold(q, kModeFold, (int)(q.ntasks - q.task_begin), sf);
@@ -1079,9 +1074,9 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
         auto box = [&](int64_t i, int b, cudaStream_t sb) {
             const int64_t tb = i * wave, te = std::min<int64_t>(T, tb + wave);
             BoxCoopParams q{};
-            q.sums = B.box_sum[b];
-            q.counts = B.box_cnt[b];
-            q.slot_k = B.box_slot[b];
+            q.sums = B.chunk_f[b];
+            q.counts = B.chunk_c[b];
+            q.slot_k = B.chunk_k[b];
             q.rows = (te - tb) * pl.ppc;
             q.nbins = A.nbins;
             q.w_min = A.box.w_min;
@@ -1114,39 +1109,47 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
         return e;
     }
     e = launch_cnn_prep(cnn_src(&A.wt), B.dev, st);
-    const int64_t wave = (int64_t)pl.grid * 1;  // tasks per chunk: one per resident block
-    p.folded = B.cf;
-    p.counts = B.cc;
-    p.slot_k = B.slot_k;
-    for (int64_t tb = 0; tb < T && e == cudaSuccess; tb += wave) {
-        const int64_t te = std::min<int64_t>(T, tb + wave);
-        p.task_begin = tb;
-        p.ntasks = te;
-        e = launch_fold(p, kModeFold, (int)(te - tb), st);
+    if (e != cudaSuccess) return e;
+    // chunks of one task per resident block through the fold/score pipeline
+    const int64_t wave = (int64_t)pl.grid;
+    auto fold = [&](int64_t i, int b, cudaStream_t sf) {
+        FoldParams q = p;
+        q.folded = B.chunk_f[b];
+        q.counts = B.chunk_c[b];
+        q.slot_k = B.chunk_k[b];
+        q.task_begin = i * wave;
+        q.ntasks = std::min<int64_t>(T, q.task_begin + wave);
+        return launch_fold(q, kModeFold, (int)(q.ntasks - q.task_begin), sf);
+    };
+    auto cnn = [&](int64_t i, int b, cudaStream_t sb) {
+        const int64_t tb = i * wave, te = std::min<int64_t>(T, tb + wave);
         const int64_t slots = (te - tb) * pl.ppc, half = (slots + 1) / 2;
-        for (int64_t h0 = 0; h0 < slots && e == cudaSuccess; h0 += half) {
+        cudaError_t ec = cudaSuccess;
+        for (int64_t h0 = 0; h0 < slots && ec == cudaSuccess; h0 += half) {
             const int64_t nh = std::min<int64_t>(half, slots - h0);
             CnnConvParams cp{};
-            cp.folded = B.cf;
-            cp.counts = B.cc;
+            cp.folded = B.chunk_f[b];
+            cp.counts = B.chunk_c[b];
             cp.k_begin = h0;
             cp.np = nh;
             cp.w = B.dev;
             cp.h3t = B.h3t;
             cp.status = ctx->status_dev;
-            e = launch_cnn_conv(cp, ctx->num_sms, st);
-            if (e != cudaSuccess) break;
+            ec = launch_cnn_conv(cp, ctx->num_sms, sb);
+            if (ec != cudaSuccess) break;
             CnnFcParams fp{};
             fp.h3t = B.h3t;
             fp.k_begin = h0;
             fp.np = nh;
             fp.w = B.dev;
             fp.score = A.score;
-            fp.slot_k = B.slot_k;
+            fp.slot_k = B.chunk_k[b];
             fp.status = ctx->status_dev;
-            e = launch_cnn_fc(fp, ctx->num_sms, st);
+            ec = launch_cnn_fc(fp, ctx->num_sms, sb);
         }
-    }
+        return ec;
+    };
+    e = box_pipeline(ctx, st, (T + wave - 1) / wave, fold, cnn);
     if (e == cudaSuccess && want_best) {
         e = launch_argmax_segmented(A.score, B.grid_s, A.S, B.fb.key, ctx->num_sms, st);
         if (e == cudaSuccess) e = launch_argmax_finalize(B.fb.key, A.S, A.best_index, A.best_score, st);
