@@ -1387,7 +1387,8 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
         return GPFC_OK;
     }
     // the largest of a fold (gpfc_fold, the epilogue search), the warp-per-profile search
-    // and the one-kernel search
+    // and the one-kernel search; planning them leaves the context's last plan as it was
+    const gpfc_fold_config last = ctx->last_plan;
     const FoldPlan pb = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeBox, n));
     const FoldPlan pf = plan_fold(ctx, n, n_periods, nbins, find_tuned(ctx, nbins, kModeFold, n));
     FoldBuffers fb{};
@@ -1397,6 +1398,7 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
         FusedBuffers B{};
         *bytes = std::max(*bytes, carve_fused(nullptr, ps, n, nbins, B));
     }
+    ctx->last_plan = last;
     return GPFC_OK;
 }
 
