@@ -15,6 +15,7 @@ replica (no data-path communication); value counts the work of all ranks.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -69,9 +70,11 @@ def env_rank():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi clocks and throttle reasons every 20 ms; started before the
+    warm-up so that it is running when the timed region starts, it keeps only the samples
+    whose nvidia-smi timestamps fall inside the region marked by begin() and end()."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -79,12 +82,19 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = (None, None)
+
+    def begin(self):
+        self.window = (datetime.datetime.now(), None)
+
+    def end(self):
+        self.window = (self.window[0], datetime.datetime.now())
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -105,21 +115,26 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = self.window
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                mhz, mhz_max = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            if t0 is not None and (ts < t0 or (t1 is not None and ts > t1)):
+                continue  # outside the timed region
+            sm.append(mhz)
+            smax.append(mhz_max)
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 20}
 
 
 def measured_peaks():
@@ -337,6 +352,8 @@ def run_gpu(args, rank, world, local_rank):
     def step():
         g.gpfc_search(ctx, t_d, f_d, p_d, NBINS, lc.t0, g.SCORER_BOX, 1, W_MAX, 0.0, score, bi, bs)
 
+    clocks = ClockSampler(local_rank)
+    clocks.start()  # running before the timed region begins
     for _ in range(max(3, args.warmup)):
         step()
     ctx.sync()
@@ -344,11 +361,10 @@ def run_gpu(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms = []
     fold_ms, fold_launches = [], []
-    clocks = ClockSampler(local_rank)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps, outside the events
@@ -361,6 +377,7 @@ def run_gpu(args, rank, world, local_rank):
         fold_launches.append(fl)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.end()
     clk = clocks.stop()
     ctx.set_timing(False)
     ctx.sync()
