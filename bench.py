@@ -35,7 +35,7 @@ UNIT = "sample·period folds/s"
 NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
-SM_FOLD_UPDATES_PER_CLK = 8           # shared-memory pipe bound of the fold, per SM
+SM_FOLD_UPDATES_PER_CLK = 8           # the pipe model: 128 B/clk / (8 B read + 8 B written)
 # DRAM bytes (read + write) per period of the one-kernel search (fold + box-SNR) of the same
 # light curve, from an ncu capture of a 58,368-period search; the search's traffic grows
 # with the number of periods (ring writes, one light-curve pass per task).
@@ -423,7 +423,17 @@ def run_gpu(args, rank, world, local_rank):
         peaks, src = measured_peaks()
         smax = float(peaks.get("sm_max_mhz", 2070.0))
         sms = ctx.num_sms
-        peak_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
+        model_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
+        # the fold's binding pipe, measured here: lane-private 8-byte shared-memory
+        # read-modify-writes (the fold's bin record) at full occupancy, and at the fold's own
+        # footprint (256 bins x 3 warps per SM)
+        probe = {}
+        for key, cfg in (("rmw8_full", (8, 32, 16, 1)), ("rmw8_fold_footprint", (8, 256, 3, 1)),
+                         ("rmw4_full", (4, 32, 16, 1))):
+            ups, upc = g.gpfc_probe_smem_rmw(*cfg, iters=20000)
+            probe[key] = {"gupdates_per_s": ups / 1e9, "updates_per_clk_sm": upc,
+                          "config": f"{cfg[0]}-byte words, {cfg[1]} bins x {cfg[2]} warps per SM"}
+        peak_gups = probe["rmw8_full"]["gupdates_per_s"]
         kmean = statistics.mean(kernel_ms)
         # the search kernel's own launch (fold + box-SNR): all n * N_PERIODS updates of a step
         # over its duration
@@ -445,15 +455,21 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
-            "roofline": {"bound": "alu", "kernel": "fold_kernel<search> (fold + box-SNR)", "achieved": achieved,
+            "roofline": {"bound": "smem", "kernel": "fold_kernel<search> (fold + box-SNR)", "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                          "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None
                          else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS,
                          "traffic_basis": "ncu dram__bytes_read+write of a 58,368-period search, scaled by periods",
                          "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
                          "search_ms": kmean,
-                         "peak_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} bin updates/clk "
-                                       f"(shared-memory pipe) x {smax:.0f} MHz ({src} sm_max_mhz)"},
+                         "peak_basis": "measured in this run by gpfc_probe_smem_rmw: lane-private 8-byte "
+                                       "(FP32 sum + 32-bit count) shared-memory read-modify-writes, 16 warps x "
+                                       f"32 bins per SM, {probe['rmw8_full']['updates_per_clk_sm']:.2f} "
+                                       "updates/clk/SM",
+                         "peak_model": model_gups,
+                         "peak_model_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} updates/clk (128 B/clk over "
+                                             f"16 B per update) x {smax:.0f} MHz ({src} sm_max_mhz)",
+                         "probe": probe},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},

@@ -347,7 +347,10 @@ int gpfc_best_period(gpfc_ctx *ctx, const float *score, int64_t n_periods,
  *  - All calls share the one key: calls that overlap on the GPU (different streams, or
  *    different host threads without ordering) race and may return each other's result.
  *    The key is cleared at the start of every call.
- * Returns GPFC_OK, GPFC_EINVAL or GPFC_ECUDA (enqueue failure). */
+ * Returns GPFC_OK, GPFC_EINVAL (checked before any CUDA call) or GPFC_ECUDA (enqueue
+ * failure). If an error from earlier work is already pending in the calling thread
+ * (cudaPeekAtLastError), the call returns GPFC_ECUDA at once, launches nothing and leaves
+ * that error pending for its owner. */
 int gpfc_best_period_noalloc(const float *score, int64_t n_periods, int64_t *best_index,
                              float *best_score, void *stream);
 
@@ -474,6 +477,26 @@ int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offset
                         const void *scorer_params, float *score, int64_t *best_index,
                         float *best_score);
 int gpfc_set_graph(gpfc_ctx *ctx, int enable);
+
+/* ------------------------------------------------------------------ measurement
+ * Peak rate of the fold's binding pipe. The paper has no counterpart: it is the
+ * denominator of the fold's roofline. The accumulation of Sec. 2.3 step 3 is one
+ * read-modify-write of a trial period's bin record in shared memory per sample and
+ * period; this call times a kernel that does only that, with each lane's records laid out
+ * [bin][lane] as the fold keeps them, eight distinct bins updated per iteration, and
+ * reports the rate.
+ *  - word_bytes 8: the fold's record (FP32 sum + 32-bit count, one 64-bit load and store);
+ *    4: one 32-bit integer word.
+ *  - nbins (power of two, 8..4096) words per lane, warps per block (1..32), blocks_per_sm
+ *    co-resident blocks per SM (the call checks they fit), iters iterations of 8 updates.
+ *  - Runs on the current device and `stream` (a cudaStream_t, NULL = default stream) and
+ *    synchronises on its own events; allocates two small device buffers.
+ *  - updates_per_s: lane-updates per second (CUDA events); updates_per_clk_sm: per SM
+ *    clock cycle (clock64 span of the slowest block). Either may be NULL.
+ * Returns GPFC_OK, GPFC_EINVAL (bad sizes, or the blocks do not fit one SM together) or
+ * GPFC_ECUDA. */
+int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t nbins, int32_t warps, int32_t blocks_per_sm,
+                        int64_t iters, void *stream, double *updates_per_s, double *updates_per_clk_sm);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_probe_smem_rmw", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -131,6 +131,9 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_last_fold_plan.argtypes = [_vp, ctypes.POINTER(FoldConfig)]
         L.gpfc_workspace_size.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_size_t)]
+        L.gpfc_probe_smem_rmw.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
         _lib = L
         return L
 
@@ -361,6 +364,22 @@ def gpfc_best_period(ctx: Context, score, best_index=None, best_score=None):
     ctx._check(ctx.lib.gpfc_best_period(ctx.handle, _ptr(score), score.numel(), _ptr(best_index),
                                         _ptr(best_score)))
     return best_index, best_score
+
+
+def gpfc_probe_smem_rmw(word_bytes: int = 8, nbins: int = 32, warps: int = 16, blocks_per_sm: int = 1,
+                        iters: int = 20000, stream=None):
+    """Measured rate of lane-private shared-memory read-modify-writes (see include/gpfc.h):
+    returns (updates per second, updates per SM clock cycle). Runs on the current device."""
+    lib = load_library()
+    if not torch.cuda.is_available():
+        raise GpfcError(-3, "no CUDA device: libgpfc runs on the GPU only")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ups, upc = ctypes.c_double(), ctypes.c_double()
+    rc = lib.gpfc_probe_smem_rmw(word_bytes, nbins, warps, blocks_per_sm, iters, _vp(s.cuda_stream),
+                                 ctypes.byref(ups), ctypes.byref(upc))
+    if rc != 0:
+        raise GpfcError(rc, lib.gpfc_strerror(rc).decode())
+    return ups.value, upc.value
 
 
 def gpfc_best_period_noalloc(score, best_index, best_score, stream=None):

@@ -50,6 +50,10 @@ extern "C" int gpfc_best_period_noalloc(const float *score, int64_t n_periods, i
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return GPFC_ECUDA;
     unsigned long long *key = nullptr;
     if (key_address(device, &key) != cudaSuccess) return GPFC_ECUDA;
+    // An error left pending by earlier work in this thread is not this call's to report or
+    // clear: refuse to run and leave it pending, so the launch status checked below is only
+    // this call's own.
+    if (cudaPeekAtLastError() != cudaSuccess) return GPFC_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the key keeps the previous call's value: clear it before the reduction
     cudaError_t e = cudaMemsetAsync(key, 0, sizeof(unsigned long long), st);

@@ -120,3 +120,29 @@ def test_batched_entry_rejects_null_context_without_gpu():
     ms, nl = ctypes.c_float(), ctypes.c_int32()
     assert lib.gpfc_fold_launch_times(None, ctypes.byref(ms), ctypes.byref(nl)) == -1
 
+
+
+def test_noalloc_entry_rejects_bad_arguments_without_gpu():
+    """gpfc_best_period_noalloc checks its arguments before any CUDA call, so the
+    rejections run here with fake (never dereferenced) device pointers."""
+    import ctypes
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    fake = ctypes.c_void_p(0x1000)
+    f = lib.gpfc_best_period_noalloc
+    assert f(None, 10, fake, fake, None) == -1           # no score
+    assert f(fake, 10, None, None, None) == -1           # both outputs NULL
+    assert f(fake, 0, fake, fake, None) == -1            # empty
+    assert f(fake, -5, fake, None, None) == -1           # negative size
+    assert f(fake, 2 ** 31, fake, None, None) == -1      # beyond the 32-bit index of the key
+    assert f(fake, 2 ** 40, None, fake, None) == -1
+
+
+def test_smem_probe_rejects_bad_arguments_without_gpu():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    f = lib.gpfc_probe_smem_rmw
+    assert f(6, 32, 16, 1, 100, None, None, None) == -1      # word size
+    assert f(8, 48, 16, 1, 100, None, None, None) == -1      # not a power of two
+    assert f(8, 32, 0, 1, 100, None, None, None) == -1       # no warps
+    assert f(4, 32, 16, 1, 0, None, None, None) == -1        # no iterations

@@ -37,6 +37,29 @@ def test_noalloc_best_period_matches_context_entry_point_twice():
     ctx.close()
 
 
+def test_noalloc_with_one_output_given():
+    """Either output may be NULL: index only, then score only, each equal to the context
+    entry point's answer."""
+    import paper_2312_02063_gb300 as g
+    ctx = g.Context(0)
+    dev = ctx.device
+    lib = g.load_library()
+    rng = np.random.default_rng(7)
+    a = torch.from_numpy(rng.normal(0, 1, 100_003).astype(np.float32)).to(dev)
+    ref_i, ref_s = g.gpfc_best_period(ctx, a)
+    ctx.sync()
+    out_i = torch.full((1,), -7, dtype=torch.int64, device=dev)
+    out_s = torch.full((1,), -7.0, dtype=torch.float32, device=dev)
+    stream = g._vp(torch.cuda.current_stream(dev).cuda_stream)
+    assert lib.gpfc_best_period_noalloc(g._ptr(a), a.numel(), g._ptr(out_i), None, stream) == 0
+    torch.cuda.synchronize()
+    assert int(out_i.item()) == int(ref_i.item()) and float(out_s.item()) == -7.0
+    assert lib.gpfc_best_period_noalloc(g._ptr(a), a.numel(), None, g._ptr(out_s), stream) == 0
+    torch.cuda.synchronize()
+    assert float(out_s.item()) == float(ref_s.item())
+    ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit():
     import paper_2312_02063_gb300 as g
     lib = g.load_library()
