@@ -58,8 +58,9 @@ struct gpfc_ctx {
 
 namespace {
 
-// Profiles scored per CNN launch pair: their fc1 operand tiles (64 MB) stay in L2.
-constexpr int64_t kCnnChunk = 16384;
+// Profiles scored per CNN launch pair: their fc1 operand tiles (high and low BF16 terms,
+// 64 MB) stay in L2.
+constexpr int64_t kCnnChunk = 8192;
 
 // Message of the last failure that had no context to hold it (gpfc_create).
 thread_local char g_create_error[512] = {0};
@@ -740,7 +741,7 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         c.take<int32_t>((size_t)chunk * nbins);
     }
     c.take<uint8_t>(cnn_dev_bytes());
-    c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+    c.take<uint8_t>(cnn_h3t_bytes(half));
     c.take<unsigned long long>(1);
     int rc = ensure_ws(ctx, c.off + 256);
     if (rc) return rc;
@@ -754,7 +755,7 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         cc[b] = w.take<int32_t>((size_t)chunk * nbins);
     }
     const CnnDev dev = cnn_dev_carve(w.take<uint8_t>(cnn_dev_bytes()));
-    uint8_t *h3t = w.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+    uint8_t *h3t = w.take<uint8_t>(cnn_h3t_bytes(half));
     unsigned long long *key = w.take<unsigned long long>(1);
 
     cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G, fb.stats,
@@ -998,7 +999,7 @@ size_t carve_batched(void *base, const BatchArgs &A, const FoldPlan &pl, int64_t
         const int64_t half = (slots + 1) / 2;
         uint8_t *d = c.take<uint8_t>(cnn_dev_bytes());
         B.dev = base ? cnn_dev_carve(d) : CnnDev{};
-        B.h3t = c.take<uint8_t>((size_t)((half + 127) / 128) * 32 * 128 * 64 * 2);
+        B.h3t = c.take<uint8_t>(cnn_h3t_bytes(half));
     }
     return c.off + 256;
 }
@@ -1552,12 +1553,12 @@ static int cnn_forward(gpfc_ctx *ctx, const float *folded, const int32_t *counts
     const int64_t chunk = std::min<int64_t>(n_periods, kCnnChunk);
     Carver c(nullptr);
     c.take<uint8_t>(cnn_dev_bytes());
-    c.take<uint8_t>((size_t)((chunk + 127) / 128) * 32 * 128 * 64 * 2);
+    c.take<uint8_t>(cnn_h3t_bytes(chunk));
     rc = ensure_ws(ctx, c.off + 256);
     if (rc) return rc;
     Carver c2(ctx->ws);
     const CnnDev dev = cnn_dev_carve(c2.take<uint8_t>(cnn_dev_bytes()));
-    uint8_t *h3t = c2.take<uint8_t>((size_t)((chunk + 127) / 128) * 32 * 128 * 64 * 2);
+    uint8_t *h3t = c2.take<uint8_t>(cnn_h3t_bytes(chunk));
     const CnnSrc src{wt->conv1_w, wt->conv1_b, wt->conv2_w, wt->conv2_b, wt->conv3_w,
                      wt->conv3_b, wt->fc1_w,   wt->fc1_b,   wt->fc2_w,   wt->fc2_b};
     cudaError_t e = launch_cnn_prep(src, dev, ctx->stream);

@@ -131,14 +131,16 @@ struct LoadDZ1T {  // A(m = j, k = profile) = dZ1[k][j]
     const float *dZ1;
     __device__ float operator()(int m, int k) const { return dZ1[(size_t)k * 256 + m]; }
 };
-struct LoadH3 {  // B(k = profile, n = fd) from the fc1 operand tiles
+struct LoadH3 {  // B(k = profile, n = fd) from the fc1 operand tiles: high + low BF16 terms
     const uint8_t *h3t;
     __device__ float operator()(int k, int fd) const
     {
         const int mt = k >> 7, r = k & 127, kc = fd >> 6, kk = fd & 63;
-        const size_t off = ((size_t)mt * 32 + kc) * (128 * 64 * 2) +
+        const size_t off = ((size_t)mt * kH3Chunks + kc) * (128 * 64 * 2) +
                            (size_t)((r >> 3) * 1024 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2);
-        return bf2f(*reinterpret_cast<const uint16_t *>(h3t + off));
+        const size_t lo = (size_t)32 * (128 * 64 * 2);  // the low terms' chunk kc + 32
+        return bf2f(*reinterpret_cast<const uint16_t *>(h3t + off)) +
+               bf2f(*reinterpret_cast<const uint16_t *>(h3t + off + lo));
     }
 };
 struct StoreDW1 {  // grad of fc1.w in PyTorch order
@@ -297,7 +299,7 @@ CnnSaved CnnSaved::layout(int64_t B)
     s.a2 = take((size_t)B * 32 * 128 * 4);
     s.h2 = take((size_t)B * 32 * 64 * 2);
     s.a3 = take((size_t)B * 64 * 64 * 4);
-    s.h3t = take((size_t)((B + 127) / 128) * 32 * 128 * 64 * 2);
+    s.h3t = take(cnn_h3t_bytes(B));
     s.z1 = take((size_t)B * 256 * 4);
     s.total = (o + 255) & ~(size_t)255;
     return s;

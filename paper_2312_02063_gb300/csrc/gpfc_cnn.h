@@ -24,6 +24,15 @@ struct CnnDev {
     uint8_t *W1t;  // fc1 weights, 32 K chunks of 256 x 64 BF16
 };
 
+// The conv3 output as fc1's A operand: per tile of 128 profiles, kH3Chunks K chunks of
+// 128 x 64 BF16 (16 KB), the 32 chunks of the activations' high BF16 terms followed by the 32
+// chunks of their low terms (each activation is carried as hi + lo).
+// The same allocation ends with the fc kernel's partial fc2 dot products, [2][tiles * 128]
+// FP32 (used when a launch splits fc1's 256 outputs over two blocks).
+constexpr int kH3Chunks = 64;
+inline size_t cnn_h3t_tiles_bytes(int64_t np) { return (size_t)((np + 127) / 128) * kH3Chunks * 128 * 64 * 2; }
+inline size_t cnn_h3t_bytes(int64_t np) { return cnn_h3t_tiles_bytes(np) + (size_t)((np + 127) / 128) * 128 * 2 * 4; }
+
 struct CnnDevLayout {
     static constexpr size_t w1 = 0;
     static constexpr size_t b1 = 512;
@@ -45,9 +54,9 @@ struct CnnConvParams {
     int64_t k_begin;         // first profile of this launch
     int64_t np;              // profiles in this launch
     CnnDev w;
-    uint8_t *h3t;            // [ceil(np/128)][32][128 x 64 BF16 tile] (local profile index)
+    uint8_t *h3t;            // [ceil(np/128)][kH3Chunks][128 x 64 BF16 tile] (local profile index)
     // activations kept for the backward pass (NULL at inference), local profile index
-    float *xsave;            // [np][256] normalised input (BF16 values)
+    float *xsave;            // [np][256] normalised input as the network sees it (hi + lo)
     float *a1save;           // [np][16][256] FP32 conv1 pre-activation
     uint16_t *h1save;        // [np][16][128] BF16
     float *a2save;           // [np][32][128] FP32 conv2 pre-activation
@@ -67,6 +76,8 @@ struct CnnFcParams {
     float *z1save;           // [np][256] fc1 pre-activation (NULL at inference)
     uint32_t *status;
     int tiles_per_block;     // set by launch_cnn_fc: 128-profile tiles per block (1 or 2)
+    int n_halves;            // set by launch_cnn_fc: 1, or 2 (a block takes one tile and half of N)
+    float *zpart;            // set by launch_cnn_fc: partial fc2 dots [2][tiles * 128] (n_halves = 2)
 };
 
 // Offsets (bytes) of the activations a training forward keeps for the backward pass.
@@ -94,6 +105,7 @@ CnnDev cnn_dev_carve(void *base);
 cudaError_t cnn_register_kernels();
 cudaError_t launch_cnn_prep(const CnnSrc &src, const CnnDev &dst, cudaStream_t st);
 cudaError_t launch_cnn_conv(const CnnConvParams &p, int num_sms, cudaStream_t st);
+// fc1 + fc2 + sigmoid over the tiles at p.h3t (an allocation of cnn_h3t_bytes(p.np) bytes).
 cudaError_t launch_cnn_fc(const CnnFcParams &p, int num_sms, cudaStream_t st);
 
 }  // namespace gpfc

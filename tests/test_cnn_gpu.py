@@ -51,8 +51,12 @@ def test_cnn_scores_match_oracle(ctx, n, seed, scale):
     z, s = run(ctx, prof, w)
     zo, so = oracle.cnn_score(w, prof)
     assert np.max(np.abs(s - so)) <= SCORE_ATOL, np.max(np.abs(s - so))
-    agree = np.mean((s > 0.5) == (so > 0.5))
-    assert agree >= 0.999 or n < 1000 and np.all(np.abs(so[(s > 0.5) != (so > 0.5)] - 0.5) < SCORE_ATOL)
+    flip = (s > 0.5) != (so > 0.5)
+    if n >= 1000:
+        assert np.mean(~flip) >= 0.999, np.mean(~flip)
+    else:
+        # one to three profiles: a flip is allowed only at a tie, within 1e-3 of 0.5
+        assert np.all(np.abs(so[flip] - 0.5) < 1e-3), so[flip]
     np.testing.assert_allclose(1 / (1 + np.exp(-z)), s, atol=1e-6)
     assert np.max(np.abs(z - zo)) <= 0.05 * (1 + np.max(np.abs(zo)))
 
@@ -124,4 +128,9 @@ def test_cnn_full_size_batch_sampled(ctx):
     _, so = oracle.cnn_score(w, pf, pc)
     assert np.max(np.abs(s[idx] - so)) <= SCORE_ATOL
     flip = (s[idx] > 0.5) != (so > 0.5)
-    assert np.mean(~flip) >= 0.999 or np.all(np.abs(so[flip] - 0.5) < SCORE_ATOL)
+    print(f"full batch: {flip.sum()} decision flips at 0.5 in {len(idx)} sampled profiles, oracle scores "
+          f"{so[flip]}")
+    # 300 samples resolve 99.9% agreement only as 'no flip': a flip is allowed only at a
+    # tie, within 1e-3 of 0.5 (the agreement itself is measured on 20,000 profiles in
+    # test_cnn_trained_gpu.py)
+    assert np.all(np.abs(so[flip] - 0.5) < 1e-3), so[flip]

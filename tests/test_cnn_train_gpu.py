@@ -1,11 +1,12 @@
 """GPU parity of the CNN training path (backward, loss, Adam) against the FP64 oracle.
 
 The oracle's FP64 gradient is itself pinned to central finite differences on the CPU
-(tests/test_oracle_cnn.py). GPU gradients come from BF16 activations and weights, so
-they are compared by cosine similarity (>= 0.999) and relative L2 error per parameter
-tensor. The bound GRAD_REL = 3e-2 is about 15 BF16 unit roundoffs (2^-9): a conv weight
-gradient passes through six to ten BF16-rounded quantities (input, pooled activations,
-weights of the layers above); measured errors are about 1-2.2%.
+(tests/test_oracle_cnn.py). GPU gradients come from the tensor-core forward (BF16
+weights, activations carried as two BF16 terms, FP32 accumulation) and an FP32 backward,
+so they are compared by cosine similarity (>= 0.999) and relative L2 error per parameter
+tensor: at most GRAD_REL = 2e-2 (the gradient tolerance of the scope table) and, as a
+regression bound, at most GRAD_REGRESSION = 2e-3 per tensor (measured: <= 6e-4 for the
+conv tensors, below 1e-4 for fc1 and fc2).
 """
 import numpy as np
 import pytest
@@ -17,7 +18,8 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 GRAD_COS = 0.999
-GRAD_REL = 3e-2
+GRAD_REL = 2e-2
+GRAD_REGRESSION = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -53,10 +55,11 @@ def test_gradients_match_fp64_oracle(ctx):
         b = grads_o[n].ravel()
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
         rel = float(np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300))
-        stats[n] = (round(cos, 6), round(rel, 4))
+        stats[n] = (round(cos, 7), float(f"{rel:.3g}"))
     print("gradient cosine / relative L2 vs FP64 oracle:", stats)
     for n, (cos, rel) in stats.items():
         assert cos >= GRAD_COS and rel <= GRAD_REL, (n, stats)
+        assert rel <= GRAD_REGRESSION, (n, stats)
 
 
 def test_autograd_function_matches_direct_calls(ctx):
