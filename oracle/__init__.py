@@ -327,3 +327,34 @@ def tpr_at_fpr(scores_pos, scores_neg, fpr):
     k = int(np.floor(fpr * len(neg)))
     thr = neg[k] if k < len(neg) else -np.inf
     return float(np.mean(np.asarray(scores_pos, np.float64) > thr)), float(thr)
+
+
+def roc(scores_pos, scores_neg, fprs=()):
+    """Detection statistics of one detector on a labelled set (Sec. 3.2: ROC curves of
+    stars scored by their best trial period, Figs. 10-13). A NaN score ranks below every
+    number (it is never a detection).
+
+    u2  = sum over (i, j) of 2 [pos_i > neg_j] + [pos_i == neg_j]   (an exact integer:
+          twice the Mann-Whitney U statistic, ties counted one half)
+    auc = u2 / (2 n_pos n_neg)
+    for each fpr: k = floor(fpr n_neg); thr = the (k+1)-th largest negative score (-inf when
+          k >= n_neg); tp = #{pos_i > thr}, tpr = tp / n_pos
+    Returns dict(u2, auc, thr [n_fpr] f64, tp [n_fpr] int64, tpr [n_fpr] f64).
+    """
+    p = np.asarray(scores_pos, np.float64).ravel()
+    n = np.asarray(scores_neg, np.float64).ravel()
+    p = np.where(np.isnan(p), -np.inf, p)
+    n = np.where(np.isnan(n), -np.inf, n)
+    ns = np.sort(n)
+    below = np.searchsorted(ns, p, side="left")      # negatives < p_i
+    upto = np.searchsorted(ns, p, side="right")      # negatives <= p_i
+    u2 = int(2 * np.sum(below, dtype=np.int64) + np.sum(upto - below, dtype=np.int64))
+    thr, tp = [], []
+    for f in fprs:
+        k = int(np.floor(float(f) * len(n)))
+        t = ns[len(n) - 1 - k] if k < len(n) else -np.inf
+        thr.append(t)
+        tp.append(int(np.sum(p > t)))
+    tp = np.asarray(tp, np.int64)
+    return {"u2": u2, "auc": u2 / (2.0 * len(p) * len(n)), "thr": np.asarray(thr, np.float64), "tp": tp,
+            "tpr": tp / float(len(p))}
