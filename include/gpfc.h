@@ -441,6 +441,23 @@ int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t
                const int64_t *grid_offsets, int64_t n_periods, double k_sigma, int32_t min_width,
                double harmonic_tol, int32_t max_peaks, gpfc_star_summary *summary, gpfc_peak *peaks);
 
+/* ------------------------------------------------------------------ detection statistics
+ * ROC statistics of a detector on labelled scores: the paper compares detectors by ROC
+ * curves of stars, each star scored by its best trial period (Sec. 3.2, Figs. 10-13).
+ *  - pos [n_pos], neg [n_neg] float32 scores (device), 1 <= n_pos, n_neg <= 2^30. A NaN
+ *    score ranks below every number (never a detection).
+ *  - u2 [1] int64 (device): sum over all (i, j) of 2 [pos_i > neg_j] + [pos_i == neg_j],
+ *    twice the Mann-Whitney U statistic; AUC = u2 / (2 n_pos n_neg), exactly.
+ *  - fpr [n_fpr] float64 HOST array of false-positive rates in [0, 1), 0 <= n_fpr <= 16:
+ *    for each, k = floor(fpr n_neg) and thr [f] float32 (device) = the (k+1)-th largest
+ *    negative score (-inf if k >= n_neg), tp [f] int64 (device) = #{pos_i > thr}; so
+ *    TPR = tp / n_pos at a false-positive rate of at most fpr. thr and tp may be NULL when
+ *    n_fpr = 0.
+ * Every output is a count over pairs of scores: exact, independent of launch order. Cost
+ * n_neg^2 + n_pos n_neg comparisons. Returns GPFC_OK, GPFC_EINVAL or GPFC_ECUDA. */
+int gpfc_roc(gpfc_ctx *ctx, const float *pos, int64_t n_pos, const float *neg, int64_t n_neg,
+             int32_t n_fpr, const double *fpr, int64_t *u2, float *thr, int64_t *tp);
+
 /* ------------------------------------------------------------------ batched search
  * gpfc_search over many stars of uneven length, each with its own period grid, in one
  * sequence of persistent launches (the paper folds one light curve at a time, Sec. 2.3;

@@ -116,6 +116,76 @@ def light_curve_kepler(seed: int = 20232204, n_cad: int = 65536, sigma_white: fl
 
 
 @dataclasses.dataclass
+class DetectionSet:
+    """Labelled stars (CSR) for the star-level detection comparison."""
+    lc_offsets: np.ndarray    # int64 [S+1]
+    times: np.ndarray         # float64 [sum N]
+    flux: np.ndarray          # float32 [sum N]
+    label: np.ndarray         # int8 [S]: 1 = one injected transit
+    sigma: np.ndarray         # float64 [S]: white-noise standard deviation
+    period: np.ndarray        # float64 [S]: injected period (NaN for label 0)
+    snr: np.ndarray           # float64 [S]: target SNR of the injection (Eq. 2; NaN for label 0)
+    epoch: np.ndarray         # float64 [S]: mid-transit epoch in [0, P) (NaN for label 0)
+    duration: np.ndarray      # float64 [S]: transit duration in days (NaN for label 0)
+    depth: np.ndarray         # float64 [S]: fractional depth (NaN for label 0)
+
+
+def detection_stars(n_stars: int = 20000, seed: int = 20235404, n_cad: int = 4096, sigma=(1e-4, 1e-3),
+                    snr=(4.0, 16.0), dur_h=(0.5, 3.0), p_range=(0.2, 1.0), gap_d=(1.0, 5.0),
+                    chunk: int = 1024) -> DetectionSet:
+    """Seeded labelled stars for star-level ROC curves (Sec. 3.2, Figs. 10-13): star s
+    carries one box transit when s is odd, none when s is even (noise only).
+
+    n_cad cadences at 29.4 min (t0 = 0) with two gaps of U[gap_d] days starting at uniform
+    times (samples inside either are dropped); flux = 1 + white noise of sigma log-uniform in
+    `sigma`; an injected box has period U[p_range] d, duration U[dur_h] h, epoch U[0, P) and
+    depth d = snr sigma / sqrt(n q) with snr ~ U[snr], n the star's sample count and q the
+    duty cycle dur / P (the SNR of Eq. 2); the flux is multiplied by (1 - d) in transit.
+    Per-star parameters are drawn first for all stars (PCG64, `seed`); the noise comes
+    from one generator per block of `chunk` stars (seed + 1 + block), so the set does not
+    depend on how it is consumed.
+    """
+    rng = _rng(seed)
+    S = int(n_stars)
+    T = n_cad * CADENCE_D
+    sig = np.exp(rng.uniform(np.log(sigma[0]), np.log(sigma[1]), S))
+    g0 = rng.uniform(0.0, T, (S, 2))
+    gl = rng.uniform(gap_d[0], gap_d[1], (S, 2))
+    per = rng.uniform(p_range[0], p_range[1], S)
+    dur = rng.uniform(dur_h[0], dur_h[1], S) / 24.0
+    epo = rng.uniform(0.0, 1.0, S) * per
+    tsnr = rng.uniform(snr[0], snr[1], S)
+    label = (np.arange(S) % 2).astype(np.int8)
+    t = np.arange(n_cad, dtype=np.float64) * CADENCE_D
+    times, flux, lens = [], [], []
+    for c0 in range(0, S, chunk):
+        c1 = min(S, c0 + chunk)
+        crng = _rng(seed + 1 + c0 // chunk)
+        keep = np.ones((c1 - c0, n_cad), bool)
+        for k in range(2):
+            keep &= ~((t[None, :] >= g0[c0:c1, k, None]) & (t[None, :] < g0[c0:c1, k, None] + gl[c0:c1, k, None]))
+        f = 1.0 + crng.normal(0.0, 1.0, (c1 - c0, n_cad)) * sig[c0:c1, None]
+        n = keep.sum(axis=1)
+        depth = tsnr[c0:c1] * sig[c0:c1] / np.sqrt(n * dur[c0:c1] / per[c0:c1])
+        P = per[c0:c1, None]
+        intr = np.abs(np.mod(t[None, :] - epo[c0:c1, None] + P / 2, P) - P / 2) < dur[c0:c1, None] / 2
+        f = np.where(intr & (label[c0:c1, None] == 1), f * (1.0 - depth[:, None]), f)
+        for r in range(c1 - c0):
+            times.append(t[keep[r]])
+            flux.append(f[r, keep[r]].astype(np.float32))
+        lens.append(n)
+    lens = np.concatenate(lens)
+    off = np.zeros(S + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    inj = label == 1
+    depth_all = tsnr * sig / np.sqrt(lens * dur / per)
+    nan = np.nan
+    return DetectionSet(off, np.concatenate(times), np.concatenate(flux), label, sig,
+                        np.where(inj, per, nan), np.where(inj, tsnr, nan), np.where(inj, epo, nan),
+                        np.where(inj, dur, nan), np.where(inj, depth_all, nan))
+
+
+@dataclasses.dataclass
 class StarBatch:
     """Many stars of uneven length, concatenated (CSR offsets)."""
     lc_offsets: np.ndarray    # int64 [S+1]

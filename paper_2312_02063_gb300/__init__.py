@@ -21,7 +21,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_probe_smem_rmw", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_probe_smem_rmw", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_roc", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -507,6 +507,26 @@ def gpfc_peaks(ctx: Context, score, periods, grid_offsets=None, k_sigma: float =
                                   float(k_sigma), int(min_width), float(harmonic_tol), int(max_peaks),
                                   _ptr(summary), _ptr(peaks) if max_peaks > 0 else None))
     return summary, peaks
+
+
+def gpfc_roc(ctx: Context, pos, neg, fprs=()):
+    """ROC statistics of labelled scores (see include/gpfc.h): returns device tensors
+    (u2 int64 [1], thr float32 [n_fpr], tp int64 [n_fpr]); AUC = u2 / (2 n_pos n_neg)."""
+    L = ctx.lib
+    if not getattr(L, "_gpfc_roc_bound", False):
+        L.gpfc_roc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_double), _vp, _vp, _vp]
+        L._gpfc_roc_bound = True
+    dev = ctx.device
+    _need(pos, torch.float32, dev, "pos")
+    _need(neg, torch.float32, dev, "neg")
+    f = (ctypes.c_double * max(1, len(fprs)))(*[float(x) for x in fprs])
+    u2 = torch.empty(1, dtype=torch.int64, device=dev)
+    thr = torch.empty(max(1, len(fprs)), dtype=torch.float32, device=dev)
+    tp = torch.empty(max(1, len(fprs)), dtype=torch.int64, device=dev)
+    ctx._check(L.gpfc_roc(ctx.handle, _ptr(pos), pos.numel(), _ptr(neg), neg.numel(), len(fprs), f, _ptr(u2),
+                          _ptr(thr), _ptr(tp)))
+    return u2, thr[: len(fprs)], tp[: len(fprs)]
 
 
 def peaks_to_numpy(summary, peaks, max_peaks: int = 8):

@@ -1855,6 +1855,38 @@ int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t
     return GPFC_OK;
 }
 
+int gpfc_roc(gpfc_ctx *ctx, const float *pos, int64_t n_pos, const float *neg, int64_t n_neg, int32_t n_fpr,
+             const double *fpr, int64_t *u2, float *thr, int64_t *tp)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!pos || !neg || !u2) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n_pos < 1 || n_pos > ((int64_t)1 << 30) || n_neg < 1 || n_neg > ((int64_t)1 << 30))
+        return set_err(ctx, GPFC_EINVAL, "n_pos and n_neg must be in [1, 2^30]");
+    if (n_fpr < 0 || n_fpr > kRocMaxFpr || (n_fpr > 0 && (!fpr || !thr || !tp)))
+        return set_err(ctx, GPFC_EINVAL, "bad false-positive rates (0..%d, host array, outputs)", kRocMaxFpr);
+    RocParams p{};
+    for (int f = 0; f < n_fpr; ++f) {
+        if (!(fpr[f] >= 0.0 && fpr[f] < 1.0)) return set_err(ctx, GPFC_EINVAL, "fpr[%d] outside [0, 1)", f);
+        p.k[f] = (int64_t)std::floor(fpr[f] * (double)n_neg);
+    }
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    p.pos = pos;
+    p.n_pos = n_pos;
+    p.neg = neg;
+    p.n_neg = n_neg;
+    p.n_fpr = n_fpr;
+    p.u2 = reinterpret_cast<unsigned long long *>(u2);
+    p.thr = thr;
+    p.tp = reinterpret_cast<unsigned long long *>(tp);
+    KernelTimer timer(ctx);
+    cudaError_t e = launch_roc(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "ROC kernels");
+    timer.stop();
+    return GPFC_OK;
+}
+
 int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offsets, const double *times,
                         const float *flux, int64_t n_total, const int64_t *grid_offsets, const double *periods,
                         int64_t n_periods_total, const double *t0s, int32_t nbins, int scorer,

@@ -205,4 +205,100 @@ cudaError_t launch_peaks(const PeakParams &p, int num_sms, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ ROC
+
+// Detection statistics of one detector over labelled scores (Sec. 3.2: ROC curves of stars
+// scored by their best trial period). Every quantity is a count over pairs of scores, so it
+// is exact and independent of the order of the atomics. A NaN score ranks below every
+// number. Cost: n_neg^2 + n_pos * n_neg comparisons (10^8 for 10^4 of each).
+constexpr int kRocThreads = 256;
+constexpr int kRocTile = 2048;
+
+__device__ __forceinline__ float roc_key(float v) { return v != v ? -INFINITY : v; }
+
+__global__ void roc_init_kernel(RocParams p)
+{
+    const int t = threadIdx.x;
+    if (t == 0) *p.u2 = 0ull;
+    if (t < p.n_fpr) {
+        p.tp[t] = 0ull;
+        p.thr[t] = -INFINITY;  // the rule's value when k >= n_neg
+    }
+}
+
+// thr[f] = the (k_f + 1)-th largest negative: negative j is it iff #{neg > neg_j} <= k_f <
+// #{neg >= neg_j} (every such j holds the same value).
+__global__ void __launch_bounds__(kRocThreads) roc_threshold_kernel(RocParams p)
+{
+    __shared__ float tile[kRocTile];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float v = j < p.n_neg ? roc_key(p.neg[j]) : 0.f;
+    int64_t g = 0, e = 0;
+    for (int64_t t0 = 0; t0 < p.n_neg; t0 += kRocTile) {
+        const int nt = (int)min((int64_t)kRocTile, p.n_neg - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[i] = roc_key(p.neg[t0 + i]);
+        __syncthreads();
+        for (int i = 0; i < nt; ++i) {
+            const float u = tile[i];
+            g += u > v;
+            e += u >= v;
+        }
+    }
+    if (j < p.n_neg)
+        for (int f = 0; f < p.n_fpr; ++f)
+            if (g <= p.k[f] && p.k[f] < e) p.thr[f] = v;
+}
+
+__device__ __forceinline__ unsigned long long roc_block_sum(unsigned long long v, unsigned long long *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0ull;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kRocThreads / 32; ++w) t += red[w];
+    return t;
+}
+
+// u2 += 2 #{pos_i > neg_j} + #{pos_i == neg_j}; tp[f] += [pos_i > thr_f]
+__global__ void __launch_bounds__(kRocThreads) roc_count_kernel(RocParams p)
+{
+    __shared__ float tile[kRocTile];
+    __shared__ unsigned long long red[kRocThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < p.n_pos;
+    const float v = live ? roc_key(p.pos[i]) : 0.f;
+    unsigned long long c = 0ull;
+    for (int64_t t0 = 0; t0 < p.n_neg; t0 += kRocTile) {
+        const int nt = (int)min((int64_t)kRocTile, p.n_neg - t0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) tile[k] = roc_key(p.neg[t0 + k]);
+        __syncthreads();
+        if (live)
+            for (int k = 0; k < nt; ++k) {
+                const float u = tile[k];
+                c += (v > u ? 2ull : 0ull) + (v == u ? 1ull : 0ull);
+            }
+    }
+    const unsigned long long s = roc_block_sum(c, red);
+    if (threadIdx.x == 0 && s) atomicAdd(p.u2, s);
+    for (int f = 0; f < p.n_fpr; ++f) {
+        const unsigned long long d = roc_block_sum(live && v > p.thr[f] ? 1ull : 0ull, red);
+        if (threadIdx.x == 0 && d) atomicAdd(&p.tp[f], d);
+    }
+}
+
+cudaError_t launch_roc(const RocParams &p, int num_sms, cudaStream_t st)
+{
+    (void)num_sms;
+    roc_init_kernel<<<1, 32, 0, st>>>(p);
+    if (p.n_fpr > 0)
+        roc_threshold_kernel<<<(int)((p.n_neg + kRocThreads - 1) / kRocThreads), kRocThreads, 0, st>>>(p);
+    roc_count_kernel<<<(int)((p.n_pos + kRocThreads - 1) / kRocThreads), kRocThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace gpfc

@@ -41,4 +41,20 @@ struct PeakParams {
 
 cudaError_t launch_peaks(const PeakParams &p, int num_sms, cudaStream_t st);
 
+// Detection statistics of a detector on labelled scores (gpfc_roc).
+constexpr int kRocMaxFpr = 16;
+struct RocParams {
+    const float *pos;
+    int64_t n_pos;
+    const float *neg;
+    int64_t n_neg;
+    int n_fpr;
+    int64_t k[kRocMaxFpr];        // floor(fpr * n_neg) of each requested rate
+    unsigned long long *u2;       // [1]
+    float *thr;                   // [n_fpr]
+    unsigned long long *tp;       // [n_fpr]
+};
+
+cudaError_t launch_roc(const RocParams &p, int num_sms, cudaStream_t st);
+
 }  // namespace gpfc

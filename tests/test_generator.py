@@ -67,3 +67,32 @@ def test_paper_vector_recipe():
         assert abs(np.sum(shape >= 0.5) / nb - q) <= 1.0 / nb + 1e-12
         noise = v - 1.0 + d * shape
         assert abs(np.std(noise) / sb - 1.0) < 0.2
+
+
+def test_detection_stars_recipe():
+    """Labelled stars: odd stars carry one box whose depth gives the target SNR of Eq. 2
+    over the star's own samples; even stars are noise only; the set is reproducible."""
+    import lcsynth
+    d = lcsynth.detection_stars(40, seed=5, n_cad=2048, sigma=(2e-4, 2e-4), snr=(10.0, 10.0))
+    assert list(d.label[:4]) == [0, 1, 0, 1] and d.lc_offsets[-1] == len(d.times) == len(d.flux)
+    lens = np.diff(d.lc_offsets)
+    assert lens.min() > 2048 - 2 * 5 / lcsynth.CADENCE_D - 1 and lens.max() <= 2048
+    for s in range(40):
+        t = d.times[d.lc_offsets[s]:d.lc_offsets[s + 1]]
+        fl = d.flux[d.lc_offsets[s]:d.lc_offsets[s + 1]].astype(np.float64)
+        assert np.all(np.diff(t) > 0)
+        if d.label[s] == 0:
+            assert np.isnan(d.period[s]) and abs(np.mean(fl) - 1) < 5 * 2e-4 / np.sqrt(len(fl)) + 1e-7
+    d2 = lcsynth.detection_stars(40, seed=5, n_cad=2048, sigma=(2e-4, 2e-4), snr=(10.0, 10.0))
+    assert np.array_equal(d.flux, d2.flux) and np.array_equal(d.times, d2.times)
+    # in-transit samples sit lower by the Eq. 2 depth for SNR 10 (within 3 sigma of their mean)
+    for s in range(1, 40, 2):
+        t = d.times[d.lc_offsets[s]:d.lc_offsets[s + 1]]
+        fl = d.flux[d.lc_offsets[s]:d.lc_offsets[s + 1]].astype(np.float64)
+        P, e, w = d.period[s], d.epoch[s], d.duration[s]
+        intr = np.abs(np.mod(t - e + P / 2, P) - P / 2) < w / 2
+        n_in = intr.sum()
+        assert abs(d.depth[s] - 10 * 2e-4 / np.sqrt(len(t) * w / P)) < 1e-15
+        if n_in > 0:
+            measured = 1.0 - fl[intr].mean()
+            assert abs(measured - d.depth[s]) < 3 * 2e-4 / np.sqrt(n_in) + 1e-6, (s, measured, d.depth[s])
