@@ -358,3 +358,6 @@ def roc(scores_pos, scores_neg, fprs=()):
     tp = np.asarray(tp, np.int64)
     return {"u2": u2, "auc": u2 / (2.0 * len(p) * len(n)), "thr": np.asarray(thr, np.float64), "tp": tp,
             "tpr": tp / float(len(p))}
+
+
+from .preprocess import bspline_design, detrend, knot_vector, segments  # noqa: E402  (pre-processing, Sec. 2.2)
