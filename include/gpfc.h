@@ -441,6 +441,44 @@ int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t
                const int64_t *grid_offsets, int64_t n_periods, double k_sigma, int32_t min_width,
                double harmonic_tol, int32_t max_peaks, gpfc_star_summary *summary, gpfc_peak *peaks);
 
+/* ------------------------------------------------------------------ pre-processing
+ * Detrending of a raw light curve before the fold (Sec. 2.2, Fig. 3): the light curve is
+ * cut into segments wherever two adjacent samples are more than time_gap apart in time or
+ * differ in flux by more than flux_gap_sigma times the flux's population standard
+ * deviation; each segment is fitted by a least-squares cubic spline (clamped end knots,
+ * interior knots `spacing` days apart) with known transits masked and outliers beyond
+ * clip_sigma times the RMS residual removed iteratively (a removed point can return; up to
+ * max_iter fits); the spacing is chosen per segment from `spacings` by the smallest
+ * BIC = n ln(RSS / n) + p ln n; the segment is divided by its fit and its first and last
+ * `edge` samples are dropped; the segments are stitched in time order. The paper names the
+ * steps, not the spline or the criterion: these forms are this library's reading, and the
+ * normal equations carry a tiny second-difference penalty on the spline coefficients
+ * (ridge times trace(B^T B) / p) so that a knot interval emptied by clipping or masking
+ * stays solvable. Fields left at 0 take the defaults. */
+typedef struct {
+    double time_gap;        /* days; default 30 x 0.020428 (30 Kepler cadences) */
+    double flux_gap_sigma;  /* default 5 */
+    double clip_sigma;      /* default 3 */
+    double ridge;           /* default 1e-9 */
+    int32_t edge;           /* samples dropped at each end of a segment; default 30 (set -1 for 0) */
+    int32_t max_iter;       /* fits per candidate spacing; default 10 */
+    int32_t n_spacings;     /* 0..8; default 5: 0.5, 1, 1.5, 2, 3 days */
+    int32_t reserved;
+    double spacings[8];     /* days, each > 0 */
+} gpfc_detrend_params;
+
+/*  - times [n] float64 (strictly increasing), flux [n] float32: device; 1 <= n <= 2^24.
+ *  - mask [n] uint8 (device) or NULL: nonzero = a known transit, never used in a fit (its
+ *    samples are still divided by the fit and returned).
+ *  - times_out [n] float64, flux_out [n] float32 (flux / fit), segment_out [n] int32 (the
+ *    sample's segment index, or NULL): device, caller-owned; the first *n_out entries are
+ *    written. n_out [1] int64: device.
+ * Everything runs in FP64 on the device; reductions run in a fixed order, so the result
+ * does not depend on scheduling. Returns GPFC_OK, GPFC_EINVAL, GPFC_ENOMEM or GPFC_ECUDA. */
+int gpfc_detrend(gpfc_ctx *ctx, const double *times, const float *flux, const uint8_t *mask, int64_t n,
+                 const gpfc_detrend_params *params, double *times_out, float *flux_out,
+                 int32_t *segment_out, int64_t *n_out);
+
 /* ------------------------------------------------------------------ detection statistics
  * ROC statistics of a detector on labelled scores: the paper compares detectors by ROC
  * curves of stars, each star scored by its best trial period (Sec. 3.2, Figs. 10-13).

@@ -21,7 +21,7 @@ from . import _build
 __all__ = [
     "GpfcError", "Context", "load_library", "library_path",
     "gpfc_fold", "gpfc_score_box", "gpfc_score_cnn", "gpfc_best_period", "gpfc_search",
-    "gpfc_best_period_noalloc", "gpfc_probe_smem_rmw", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_roc", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
+    "gpfc_best_period_noalloc", "gpfc_probe_smem_rmw", "gpfc_search_batched", "gpfc_fold_equal_count", "gpfc_peaks", "peaks_to_numpy", "gpfc_roc", "gpfc_detrend", "gpfc_synth_vectors", "gpfc_autotune", "FoldConfig",
     "SCORER_BOX", "SCORER_CNN",
 ]
 
@@ -507,6 +507,41 @@ def gpfc_peaks(ctx: Context, score, periods, grid_offsets=None, k_sigma: float =
                                   float(k_sigma), int(min_width), float(harmonic_tol), int(max_peaks),
                                   _ptr(summary), _ptr(peaks) if max_peaks > 0 else None))
     return summary, peaks
+
+
+class DetrendParams(ctypes.Structure):
+    _fields_ = [("time_gap", ctypes.c_double), ("flux_gap_sigma", ctypes.c_double), ("clip_sigma", ctypes.c_double),
+                ("ridge", ctypes.c_double), ("edge", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("n_spacings", ctypes.c_int32), ("reserved", ctypes.c_int32), ("spacings", ctypes.c_double * 8)]
+
+
+def gpfc_detrend(ctx: Context, times, flux, mask=None, spacings=(), edge: int = 30, **kw):
+    """Pre-processing of Sec. 2.2 (see include/gpfc.h): returns device tensors (times f64,
+    detrended flux f32, segment index i32), each of the output length."""
+    L = ctx.lib
+    if not getattr(L, "_gpfc_detrend_bound", False):
+        L.gpfc_detrend.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(DetrendParams), _vp, _vp, _vp,
+                                   _vp]
+        L._gpfc_detrend_bound = True
+    dev = ctx.device
+    n = times.numel()
+    _need(times, torch.float64, dev, "times")
+    _need(flux, torch.float32, dev, "flux", n)
+    if mask is not None:
+        _need(mask, torch.uint8, dev, "mask", n)
+    prm = DetrendParams(**kw)
+    prm.edge = edge if edge > 0 else -1
+    prm.n_spacings = len(spacings)
+    for i, v in enumerate(spacings):
+        prm.spacings[i] = float(v)
+    t_out = torch.empty(n, dtype=torch.float64, device=dev)
+    f_out = torch.empty(n, dtype=torch.float32, device=dev)
+    s_out = torch.empty(n, dtype=torch.int32, device=dev)
+    n_out = torch.empty(1, dtype=torch.int64, device=dev)
+    ctx._check(L.gpfc_detrend(ctx.handle, _ptr(times), _ptr(flux), _ptr(mask), n, ctypes.byref(prm), _ptr(t_out),
+                              _ptr(f_out), _ptr(s_out), _ptr(n_out)))
+    k = int(n_out.item())
+    return t_out[:k], f_out[:k], s_out[:k]
 
 
 def gpfc_roc(ctx: Context, pos, neg, fprs=()):

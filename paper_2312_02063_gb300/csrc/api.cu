@@ -17,6 +17,7 @@
 #include "gpfc_synth.h"
 #include "gpfc_twotier.h"
 #include "gpfc_decide.h"
+#include "gpfc_detrend.h"
 
 using namespace gpfc;
 
@@ -1851,6 +1852,79 @@ int gpfc_peaks(gpfc_ctx *ctx, const float *score, const double *periods, int32_t
     KernelTimer timer(ctx);
     cudaError_t e = launch_peaks(p, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "decision kernel");
+    timer.stop();
+    return GPFC_OK;
+}
+
+int gpfc_detrend(gpfc_ctx *ctx, const double *times, const float *flux, const uint8_t *mask, int64_t n,
+                 const gpfc_detrend_params *params, double *times_out, float *flux_out, int32_t *segment_out,
+                 int64_t *n_out)
+{
+    if (!ctx) return GPFC_EINVAL;
+    if (!times || !flux || !times_out || !flux_out || !n_out) return set_err(ctx, GPFC_EINVAL, "NULL argument");
+    if (n < 1 || n > ((int64_t)1 << 24)) return set_err(ctx, GPFC_EINVAL, "n = %lld outside [1, 2^24]", (long long)n);
+    DetrendParams p{};
+    gpfc_detrend_params q{};
+    if (params) q = *params;
+    p.time_gap = q.time_gap > 0.0 ? q.time_gap : 30.0 * 0.020428;
+    p.flux_gap_sigma = q.flux_gap_sigma > 0.0 ? q.flux_gap_sigma : 5.0;
+    p.clip_sigma = q.clip_sigma > 0.0 ? q.clip_sigma : 3.0;
+    p.ridge = q.ridge > 0.0 ? q.ridge : 1e-9;
+    p.edge = q.edge > 0 ? q.edge : (q.edge < 0 ? 0 : 30);
+    p.max_iter = q.max_iter > 0 ? q.max_iter : 10;
+    if (q.n_spacings < 0 || q.n_spacings > kDetrendMaxSpacings)
+        return set_err(ctx, GPFC_EINVAL, "n_spacings must be 0..%d", kDetrendMaxSpacings);
+    if (q.n_spacings == 0) {
+        const double d[5] = {0.5, 1.0, 1.5, 2.0, 3.0};
+        p.n_sp = 5;
+        for (int i = 0; i < 5; ++i) p.sp[i] = d[i];
+    } else {
+        p.n_sp = q.n_spacings;
+        for (int i = 0; i < p.n_sp; ++i) {
+            if (!(q.spacings[i] > 0.0 && q.spacings[i] < INFINITY))
+                return set_err(ctx, GPFC_EINVAL, "spacings[%d] must be positive and finite", i);
+            p.sp[i] = q.spacings[i];
+        }
+    }
+    cudaSetDevice(ctx->device);
+    int rc = take_latched(ctx);
+    if (rc) return rc;
+    const int G = (int)std::min<int64_t>(4 * (int64_t)ctx->num_sms, std::max<int64_t>(1, (n + 2047) / 2048));
+    auto carve = [&](void *base) {
+        Carver c(base);
+        p.partial = c.take<double>(2 * G);
+        p.blk_count = c.take<int64_t>(G);
+        p.blk_off = c.take<int64_t>(G + 1);
+        p.n_seg = c.take<int64_t>(1);
+        p.seg_start = c.take<int64_t>(n + 1);
+        p.seg_keep = c.take<int64_t>(n);
+        p.seg_off = c.take<int64_t>(n);
+        p.G4 = c.take<double>(4 * n);
+        p.LB = c.take<double>(4 * n);
+        p.rhs = c.take<double>(n);
+        p.coef = c.take<double>(n);
+        p.trend = c.take<double>(n);
+        p.best = c.take<double>(n);
+        p.used = c.take<uint8_t>(n);
+        p.used2 = c.take<uint8_t>(n);
+        p.det = c.take<float>(n);
+        return c.off + 256;
+    };
+    rc = ensure_ws(ctx, carve(nullptr));
+    if (rc) return rc;
+    carve(ctx->ws);
+    p.t = times;
+    p.f = flux;
+    p.mask = mask;
+    p.n = n;
+    p.blocks = G;
+    p.t_out = times_out;
+    p.f_out = flux_out;
+    p.seg_out = segment_out;
+    p.n_out = n_out;
+    KernelTimer timer(ctx);
+    cudaError_t e = launch_detrend(p, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "pre-processing kernels");
     timer.stop();
     return GPFC_OK;
 }

@@ -102,6 +102,13 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert [int(v) for v in out[6:12]] == [g.BOX_AUTO, g.BOX_EPILOGUE, g.BOX_WARP, g.BOX_FUSED, g.SCORER_BOX,
                                            g.SCORER_CNN]
     assert int(out[4]) == g.STAR_SUMMARY_DTYPE.itemsize
+    src2 = tmp_path / "layout2.c"
+    src2.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gpfc.h"\nint main(void) { printf("%zu %zu\\n", '
+                    'sizeof(gpfc_detrend_params), offsetof(gpfc_detrend_params, spacings)); return 0; }\n')
+    exe2 = tmp_path / "layout2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src2), "-o", str(exe2)], check=True)
+    o2 = subprocess.run([str(exe2)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(o2[0]) == ctypes.sizeof(g.DetrendParams) and int(o2[1]) == g.DetrendParams.spacings.offset
     assert int(out[5]) == g.PEAK_DTYPE.itemsize
 
 
@@ -146,3 +153,9 @@ def test_smem_probe_rejects_bad_arguments_without_gpu():
     assert f(8, 48, 16, 1, 100, None, None, None) == -1      # not a power of two
     assert f(8, 32, 0, 1, 100, None, None, None) == -1       # no warps
     assert f(4, 32, 16, 1, 0, None, None, None) == -1        # no iterations
+
+
+def test_detrend_rejects_bad_arguments_without_gpu():
+    import paper_2312_02063_gb300 as g
+    lib = g.load_library()
+    assert lib.gpfc_detrend(None, None, None, None, 10, None, None, None, None, None) == -1
