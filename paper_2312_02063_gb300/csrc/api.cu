@@ -1668,12 +1668,12 @@ int gpfc_cnn_backward(gpfc_ctx *ctx, const float *dlogit, int64_t batch, const g
     int rc = take_latched(ctx);
     if (rc) return rc;
     const int nblk = (int)std::min<int64_t>(batch, (int64_t)ctx->num_sms * 2);
-    rc = ensure_ws(ctx, cnn_backward_ws_bytes(batch, nblk));
+    rc = ensure_ws(ctx, cnn_backward_ws_bytes(batch, nblk, ctx->num_sms));
     if (rc) return rc;
     const CnnGrads g{gr->conv1_w, gr->conv1_b, gr->conv2_w, gr->conv2_b, gr->conv3_w,
                      gr->conv3_b, gr->fc1_w,   gr->fc1_b,   gr->fc2_w,   gr->fc2_b};
     cudaError_t e = launch_cnn_backward(cnn_src(wt), static_cast<const uint8_t *>(saved), batch, dlogit, g, ctx->ws,
-                                        nblk, ctx->stream);
+                                        nblk, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "CNN backward kernels");
     return GPFC_OK;
 }

@@ -1,16 +1,21 @@
 // cnn_train.cu -- backward pass, loss and Adam update of the CNN scorer (sm_103a).
 //
 // The forward pass for training is the tensor-core forward of cnn.cu run with its
-// activation saves switched on (FP32 pre-activations, BF16 pooled outputs, the fc1 operand
+// activation saves switched on (FP32 pre-activations, pooled outputs, the fc1 operand
 // tiles and fc1's FP32 pre-activations), so the backward takes the ReLU and max-pool
-// decisions the forward took. The backward pass runs on CUDA cores in FP32
-// from those saved values and from the BF16-rounded weights the forward used:
-//   fc2/fc1 head (per profile), dW(fc1) and dh3 as tiled FP32 GEMMs,
-//   ReLU + max-pool backward (the gradient goes to the first maximum of each pair),
-//   conv weight and input gradients per layer (circular, padding 2).
-// Every weight gradient is reduced deterministically: per-block partial sums, then a
-// fixed-order sum over the blocks. Loss: binary cross-entropy with logits (mean).
-// Adam (Kingma & Ba) updates FP32 master weights in place.
+// decisions the forward took. The backward pass:
+//   fc2/fc1 head (per profile, CUDA cores);
+//   dW(fc1) = dZ1^T h3 and dh3 = dZ1 W1 as BF16 tensor-core GEMMs (tcgemm.cu);
+//   ReLU + max-pool backward (the gradient goes to the first maximum of each pair);
+//   conv3 and conv2: weight gradients dW[co][ci,tap] = sum over (profile, position) of
+//   da[co][l] h[ci][l + tap - 2] and input gradients dh[(profile, position)][ci] = sum over
+//   (co, tap) of da[co][m - tap + 2] W[co][ci][tap] (circular), as BF16 tensor-core GEMMs
+//   on operands packed from the saved activations (im2col in the operand layout);
+//   conv1's 80 weights and every bias by CUDA-core reductions.
+// GEMM operands are BF16 (round to nearest even), accumulation FP32. Every gradient is
+// reduced deterministically: split-K partials and per-block partials are added in a fixed
+// order. Loss: binary cross-entropy with logits (mean). Adam (Kingma & Ba) updates FP32
+// master weights in place.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -18,6 +23,7 @@
 
 #include "gpfc_cnn.h"
 #include "gpfc_common.cuh"
+#include "gpfc_tcgemm.h"
 
 namespace gpfc {
 
@@ -78,59 +84,9 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const float *z1, const fl
     if (j == 0) pp[512] = gb2;
 }
 
-// ------------------------------------------------------------------ FP32 tiled GEMM
-
-// C[m][n] = sum_k A(m, k) B(k, n); 64 x 64 tile per block, 256 threads, 4 x 4 per thread.
-template <class LA, class LB, class ST>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, LA la, LB lb, ST st)
-{
-    constexpr int BK = 16;
-    __shared__ float As[BK][64 + 4];
-    __shared__ float Bs[BK][64 + 4];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = tid + 256 * i, kk = e >> 6, mm = e & 63;
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? la(m, k) : 0.f;
-            const int n = n0 + mm;
-            Bs[kk][mm] = (n < N && k < K) ? lb(k, n) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[kk][ty * 4 + i];
-                b[i] = Bs[kk][tx * 4 + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a[i], b[jj], acc[i][jj]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + jj;
-            if (m < M && n < N) st(m, n, acc[i][jj]);
-        }
-}
-
 // device fc1 feature fd = position * 64 + channel <-> PyTorch feature channel * 32 + position
 __host__ __device__ __forceinline__ int pt_feature(int fd) { return (fd & 63) * 32 + (fd >> 6); }
 
-struct LoadDZ1T {  // A(m = j, k = profile) = dZ1[k][j]
-    const float *dZ1;
-    __device__ float operator()(int m, int k) const { return dZ1[(size_t)k * 256 + m]; }
-};
 struct LoadH3 {  // B(k = profile, n = fd) from the fc1 operand tiles: high + low BF16 terms
     const uint8_t *h3t;
     __device__ float operator()(int k, int fd) const
@@ -143,21 +99,52 @@ struct LoadH3 {  // B(k = profile, n = fd) from the fc1 operand tiles: high + lo
                bf2f(*reinterpret_cast<const uint16_t *>(h3t + off + lo));
     }
 };
-struct StoreDW1 {  // grad of fc1.w in PyTorch order
-    float *g;
-    __device__ void operator()(int j, int fd, float v) const { g[(size_t)j * 2048 + pt_feature(fd)] = v; }
-};
-struct LoadDZ1 {  // A(m = profile, k = j)
+// ------------------------------------------------------------------ GEMM operand loaders
+// (element (row, k) of a packed operand; the packer rounds to BF16)
+
+struct LdDZ1T {  // dW(fc1): A(j, profile)
     const float *dZ1;
-    __device__ float operator()(int m, int k) const { return dZ1[(size_t)m * 256 + k]; }
+    __device__ float operator()(int64_t j, int64_t k) const { return dZ1[k * 256 + j]; }
 };
-struct LoadW1 {  // B(k = j, n = fd) = BF16-rounded fc1.w[j][pt_feature(fd)]
+struct LdH3T {  // dW(fc1): B(feature fd, profile) = h3 (high + low terms)
+    const uint8_t *h3t;
+    __device__ float operator()(int64_t fd, int64_t k) const { return LoadH3{h3t}((int)k, (int)fd); }
+};
+struct LdDZ1 {  // dh3: A(profile, j)
+    const float *dZ1;
+    __device__ float operator()(int64_t k, int64_t j) const { return dZ1[k * 256 + j]; }
+};
+struct LdW1T {  // dh3: B(fd, j) = fc1.w[j][pt_feature(fd)]
     const float *w;
-    __device__ float operator()(int k, int fd) const { return rbf(w[(size_t)k * 2048 + pt_feature(fd)]); }
+    __device__ float operator()(int64_t fd, int64_t j) const { return w[j * 2048 + pt_feature((int)fd)]; }
 };
-struct StoreDH3 {
-    float *d;
-    __device__ void operator()(int m, int fd, float v) const { d[(size_t)m * 2048 + fd] = v; }
+template <int COUT, int L>
+struct LdDa {  // conv weight gradient: A(co, (profile b, position l))
+    const float *da;
+    __device__ float operator()(int64_t co, int64_t k) const { return da[((k / L) * COUT + co) * L + (k % L)]; }
+};
+template <int CIN, int L>
+struct LdHim {  // conv weight gradient: B((ci, tap), (b, l)) = h[b][ci][(l + tap - 2) mod L]
+    const uint16_t *h;
+    __device__ float operator()(int64_t n, int64_t k) const
+    {
+        const int ci = (int)(n / 5), tap = (int)(n % 5), l = (int)(k % L);
+        return bf2f(h[((k / L) * CIN + ci) * L + ((l + tap - 2 + L) % L)]);
+    }
+};
+template <int COUT, int L>
+struct LdDaShift {  // conv input gradient: A((b, m), (co, tap)) = da[b][co][(m - tap + 2) mod L]
+    const float *da;
+    __device__ float operator()(int64_t r, int64_t k) const
+    {
+        const int m = (int)(r % L), co = (int)(k / 5), tap = (int)(k % 5);
+        return da[((r / L) * COUT + co) * L + ((m - tap + 2 + L) % L)];
+    }
+};
+template <int CIN>
+struct LdWT {  // conv input gradient: B(ci, (co, tap)) = W[co][ci][tap]
+    const float *W;
+    __device__ float operator()(int64_t ci, int64_t k) const { return W[((k / 5) * CIN + ci) * 5 + (k % 5)]; }
 };
 
 // ------------------------------------------------------------------ ReLU + max-pool backward
@@ -305,21 +292,7 @@ CnnSaved CnnSaved::layout(int64_t B)
     return s;
 }
 
-size_t cnn_backward_ws_bytes(int64_t B, int nblk)
-{
-    size_t o = 0;
-    auto take = [&](size_t bytes) { o = ((o + 255) & ~(size_t)255) + bytes; };
-    take((size_t)B * 256 * 4);         // dZ1
-    take((size_t)B * 2048 * 4);        // dH3
-    take((size_t)B * 64 * 64 * 4);     // da3
-    take((size_t)B * 32 * 64 * 4);     // dh2
-    take((size_t)B * 32 * 128 * 4);    // da2
-    take((size_t)B * 16 * 128 * 4);    // dh1
-    take((size_t)B * 16 * 256 * 4);    // da1
-    take((size_t)nblk * (64 * 32 * 5 + 64) * 4);  // conv partials (largest layer)
-    take((size_t)nblk * 513 * 4);      // head partials
-    return o + 256;
-}
+// ------------------------------------------------------------------ backward launches
 
 template <int CIN, int COUT, int L, bool DGRAD, bool XF32>
 static cudaError_t run_conv_bwd(const float *da, const void *hin, const float *W, float *dh, float *part,
@@ -336,8 +309,139 @@ static cudaError_t run_conv_bwd(const float *da, const void *hin, const float *W
     return cudaGetLastError();
 }
 
+// per-block partial sums over the profiles of da[b][c][l] for each channel c (bias gradients)
+template <int C, int L>
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float *da, int64_t B, float *part)
+{
+    __shared__ float acc[C];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
+    __syncthreads();
+    for (int64_t k = blockIdx.x; k < B; k += gridDim.x) {
+        for (int c = threadIdx.x >> 5; c < C; c += blockDim.x >> 5) {
+            float s = 0.f;
+            for (int l = threadIdx.x & 31; l < L; l += 32) s += da[(k * C + c) * L + l];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if ((threadIdx.x & 31) == 0) acc[c] += s;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) part[(size_t)blockIdx.x * C + c] = acc[c];
+}
+
+// out(m, n) = sum over splits s (in order) of part[s][m][n], stored by st(m, n, value)
+template <class ST>
+__global__ void reduce_splits_kernel(const float *part, int splits, int64_t rows, int64_t cols, ST st)
+{
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int s = 0; s < splits; ++s) v += (double)part[(size_t)s * total + e];
+        st(e / cols, e % cols, (float)v);
+    }
+}
+struct StWf1 {  // dW(fc1)[j][fd] -> PyTorch order
+    float *g;
+    __device__ void operator()(int64_t j, int64_t fd, float v) const { g[j * 2048 + pt_feature((int)fd)] = v; }
+};
+struct StRowMajor {
+    float *g;
+    int64_t ld;
+    __device__ void operator()(int64_t r, int64_t c, float v) const { g[r * ld + c] = v; }
+};
+template <int C, int L>
+struct StDh {  // input gradient [(b, m)][ci] -> [b][ci][m]
+    float *dh;
+    __device__ void operator()(int64_t r, int64_t ci, float v) const { dh[((r / L) * C + ci) * L + (r % L)] = v; }
+};
+
+// The tensor-core GEMMs of one backward pass: (rows of A and of the output, rows of B = N,
+// K, N tile, split-K count). Operands and partials share three workspace buffers.
+struct BwdGemmShape {
+    int64_t M, N, K;
+    int bn, splits;
+};
+
+static BwdGemmShape bwd_shape(int which, int64_t B, int num_sms)
+{
+    BwdGemmShape s{};
+    switch (which) {
+    case 0: s = {256, 2048, B, 256, 1}; break;           // dW(fc1)
+    case 1: s = {B, 2048, 256, 256, 1}; break;           // dh3
+    case 2: s = {64, 160, B * 64, 160, 1}; break;        // dW(conv3)
+    case 3: s = {B * 64, 32, 320, 32, 1}; break;         // dh2
+    case 4: s = {32, 80, B * 128, 80, 1}; break;         // dW(conv2)
+    default: s = {B * 128, 16, 160, 16, 1}; break;       // dh1
+    }
+    const int64_t mt = (s.M + 127) / 128, nt = (s.N + s.bn - 1) / s.bn, kch = (s.K + 63) / 64;
+    if (mt * nt < num_sms) s.splits = (int)std::min<int64_t>(kch, (num_sms + mt * nt - 1) / (mt * nt));
+    return s;
+}
+
+static void bwd_ws_sizes(int64_t B, int num_sms, size_t &a, size_t &b, size_t &part)
+{
+    a = b = part = 0;
+    for (int w = 0; w < 6; ++w) {
+        const BwdGemmShape s = bwd_shape(w, B, num_sms);
+        a = std::max(a, packed_bytes(s.M, 128, s.K));
+        b = std::max(b, packed_bytes(s.N, s.bn, s.K));
+        part = std::max(part, (size_t)s.splits * (size_t)s.M * (size_t)((s.N + s.bn - 1) / s.bn * s.bn) * 4);
+    }
+}
+
+size_t cnn_backward_ws_bytes(int64_t B, int nblk, int num_sms)
+{
+    size_t o = 0;
+    auto take = [&](size_t bytes) { o = ((o + 255) & ~(size_t)255) + bytes; };
+    take((size_t)B * 256 * 4);         // dZ1
+    take((size_t)B * 2048 * 4);        // dH3
+    take((size_t)B * 64 * 64 * 4);     // da3
+    take((size_t)B * 32 * 64 * 4);     // dh2
+    take((size_t)B * 32 * 128 * 4);    // da2
+    take((size_t)B * 16 * 128 * 4);    // dh1
+    take((size_t)B * 16 * 256 * 4);    // da1
+    take((size_t)nblk * (16 * 5 + 16) * 4);  // conv1 weight/bias partials
+    take((size_t)nblk * 64 * 4);       // bias partials
+    take((size_t)nblk * 513 * 4);      // head partials
+    size_t a, b, part;
+    bwd_ws_sizes(B, num_sms, a, b, part);
+    take(a);
+    take(b);
+    take(part);
+    return o + 256;
+}
+
+// pack A and B of GEMM `which`, run it and hand its partials to `store`
+template <class LA, class LB, class ST>
+static cudaError_t bwd_gemm(int which, int64_t B, int num_sms, LA la, LB lb, ST store, uint8_t *pa, uint8_t *pb,
+                            float *part, cudaStream_t st)
+{
+    const BwdGemmShape s = bwd_shape(which, B, num_sms);
+    const int64_t kch = (s.K + 63) / 64;
+    const int64_t ga = std::min<int64_t>(65535, ((s.M + 127) / 128 * 128 * kch * 8 + 255) / 256);
+    const int64_t gb = std::min<int64_t>(65535, ((s.N + s.bn - 1) / s.bn * s.bn * kch * 8 + 255) / 256);
+    pack_tiles_kernel<<<(int)ga, 256, 0, st>>>(s.M, 128, s.K, la, pa);
+    pack_tiles_kernel<<<(int)gb, 256, 0, st>>>(s.N, s.bn, s.K, lb, pb);
+    TcGemm g{};
+    g.A = pa;
+    g.B = pb;
+    g.mtiles = (s.M + 127) / 128;
+    g.ntiles = (int)((s.N + s.bn - 1) / s.bn);
+    g.kchunks = (int)kch;
+    g.bn = s.bn;
+    g.splits = s.splits;
+    g.rows_out = s.M;
+    g.ldp = (int64_t)g.ntiles * s.bn;
+    g.part = part;
+    cudaError_t e = launch_tcgemm(g, num_sms, st);
+    if (e != cudaSuccess) return e;
+    const int64_t total = s.M * g.ldp;
+    reduce_splits_kernel<<<(int)std::min<int64_t>(4096, (total + 255) / 256), 256, 0, st>>>(part, s.splits, s.M,
+                                                                                              g.ldp, store);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cnn_backward(const CnnSrc &w, const uint8_t *saved, int64_t B, const float *dlogit,
-                                const CnnGrads &g, void *ws, int nblk, cudaStream_t st)
+                                const CnnGrads &g, void *ws, int nblk, int num_sms, cudaStream_t st)
 {
     const CnnSaved S = CnnSaved::layout(B);
     uint8_t *base = static_cast<uint8_t *>(ws);
@@ -355,34 +459,50 @@ cudaError_t launch_cnn_backward(const CnnSrc &w, const uint8_t *saved, int64_t B
     float *da2 = reinterpret_cast<float *>(take((size_t)B * 32 * 128 * 4));
     float *dh1 = reinterpret_cast<float *>(take((size_t)B * 16 * 128 * 4));
     float *da1 = reinterpret_cast<float *>(take((size_t)B * 16 * 256 * 4));
-    float *cpart = reinterpret_cast<float *>(take((size_t)nblk * (64 * 32 * 5 + 64) * 4));
+    float *cpart = reinterpret_cast<float *>(take((size_t)nblk * (16 * 5 + 16) * 4));
+    float *bpart = reinterpret_cast<float *>(take((size_t)nblk * 64 * 4));
     float *hpart = reinterpret_cast<float *>(take((size_t)nblk * 513 * 4));
+    size_t sa, sb, sp;
+    bwd_ws_sizes(B, num_sms, sa, sb, sp);
+    uint8_t *pa = take(sa);
+    uint8_t *pb = take(sb);
+    float *gpart = reinterpret_cast<float *>(take(sp));
+    const int sms = num_sms;
 
     const float *z1 = reinterpret_cast<const float *>(saved + S.z1);
     head_bwd_kernel<<<nblk, 256, 0, st>>>(z1, dlogit, w.wf2, B, dZ1, hpart);
     reduce_parts_kernel<<<1, 256, 0, st>>>(hpart, nblk, 513, 0, 256, g.wf2);
     reduce_parts_kernel<<<1, 256, 0, st>>>(hpart, nblk, 513, 256, 256, g.bf1);
     reduce_parts_kernel<<<1, 32, 0, st>>>(hpart, nblk, 513, 512, 1, g.bf2);
-    {   // dW(fc1)[256][2048] = dZ1^T h3
-        dim3 grid(2048 / 64, 256 / 64);
-        gemm_kernel<<<grid, 256, 0, st>>>(256, 2048, (int)B, LoadDZ1T{dZ1}, LoadH3{saved + S.h3t}, StoreDW1{g.wf1});
-    }
-    {   // dh3[B][2048] = dZ1 W1
-        dim3 grid(2048 / 64, (unsigned)((B + 63) / 64));
-        gemm_kernel<<<grid, 256, 0, st>>>((int)B, 2048, 256, LoadDZ1{dZ1}, LoadW1{w.wf1}, StoreDH3{dH3});
-    }
+    // dW(fc1)[256][2048] = dZ1^T h3; dh3[B][2048] = dZ1 W1
+    cudaError_t e = bwd_gemm(0, B, sms, LdDZ1T{dZ1}, LdH3T{saved + S.h3t}, StWf1{g.wf1}, pa, pb, gpart, st);
+    if (e == cudaSuccess) e = bwd_gemm(1, B, sms, LdDZ1{dZ1}, LdW1T{w.wf1}, StRowMajor{dH3, 2048}, pa, pb, gpart, st);
+    if (e != cudaSuccess) return e;
     const int eb = 256;
     const int egrid = (int)std::min<int64_t>((B * 64 * 32 + eb - 1) / eb, 65535);
     poolrelu_bwd_kernel<64, 64, true><<<egrid, eb, 0, st>>>(reinterpret_cast<const float *>(saved + S.a3), dH3,
                                                               da3, B);
-    cudaError_t e = run_conv_bwd<32, 64, 64, true, false>(da3, saved + S.h2, w.w3, dh2, cpart, B, nblk, g.w3, g.b3, st);
+    // conv3: dW[64][160] and dh2, bias by reduction
+    e = bwd_gemm(2, B, sms, LdDa<64, 64>{da3}, LdHim<32, 64>{reinterpret_cast<const uint16_t *>(saved + S.h2)},
+                 StRowMajor{g.w3, 160}, pa, pb, gpart, st);
+    if (e == cudaSuccess)
+        e = bwd_gemm(3, B, sms, LdDaShift<64, 64>{da3}, LdWT<32>{w.w3}, StDh<32, 64>{dh2}, pa, pb, gpart, st);
     if (e != cudaSuccess) return e;
+    bias_grad_kernel<64, 64><<<nblk, 256, 0, st>>>(da3, B, bpart);
+    reduce_parts_kernel<<<1, 64, 0, st>>>(bpart, nblk, 64, 0, 64, g.b3);
     poolrelu_bwd_kernel<32, 128, false><<<egrid, eb, 0, st>>>(reinterpret_cast<const float *>(saved + S.a2), dh2,
                                                                 da2, B);
-    e = run_conv_bwd<16, 32, 128, true, false>(da2, saved + S.h1, w.w2, dh1, cpart, B, nblk, g.w2, g.b2, st);
+    // conv2: dW[32][80] and dh1, bias by reduction
+    e = bwd_gemm(4, B, sms, LdDa<32, 128>{da2}, LdHim<16, 128>{reinterpret_cast<const uint16_t *>(saved + S.h1)},
+                 StRowMajor{g.w2, 80}, pa, pb, gpart, st);
+    if (e == cudaSuccess)
+        e = bwd_gemm(5, B, sms, LdDaShift<32, 128>{da2}, LdWT<16>{w.w2}, StDh<16, 128>{dh1}, pa, pb, gpart, st);
     if (e != cudaSuccess) return e;
+    bias_grad_kernel<32, 128><<<nblk, 256, 0, st>>>(da2, B, bpart);
+    reduce_parts_kernel<<<1, 64, 0, st>>>(bpart, nblk, 32, 0, 32, g.b2);
     poolrelu_bwd_kernel<16, 256, false><<<egrid, eb, 0, st>>>(reinterpret_cast<const float *>(saved + S.a1), dh1,
                                                                 da1, B);
+    // conv1 (16 x 5 weights) on CUDA cores
     e = run_conv_bwd<1, 16, 256, false, true>(da1, saved + S.x, w.w1, nullptr, cpart, B, nblk, g.w1, g.b1, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -92,9 +92,9 @@ struct CnnGrads {
 };
 
 size_t cnn_saved_bytes(int64_t B);
-size_t cnn_backward_ws_bytes(int64_t B, int nblk);
+size_t cnn_backward_ws_bytes(int64_t B, int nblk, int num_sms);
 cudaError_t launch_cnn_backward(const CnnSrc &w, const uint8_t *saved, int64_t B, const float *dlogit,
-                                const CnnGrads &g, void *ws, int nblk, cudaStream_t st);
+                                const CnnGrads &g, void *ws, int nblk, int num_sms, cudaStream_t st);
 cudaError_t launch_bce(const float *z, const float *y, int64_t n, float *dlogit, float *loss, void *ws,
                        cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
