@@ -36,10 +36,10 @@ NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
 SM_FOLD_UPDATES_PER_CLK = 8           # the pipe model: 128 B/clk / (8 B read + 8 B written)
-# DRAM bytes (read + write) per period of the one-kernel search (fold + box-SNR) of the same
-# light curve, from an ncu capture of a 58,368-period search; the search's traffic grows
-# with the number of periods (ring writes, one light-curve pass per task).
-SEARCH_DRAM_BYTES_PER_PERIOD = (34.224128e6 + 196.570112e6) / 58368  # profiles/fold_kernel_search_kepler62835.md
+# DRAM bytes (read + write) of one whole 250,000-period one-kernel search (fold + box-SNR) of
+# the same light curve in steady state (no cache flush, one ncu pass):
+# profiles/dram_traffic_steady_state_kepler62835.md
+SEARCH_DRAM_BYTES_PER_PERIOD = (219.01e6 + 960.84e6) / 250000
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -253,7 +253,60 @@ def cnn_measurements(g, ctx, lc, periods, t_d, f_d, p_d, flush, stream, args):
                                     "reported separately"}
         if args.star_count > 0:
             out["detection_star"] = star_detection(g, ctx, wt, args)
+    if args.train_time_steps > 0:
+        out["training"] = training_throughput(g, ctx, args, peaks, src)
     return out
+
+
+def training_throughput(g, ctx, args, peaks, src):
+    """Training steps of the C4 recipe (batch 4,096 profiles generated and folded on the GPU
+    from 65,536-sample light curves, tensor-core forward and backward, Adam), timed with CUDA
+    events after warm-up steps; the epoch time is the per-step time times 489 steps
+    (2,000,000 profiles). Counted work per profile: forward 3,056,128 FLOP plus backward
+    twice that (data generation not counted)."""
+    import torch
+    from paper_2312_02063_gb300 import train as tr
+    t = tr.Trainer(ctx, batch=4096, lr=1e-3)
+    for _ in range(3):
+        t.step()
+    ctx.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.train_time_steps):
+        t.step()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / args.train_time_steps
+    # the same steps split: data generation alone, and forward + loss + backward + Adam on one
+    # resident batch
+    f, c, y, _, _ = g.gpfc_synth_profiles(ctx, tr.TRAIN_SEED, 0, 4096)
+    a.record()
+    for i in range(args.train_time_steps):
+        g.gpfc_synth_profiles(ctx, tr.TRAIN_SEED, 4096 * (i + 1), 4096)
+    b.record()
+    b.synchronize()
+    ms_gen = a.elapsed_time(b) / args.train_time_steps
+    a.record()
+    for _ in range(args.train_time_steps):
+        logit, saved = g.gpfc_cnn_forward_train(ctx, f, t.params, c)
+        _, dl = g.gpfc_bce_with_logits(ctx, logit, y)
+        grads = g.gpfc_cnn_backward(ctx, dl, t.params, saved)
+        for n in tr.CNN_PARAM_NAMES:
+            g.gpfc_adam(ctx, t.params[n], grads[n], t.m[n], t.v[n], 10, 1e-3)
+    b.record()
+    b.synchronize()
+    ms_model = a.elapsed_time(b) / args.train_time_steps
+    flop = 3 * 3_056_128.0 * 4096
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    tf = flop / (ms_model * 1e-3) / 1e12
+    return {"ms_per_step": ms, "profiles_per_s": 4096 / (ms * 1e-3), "epoch_s_2M": ms * 1e-3 * (2_000_000 / 4096),
+            "ms_data_generation": ms_gen, "ms_forward_backward_adam": ms_model, "model_tflops": tf,
+            "roofline": {"bound": "tensor", "kernel": "forward + backward + Adam of one resident batch",
+                         "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_basis": f"{src} bf16_tflops_sustained"},
+            "workload": "C4 training steps: 4,096 profiles per step generated and folded on the GPU from "
+                        "65,536-sample light curves, BF16 tensor-core forward and backward, BCE, Adam",
+                        "steps_timed": args.train_time_steps}
 
 
 def star_detection(g, ctx, weights, args):
@@ -547,7 +600,8 @@ def run_gpu(args, rank, world, local_rank):
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                          "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None
                          else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS,
-                         "traffic_basis": "ncu dram__bytes_read+write of a 58,368-period search, scaled by periods",
+                         "traffic_basis": "ncu dram__bytes_read+write of one 250,000-period search in steady "
+                                          "state (no cache flush), scaled by periods",
                          "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
                          "search_ms": kmean,
                          "peak_basis": "measured in this run by gpfc_probe_smem_rmw: lane-private 8-byte "
@@ -591,6 +645,7 @@ def main():
     ap.add_argument("--no-cnn", action="store_true", help="skip the CNN and detection measurements")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--star-count", type=int, default=20000, help="labelled stars of the star-level comparison (0: skip)")
+    ap.add_argument("--train-time-steps", type=int, default=50, help="timed training steps (0: skip)")
     ap.add_argument("--star-densities", type=int, nargs="+", default=[2000, 5000, 10000, 20000])
     ap.add_argument("--cnn-profiles", type=int, default=262_144)
     ap.add_argument("--eval-profiles", type=int, default=40_000)
