@@ -571,7 +571,7 @@ def run_gpu(args, rank, world, local_rank):
         probe = {}
         for key, cfg in (("rmw8_full", (8, 32, 16, 1)), ("rmw8_fold_footprint", (8, 256, 3, 1)),
                          ("rmw4_full", (4, 32, 16, 1))):
-            ups, upc = g.gpfc_probe_smem_rmw(*cfg, iters=20000)
+            ups, upc = g.gpfc_probe_smem_rmw(*cfg, iters=20000, op=0)
             probe[key] = {"gupdates_per_s": ups / 1e9, "updates_per_clk_sm": upc,
                           "config": f"{cfg[0]}-byte words, {cfg[1]} bins x {cfg[2]} warps per SM"}
         peak_gups = probe["rmw8_full"]["gupdates_per_s"]

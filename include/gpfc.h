@@ -540,8 +540,11 @@ int gpfc_set_graph(gpfc_ctx *ctx, int enable);
  * period; this call times a kernel that does only that, with each lane's records laid out
  * [bin][lane] as the fold keeps them, eight distinct bins updated per iteration, and
  * reports the rate.
- *  - word_bytes 8: the fold's record (FP32 sum + 32-bit count, one 64-bit load and store);
- *    4: one 32-bit integer word.
+ *  - word_bytes 8: FP32 sum + 32-bit count packed in 64 bits (op 0: one 64-bit load and
+ *    store per update; op 1: one red.shared.add.u64); 6: FP32 sum word plus a 16-bit
+ *    count, two counts per 32-bit word (op 0: 32-bit and 16-bit loads and stores; op 1:
+ *    red.shared.add.f32 to the sum and red.shared.add.u32 to the paired count); 4: one
+ *    32-bit word (op 0: load and store; op 1: red.shared.add.u32).
  *  - nbins (power of two, 8..4096) words per lane, warps per block (1..32), blocks_per_sm
  *    co-resident blocks per SM (the call checks they fit), iters iterations of 8 updates.
  *  - Runs on the current device and `stream` (a cudaStream_t, NULL = default stream) and
@@ -550,7 +553,7 @@ int gpfc_set_graph(gpfc_ctx *ctx, int enable);
  *    clock cycle (clock64 span of the slowest block). Either may be NULL.
  * Returns GPFC_OK, GPFC_EINVAL (bad sizes, or the blocks do not fit one SM together) or
  * GPFC_ECUDA. */
-int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t nbins, int32_t warps, int32_t blocks_per_sm,
+int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t op, int32_t nbins, int32_t warps, int32_t blocks_per_sm,
                         int64_t iters, void *stream, double *updates_per_s, double *updates_per_clk_sm);
 
 #ifdef __cplusplus

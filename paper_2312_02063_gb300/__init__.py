@@ -132,7 +132,7 @@ def load_library(build_if_missing: bool = True):
         L.gpfc_workspace_size.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_size_t)]
         L.gpfc_probe_smem_rmw.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                          ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int32, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
         _lib = L
         return L
@@ -367,7 +367,7 @@ def gpfc_best_period(ctx: Context, score, best_index=None, best_score=None):
 
 
 def gpfc_probe_smem_rmw(word_bytes: int = 8, nbins: int = 32, warps: int = 16, blocks_per_sm: int = 1,
-                        iters: int = 20000, stream=None):
+                        iters: int = 20000, stream=None, op: int = 0):
     """Measured rate of lane-private shared-memory read-modify-writes (see include/gpfc.h):
     returns (updates per second, updates per SM clock cycle). Runs on the current device."""
     lib = load_library()
@@ -375,7 +375,7 @@ def gpfc_probe_smem_rmw(word_bytes: int = 8, nbins: int = 32, warps: int = 16, b
         raise GpfcError(-3, "no CUDA device: libgpfc runs on the GPU only")
     s = stream if stream is not None else torch.cuda.current_stream()
     ups, upc = ctypes.c_double(), ctypes.c_double()
-    rc = lib.gpfc_probe_smem_rmw(word_bytes, nbins, warps, blocks_per_sm, iters, _vp(s.cuda_stream),
+    rc = lib.gpfc_probe_smem_rmw(word_bytes, op, nbins, warps, blocks_per_sm, iters, _vp(s.cuda_stream),
                                  ctypes.byref(ups), ctypes.byref(upc))
     if rc != 0:
         raise GpfcError(rc, lib.gpfc_strerror(rc).decode())

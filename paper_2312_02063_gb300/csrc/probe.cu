@@ -7,8 +7,7 @@
 // a warp's 32 accesses never conflict beyond the word width), and updates eight distinct
 // bins per iteration (all eight loads issued before the adds and stores, as the fold's
 // regular-cadence loop does). The bin sequence is two integer adds and a mask per update;
-// nothing else competes for issue. The word is either 8 bytes (FP32 sum + 32-bit count,
-// the fold's record) or 4 bytes (one 32-bit integer).
+// nothing else competes for issue. The record kinds are listed below.
 #include <cstdint>
 
 #include "gpfc.h"
@@ -17,27 +16,62 @@
 namespace gpfc {
 namespace {
 
-template <bool W64>
+// Record kinds. LDST8: FP32 sum + 32-bit count packed in 8 bytes, one 64-bit load and
+// store per update (the fold's default record). LDST6: FP32 sum word [bin][lane] plus a
+// 16-bit count, two per 32-bit word [bin/2][lane] (load and store of each). LDST4: one
+// 32-bit word. RED6: the 6-byte record updated by no-return shared reductions
+// (red.shared.add.f32 to the sum, red.shared.add.u32 of 1 << 16 (bin & 1) to the paired
+// count). RED4: red.shared.add.u32 to a 32-bit word. RED8: red.shared.add.u64 to a 64-bit
+// word.
+enum ProbeKind { kLdSt8, kLdSt6, kLdSt4, kRed6, kRed4, kRed8 };
+
+__host__ __device__ constexpr uint32_t probe_bytes_x2(int k)  // twice the bytes per bin
+{
+    return (k == kLdSt8 || k == kRed8) ? 16u : ((k == kLdSt6 || k == kRed6) ? 12u : 8u);
+}
+
+template <int KIND>
 __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *cycles, uint32_t *sink)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr uint32_t kW = W64 ? 8u : 4u;
-    const uint32_t base = smem_u32(sm) + ((uint32_t)warp * (uint32_t)nbins * 32u + (uint32_t)lane) * kW;
+    constexpr bool kSix = KIND == kLdSt6 || KIND == kRed6;
+    constexpr uint32_t kW = kSix ? 4u : probe_bytes_x2(KIND) / 2u;  // bytes of the word addressed per bin
+    const uint32_t wbase = smem_u32(sm) + (uint32_t)warp * (uint32_t)nbins * 32u * probe_bytes_x2(KIND) / 2u;
+    const uint32_t base = wbase + (uint32_t)lane * kW;
+    const uint32_t cbase = wbase + (uint32_t)nbins * 128u + (uint32_t)lane * 4u;  // 6-byte records: counts
     const uint32_t mask = (uint32_t)nbins - 1u;
-    for (int b = 0; b < nbins; ++b) {
-        if (W64) asm volatile("st.shared.v2.u32 [%0], {%1, %1};" ::"r"(base + (uint32_t)b * 32u * kW), "r"(0u));
-        else asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + (uint32_t)b * 32u * kW), "r"(0u));
+    const uint32_t words = kSix ? nbins + nbins / 2 : nbins;
+    for (uint32_t b = 0; b < words; ++b) {
+        if (kW == 8) asm volatile("st.shared.v2.u32 [%0], {%1, %1};" ::"r"(base + b * 256u), "r"(0u));
+        else asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + b * 128u), "r"(0u));
     }
     __syncthreads();
     const long long t0 = clock64();
     uint32_t b = (uint32_t)lane * 7u;
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
-        uint32_t a[8];
+        uint32_t bb[8], a[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = base + ((b + 37u * (uint32_t)u) & mask) * 32u * kW;
-        if (W64) {
+        for (int u = 0; u < 8; ++u) {
+            bb[u] = (b + 37u * (uint32_t)u) & mask;
+            a[u] = base + bb[u] * 32u * kW;
+        }
+        if (KIND == kRed6) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a[u]), "f"(1.0f) : "memory");
+                asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(cbase + (bb[u] >> 1) * 128u),
+                             "r"(1u << ((bb[u] & 1u) << 4)) : "memory");
+            }
+        } else if (KIND == kRed4) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a[u]), "r"(3u) : "memory");
+        } else if (KIND == kRed8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a[u]), "l"(0x0000010000000003ull) : "memory");
+        } else if (KIND == kLdSt8) {
             uint32_t s[8], c[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -46,6 +80,20 @@ __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *
             for (int u = 0; u < 8; ++u) {
                 const float v = __uint_as_float(s[u]) + 1.0f;
                 asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a[u]), "r"(__float_as_uint(v)), "r"(c[u] + 1u));
+            }
+        } else if (KIND == kLdSt6) {
+            uint32_t s[8], c[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(s[u]) : "r"(a[u]));
+                asm volatile("ld.shared.u16 %0, [%1];" : "=r"(c[u]) : "r"(cbase + (bb[u] >> 1) * 128u + (bb[u] & 1u) * 2u));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float v = __uint_as_float(s[u]) + 1.0f;
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(a[u]), "r"(__float_as_uint(v)));
+                asm volatile("st.shared.u16 [%0], %1;" ::"r"(cbase + (bb[u] >> 1) * 128u + (bb[u] & 1u) * 2u),
+                             "h"((unsigned short)(c[u] + 1u)));
             }
         } else {
             uint32_t s[8];
@@ -70,12 +118,13 @@ __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *
 }  // namespace
 }  // namespace gpfc
 
-extern "C" int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t nbins, int32_t warps, int32_t blocks_per_sm,
-                                   int64_t iters, void *stream, double *updates_per_s,
+extern "C" int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t op, int32_t nbins, int32_t warps,
+                                   int32_t blocks_per_sm, int64_t iters, void *stream, double *updates_per_s,
                                    double *updates_per_clk_sm)
 {
-    if ((word_bytes != 4 && word_bytes != 8) || nbins < 8 || nbins > 4096 || (nbins & (nbins - 1)) ||
-        warps < 1 || warps > 32 || blocks_per_sm < 1 || blocks_per_sm > 32 || iters < 1 || iters > (1 << 30))
+    if ((word_bytes != 4 && word_bytes != 6 && word_bytes != 8) || (op != 0 && op != 1) || nbins < 8 ||
+        nbins > 4096 || (nbins & (nbins - 1)) || warps < 1 || warps > 32 || blocks_per_sm < 1 ||
+        blocks_per_sm > 32 || iters < 1 || iters > (1 << 30))
         return GPFC_EINVAL;
     const size_t smem = (size_t)warps * nbins * 32 * word_bytes;
     int dev = 0, sms = 0, max_smem = 0;
@@ -84,7 +133,10 @@ extern "C" int gpfc_probe_smem_rmw(int32_t word_bytes, int32_t nbins, int32_t wa
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)max_smem) return GPFC_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    auto kern = word_bytes == 8 ? gpfc::smem_rmw_probe_kernel<true> : gpfc::smem_rmw_probe_kernel<false>;
+    using namespace gpfc;
+    auto kern = word_bytes == 8 ? (op ? smem_rmw_probe_kernel<kRed8> : smem_rmw_probe_kernel<kLdSt8>)
+              : word_bytes == 6 ? (op ? smem_rmw_probe_kernel<kRed6> : smem_rmw_probe_kernel<kLdSt6>)
+                                : (op ? smem_rmw_probe_kernel<kRed4> : smem_rmw_probe_kernel<kLdSt4>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GPFC_ECUDA;
     int occ = 0;

@@ -149,10 +149,11 @@ def test_smem_probe_rejects_bad_arguments_without_gpu():
     import paper_2312_02063_gb300 as g
     lib = g.load_library()
     f = lib.gpfc_probe_smem_rmw
-    assert f(6, 32, 16, 1, 100, None, None, None) == -1      # word size
-    assert f(8, 48, 16, 1, 100, None, None, None) == -1      # not a power of two
-    assert f(8, 32, 0, 1, 100, None, None, None) == -1       # no warps
-    assert f(4, 32, 16, 1, 0, None, None, None) == -1        # no iterations
+    assert f(5, 0, 32, 16, 1, 100, None, None, None) == -1      # word size
+    assert f(8, 2, 32, 16, 1, 100, None, None, None) == -1      # operation
+    assert f(8, 0, 48, 16, 1, 100, None, None, None) == -1      # not a power of two
+    assert f(8, 1, 32, 0, 1, 100, None, None, None) == -1       # no warps
+    assert f(4, 0, 32, 16, 1, 0, None, None, None) == -1        # no iterations
 
 
 def test_detrend_rejects_bad_arguments_without_gpu():
