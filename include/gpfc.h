@@ -82,21 +82,30 @@ int gpfc_fold_launch_times(gpfc_ctx *ctx, float *total_ms, int32_t *launches);
 
 /* Launch configuration of the fold kernel (gpfc_fold, gpfc_search, gpfc_search_batched).
  * Every field 0 means "automatic" (the autotuner's choice if it has one, else a default).
- * The results do not depend on it except for the FP32 rounding of the per-chunk partial
- * sums (chunk): warps, layout, tile and blocks_per_sm give bit-identical outputs.
+ * Layouts 1 and 2 give bit-identical outputs for any warps, tile and blocks_per_sm (chunk
+ * changes the FP32 rounding of the per-chunk partial sums). Layout 3 sums flux quantised to
+ * multiples of 2^-e (e per star, the largest with chunk x max|x| 2^e < 2^31) exactly and
+ * rounds each bin once to FP32: bit-identical for any warps, streams, tile and
+ * blocks_per_sm; chunk sets e.
  *   warps          warps per block, 32 trial periods per warp (1..16, capped by shared memory)
  *   layout         shared-memory bins: 1 = FP32 sum + 16-bit count (6 B per bin),
- *                  2 = FP32 sum + 32-bit count in one 64-bit word (8 B per bin)
+ *                  2 = FP32 sum + 32-bit count in one 64-bit word (8 B per bin),
+ *                  3 = fixed-point 32-bit sum + 32-bit count updated by shared-memory
+ *                  reductions (8 B per bin; flux quantised per star, see gpfc_fold)
  *   chunk          samples per compensated chunk (rounded down to a multiple of 16, 256..65520)
  *   tile           light-curve samples per bulk copy into shared memory: 512, 1024 or 2048
  *   blocks_per_sm  resident blocks per multiprocessor of the persistent grid (capped by
- *                  what fits) */
+ *                  what fits)
+ *   streams        layout 3 only: warps that fold disjoint samples of each warp's 32 periods
+ *                  into the same bins (1..12 with warps x streams <= 12; the box epilogue of
+ *                  gpfc_search below 256 bins always uses 1) */
 typedef struct {
     int32_t warps;
     int32_t layout;
     int32_t chunk;
     int32_t tile;
     int32_t blocks_per_sm;
+    int32_t streams;
 } gpfc_fold_config;
 
 /* Set (cfg != NULL) or reset to automatic (cfg == NULL) the context's fold config.
@@ -113,7 +122,9 @@ int gpfc_last_fold_plan(const gpfc_ctx *ctx, gpfc_fold_config *out);
 /* Autotuner. gpfc_autotune times the fold kernel on the given star (device arrays, as
  * for gpfc_search) over its first min(n_periods, 4 * 128 * SMs) periods for every launch
  * config (layout x tile x warps, with the blocks per SM that fit) whose resident periods
- * per SM are at least half the largest, and keeps the fastest in the context under
+ * per SM are at least half the largest, among the layouts of the same arithmetic as the
+ * default (or the set) layout: 1 and 2 (FP32 partial sums), or 3 (fixed point), so a tuned
+ * config gives the same results as the default one; it keeps the fastest in the context under
  * (nbins, scorer, floor(log2 n)). scorer GPFC_SCORER_BOX times the fold with its box-SNR
  * epilogue (scorer_params: gpfc_box_params*), GPFC_SCORER_CNN the fold that writes
  * profiles (scorer_params unused). The chosen config goes to *out (host, may be NULL).
@@ -391,7 +402,9 @@ typedef enum { GPFC_SCORER_BOX = 0, GPFC_SCORER_CNN = 1 } gpfc_scorer;
  * counts in L2, and the fold warps take leftover profiles when they would otherwise wait
  * for a slot (when the extra warp's shared memory does not fit, GPFC_BOX_WARP is used; a
  * batched search whose tuned fold block leaves no room takes the default fold block).
- * GPFC_BOX_AUTO (the default) takes GPFC_BOX_FUSED from nbins >= 256, else the epilogue.
+ * GPFC_BOX_AUTO (the default) takes GPFC_BOX_FUSED from nbins >= 256, else the epilogue;
+ * with fold layout 3 (the default from 256 bins) the one-kernel block does not fit beside
+ * twelve fold warps, so GPFC_BOX_WARP runs.
  * The box scores of the warp and fused paths are bit-identical; a batched search and the
  * per-star search agree bit for bit whatever the path. */
 typedef enum { GPFC_BOX_AUTO = 0, GPFC_BOX_EPILOGUE = 1, GPFC_BOX_WARP = 2, GPFC_BOX_FUSED = 3 } gpfc_box_path;

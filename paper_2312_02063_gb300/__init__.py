@@ -44,7 +44,7 @@ class GpfcError(RuntimeError):
 
 class FoldConfig(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int32), ("layout", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("streams", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -52,6 +52,7 @@ class FoldConfig(ctypes.Structure):
 
 LAYOUT_PAIRED16 = 1
 LAYOUT_PACKED64 = 2
+LAYOUT_RED32 = 3
 
 
 class CnnWeights(ctypes.Structure):
@@ -196,9 +197,9 @@ class Context:
     def sync(self):
         self._check(self.lib.gpfc_sync(self.handle))
 
-    def set_fold_config(self, warps=0, layout=0, chunk=0, tile=0, blocks_per_sm=0):
+    def set_fold_config(self, warps=0, layout=0, chunk=0, tile=0, blocks_per_sm=0, streams=0):
         """Fold launch configuration; 0 means automatic for each field."""
-        cfg = FoldConfig(int(warps), int(layout), int(chunk), int(tile), int(blocks_per_sm))
+        cfg = FoldConfig(int(warps), int(layout), int(chunk), int(tile), int(blocks_per_sm), int(streams))
         self._check(self.lib.gpfc_set_fold_config(self.handle, ctypes.byref(cfg)))
 
     def last_fold_plan(self) -> dict:

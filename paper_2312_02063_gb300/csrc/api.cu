@@ -149,14 +149,16 @@ int ensure_ws(gpfc_ctx *ctx, size_t bytes)
 }
 
 struct FoldPlan {
-    int warps, ppc, grid, G, layout, chunk, tile, bps;
+    int warps, ppc, grid, G, layout, chunk, tile, bps, streams;
     int64_t ntasks;
 };
 
-// At 256 bins and more, three warps of 8-byte bins (one 64-bit shared access per
-// update) fold faster than four warps of 6-byte bins; below that the smaller bins win by
-// fitting more warps.
-int default_layout(int nbins) { return nbins >= 256 ? kLayoutPacked64 : kLayoutPaired16; }
+// At 256 bins and more the reduction layout: its updates need no load, so three period
+// groups of 8-byte bins can be folded by twelve warps at once (1.3x the 64-bit
+// read-modify-write layout on a Kepler-length star). Below 256 bins the box search runs
+// in the fold's epilogue, one warp per 32 periods, where the 6-byte bins fit the most
+// warps.
+int default_layout(int nbins) { return nbins >= 256 ? kLayoutRed32 : kLayoutPaired16; }
 
 int floor_log2(int64_t n)
 {
@@ -198,12 +200,20 @@ FoldPlan plan_with(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const 
     // partials are then added with Kahan compensation. Each flush costs a few L2 round
     // trips that one warp per scheduler cannot hide, so chunks are as long as precision
     // allows (the C2 search: 18.3 / 17.3 / 16.7 ms at 32 / 64 / 128 samples per bin).
-    int64_t chunk = cfg.chunk > 0 ? cfg.chunk : (int64_t)128 * nbins;
+    // The reduction layout's sums are exact, so its chunks are as long as allowed: one
+    // chunk per star up to 65,520 samples (each flush stalls all the block's warps; the
+    // fixed-point unit grows with the chunk).
+    int64_t chunk = cfg.chunk > 0 ? cfg.chunk : (pl.layout == kLayoutRed32 ? (int64_t)65520 : (int64_t)128 * nbins);
     pl.chunk = (int)std::min<int64_t>(65520, std::max<int64_t>(256, chunk)) & ~15;
     pl.warps = w;
     pl.ppc = 32 * w;
     pl.ntasks = (np + pl.ppc - 1) / pl.ppc;
-    const int occ = std::max(1, fold_blocks_per_sm(nbins, w, pl.layout, pl.tile));
+    // layout 3: enough sample streams for 12 fold warps (three per scheduler); a one-kernel
+    // search block needs one warp fewer for its scorer
+    pl.streams = 1;
+    if (pl.layout == kLayoutRed32) pl.streams = cfg.streams > 0 ? cfg.streams : kMaxRedWarps / w;
+    pl.streams = std::max(1, std::min(pl.streams, kMaxRedWarps / w));
+    const int occ = std::max(1, fold_blocks_per_sm(nbins, w, pl.layout, pl.tile, pl.streams));
     pl.bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
     pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms * pl.bps);
     pl.G = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 8191) / 8192));
@@ -220,7 +230,7 @@ FoldPlan plan_fold(gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const gpfc_f
         if (!cfg.blocks_per_sm) cfg.blocks_per_sm = tuned->blocks_per_sm;
     }
     const FoldPlan pl = plan_with(ctx, n, np, nbins, cfg);
-    ctx->last_plan = gpfc_fold_config{pl.warps, pl.layout, pl.chunk, pl.tile, pl.bps};
+    ctx->last_plan = gpfc_fold_config{pl.warps, pl.layout, pl.chunk, pl.tile, pl.bps, pl.streams};
     return pl;
 }
 
@@ -237,12 +247,13 @@ size_t carve_fold(void *base, const FoldPlan &pl, int64_t n_total, int nstars, i
                   FoldBuffers &fb)
 {
     Carver c(base);
-    fb.partial = c.take<double>((size_t)3 * nstars * pl.G);  // sums, squares, min steps
+    fb.partial = c.take<double>((size_t)4 * nstars * pl.G);  // sums, squares, min steps, max |x|
     fb.stats = c.take<StarStats>(nstars);
     const int64_t se = scratch_elems(n_total, nstars);
     fb.smp.tau_lo = c.take<uint32_t>(se);
     fb.smp.tau_hi = c.take<int32_t>(se);
     fb.smp.x = c.take<float>(se);
+    fb.smp.xq = c.take<int32_t>(se);
     fb.smp.flags = c.take<uint8_t>(se / 16 + 64);
     fb.ws_sc = c.take<float2>((size_t)pl.grid * nbins * pl.ppc);
     fb.ws_cnt = c.take<uint32_t>((size_t)pl.grid * nbins * pl.ppc);
@@ -291,12 +302,13 @@ int prep_groups(int64_t n) { return (int)std::min<int64_t>(256, std::max<int64_t
 size_t carve_wide(void *base, int64_t n, WideBuffers &w)
 {
     Carver c(base);
-    w.partial = c.take<double>((size_t)3 * prep_groups(n));
+    w.partial = c.take<double>((size_t)4 * prep_groups(n));
     w.stats = c.take<StarStats>(1);
     const int64_t se = scratch_elems(n, 1);
     w.smp.tau_lo = c.take<uint32_t>(se);
     w.smp.tau_hi = c.take<int32_t>(se);
     w.smp.x = c.take<float>(se);
+    w.smp.xq = nullptr;  // the two-tier fold quantises on its own
     w.smp.flags = c.take<uint8_t>(se / 16 + 64);
     w.q = c.take<long long>(n);
     w.maxbits = c.take<unsigned int>(1);
@@ -436,7 +448,7 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     if (rc) return rc;
     carve_fold(ctx->ws, pl, n, 1, nbins, fb);
     cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G,
-                                fb.stats, ctx->status_dev, ctx->stream);
+                                fb.stats, ctx->status_dev, ctx->stream, pl.chunk);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
     p.smp = fb.smp;
     p.lc_off = nullptr;
@@ -453,6 +465,7 @@ int run_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, c
     p.warps = pl.warps;
     p.chunk = pl.chunk;
     p.layout = pl.layout;
+    p.streams = pl.streams;
     p.tile = pl.tile;
     p.ws_sc = fb.ws_sc;
     p.ws_cnt = fb.ws_cnt;
@@ -535,7 +548,13 @@ cudaError_t timed_fold(gpfc_ctx *ctx, cudaStream_t sf, Launch launch)
 bool fused_plan(gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, FoldPlan &pl)
 {
     pl = plan_fold(ctx, n, np, nbins, find_tuned(ctx, nbins, kModeFold, n));
-    const int bps = search_blocks_per_sm(nbins, pl.warps, pl.layout, pl.tile);
+    int bps = search_blocks_per_sm(nbins, pl.warps, pl.layout, pl.tile, pl.streams);
+    if (bps < 1 && !ctx->fold_cfg.tile && pl.tile > 512) {
+        // the scorer staging did not fit beside 1024-sample tiles: halve the tiles
+        pl.tile = 512;
+        ctx->last_plan.tile = 512;
+        bps = search_blocks_per_sm(nbins, pl.warps, pl.layout, pl.tile, pl.streams);
+    }
     if (bps < 1) return false;
     pl.bps = bps;
     pl.grid = (int)std::min<int64_t>(pl.ntasks, (int64_t)ctx->num_sms * bps);
@@ -577,7 +596,7 @@ int run_search_box_fused(gpfc_ctx *ctx, const double *times, const float *flux, 
     carve_fused(ctx->ws, pl, n, nbins, B);
     const bool want_best = best_index || best_score;
     cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, B.fb.smp, B.fb.partial, pl.G,
-                                B.fb.stats, ctx->status_dev, ctx->stream);
+                                B.fb.stats, ctx->status_dev, ctx->stream, pl.chunk);
     if (e == cudaSuccess && want_best) e = cudaMemsetAsync(B.fb.key, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
     FoldParams p{};
@@ -593,6 +612,7 @@ int run_search_box_fused(gpfc_ctx *ctx, const double *times, const float *flux, 
     p.warps = pl.warps;
     p.chunk = pl.chunk;
     p.layout = pl.layout;
+    p.streams = pl.streams;
     p.tile = pl.tile;
     p.ws_sc = B.fb.ws_sc;
     p.ws_cnt = B.fb.ws_cnt;
@@ -653,7 +673,7 @@ int run_search_box_warp(gpfc_ctx *ctx, const double *times, const float *flux, i
     }
     const bool want_best = best_index || best_score;
     cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G, fb.stats,
-                                ctx->status_dev, ctx->stream);
+                                ctx->status_dev, ctx->stream, pl.chunk);
     if (e == cudaSuccess && want_best) e = cudaMemsetAsync(fb.key, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
     KernelTimer timer(ctx);
@@ -672,6 +692,7 @@ int run_search_box_warp(gpfc_ctx *ctx, const double *times, const float *flux, i
         p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
+        p.streams = pl.streams;
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
@@ -760,7 +781,7 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
     unsigned long long *key = w.take<unsigned long long>(1);
 
     cudaError_t e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, t0, fb.smp, fb.partial, pl.G, fb.stats,
-                                ctx->status_dev, ctx->stream);
+                                ctx->status_dev, ctx->stream, pl.chunk);
     if (e == cudaSuccess) e = launch_cnn_prep(cnn_src(wt), dev, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
     KernelTimer timer(ctx);
@@ -782,6 +803,7 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
+        p.streams = pl.streams;
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
@@ -832,8 +854,9 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
 // ------------------------------------------------------------------ autotuner
 
 // Times the fold kernel of `mode` (kModeFold without output writes, or kModeBox) on one
-// star over its first periods, for every launch config whose resident periods per SM
-// are at least half the largest, and keeps the fastest under (nbins, mode, log2 n_key).
+// star over its first periods, for every launch config of the default layout's
+// arithmetic whose resident periods per SM are at least half the largest, and keeps the
+// fastest under (nbins, mode, log2 n_key).
 int tune_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, const double *periods,
               int64_t np, int nbins, int mode, const gpfc_box_params *bp, int64_t n_key, gpfc_fold_config *out)
 {
@@ -844,7 +867,11 @@ int tune_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, 
     };
     std::vector<Cand> cands;
     int best_res = 0;
-    for (int layout = 1; layout <= 2; ++layout) {
+    // layouts of the default's arithmetic only (FP32 partial sums: 1 and 2; exact fixed
+    // point: 3), so tuning never changes a result
+    const bool fixed = (ctx->fold_cfg.layout ? ctx->fold_cfg.layout : default_layout(nbins)) == kLayoutRed32;
+    for (int layout = 1; layout <= 3; ++layout) {
+        if ((layout == kLayoutRed32) != fixed) continue;
         for (int tile = 512; tile <= kMaxTile; tile *= 2) {
             const int maxw = fold_max_warps(nbins, layout, tile);
             for (int w = 1; w <= maxw; ++w) {
@@ -877,8 +904,9 @@ int tune_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, 
         carve_fold(ctx->ws, pl, n, 1, nbins, fb);  // the sample scratch sits at the same place for all
         cudaError_t e = cudaSuccess;
         if (!prepped) {
+            // the longest chunk, so the fixed-point flux fits every candidate's chunks
             e = launch_prep(times, flux, nullptr, n, 1, n, nullptr, NAN, fb.smp, fb.partial, pl.G, fb.stats,
-                            ctx->status_dev, ctx->stream);
+                            ctx->status_dev, ctx->stream, 65520);
             if (e != cudaSuccess) return cuda_err(ctx, e, "prep kernels");
             prepped = true;
         }
@@ -895,6 +923,7 @@ int tune_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n, 
         p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
+        p.streams = pl.streams;
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
@@ -1018,7 +1047,7 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
                                       B.task_off, ctx->status_dev, st);
     if (e == cudaSuccess)
         e = launch_prep(A.times, A.flux, B.lc_s, A.n_total, A.S, 0, A.t0s, NAN, B.fb.smp, B.fb.partial, pl.G,
-                        B.fb.stats, ctx->status_dev, st);
+                        B.fb.stats, ctx->status_dev, st, pl.chunk);
     if (e != cudaSuccess) return e;
     FoldParams p{};
     p.smp = B.fb.smp;
@@ -1036,6 +1065,7 @@ cudaError_t enqueue_batched(gpfc_ctx *ctx, const BatchArgs &A, const FoldPlan &p
     p.warps = pl.warps;
     p.chunk = pl.chunk;
     p.layout = pl.layout;
+    p.streams = pl.streams;
     p.tile = pl.tile;
     p.ws_sc = B.fb.ws_sc;
     p.ws_cnt = B.fb.ws_cnt;
@@ -1294,9 +1324,11 @@ int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg)
         ctx->fold_cfg = gpfc_fold_config{0, 0, 0, 0, 0};
         return GPFC_OK;
     }
-    if (cfg->warps < 0 || cfg->warps > kMaxFoldWarps || cfg->layout < 0 || cfg->layout > 2 ||
+    if (cfg->warps < 0 || cfg->warps > kMaxFoldWarps || cfg->layout < 0 || cfg->layout > 3 ||
         cfg->chunk < 0 || cfg->chunk > 65520 || (cfg->tile != 0 && cfg->tile != 512 && cfg->tile != 1024 &&
-                                                   cfg->tile != 2048) || cfg->blocks_per_sm < 0)
+                                                   cfg->tile != 2048) || cfg->blocks_per_sm < 0 ||
+        cfg->streams < 0 || cfg->streams > kMaxRedWarps || (cfg->streams > 1 && cfg->layout != kLayoutRed32) ||
+        (cfg->warps > 0 && cfg->warps * std::max(1, cfg->streams) > kMaxRedWarps))
         return set_err(ctx, GPFC_EINVAL, "fold config out of range");
     ctx->fold_cfg = *cfg;
     return GPFC_OK;
@@ -1304,7 +1336,7 @@ int gpfc_set_fold_config(gpfc_ctx *ctx, const gpfc_fold_config *cfg)
 
 int gpfc_fold_max_warps(int32_t nbins, int32_t layout)
 {
-    if (nbins < 2 || nbins > kMaxNbinsLane || layout < 1 || layout > 2) return 0;
+    if (nbins < 2 || nbins > kMaxNbinsLane || layout < 1 || layout > 3) return 0;
     return fold_max_warps(nbins, layout);
 }
 
@@ -2038,10 +2070,10 @@ int gpfc_search_batched(gpfc_ctx *ctx, int32_t n_stars, const int64_t *lc_offset
         // the one-kernel search, with the tuned fold config if its block fits, else the
         // default one
         FoldPlan ps = pl;
-        int bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile);
+        int bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile, ps.streams);
         if (bps < 1) {
             ps = plan_fold(ctx, n_avg, n_periods_total, nbins, nullptr);
-            bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile);
+            bps = search_blocks_per_sm(nbins, ps.warps, ps.layout, ps.tile, ps.streams);
         }
         // a block numbers the rows of its tasks in 32-bit tickets
         const int64_t rows_per_block = (task_bound(A, ps.ppc) + ctx->num_sms - 1) / ctx->num_sms * ps.ppc;

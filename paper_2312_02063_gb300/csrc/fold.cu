@@ -111,6 +111,7 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
 {
     __shared__ double red[32];
     __shared__ long long redm[32];
+    __shared__ float redx[32];
     __shared__ double s_fref;
     const int s = blockIdx.y;
     const int G = gridDim.x;
@@ -131,6 +132,7 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
     const int64_t j0 = (int64_t)blockIdx.x * per;
     const int64_t j1 = min(len, j0 + per);
     double acc = 0.0;
+    float amax = 0.f;  // largest |x| of this block's samples
     bool bad = false;
     long long dmin = LLONG_MAX;  // smallest positive step tau_j - tau_{j-1}
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -143,6 +145,7 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
         smp.tau_hi[base + j] = (int32_t)(tau >> 32);
         const double d = (double)flux[b + j] - f_ref;
         smp.x[base + j] = (float)d;
+        amax = fmaxf(amax, fabsf((float)d));
         acc += d * d;
     }
     if (bad) report_error(status, kErrRange);
@@ -160,6 +163,8 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
         dmin = u < dmin ? u : dmin;
     }
     if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = dmin;
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) redx[threadIdx.x >> 5] = amax;
     double t = block_sum_f64(acc, red);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -167,6 +172,9 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
         long long m = LLONG_MAX;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = redm[w] < m ? redm[w] : m;
         pmin[(size_t)s * G + blockIdx.x] = m;
+        float xm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) xm = fmaxf(xm, redx[w]);
+        partial[(size_t)3 * gridDim.y * G + (size_t)s * G + blockIdx.x] = (double)xm;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[s].f_ref = f_ref;
@@ -177,29 +185,48 @@ __global__ void prep_quant_kernel(const double *times, const float *flux, const 
     }
 }
 
-// Pass 3: sigma = sqrt(sum (flux - f_ref)^2 / n) and the smallest positive time step
-// per star. grid = stars, 32 threads.
-__global__ void prep_sigma_kernel(const double *partial, const long long *pmin, int G, int nstars,
+// Exponent of the fixed-point flux: the largest e (|e| <= 200) with xmax 2^e <= lim, so that
+// every |rint(x 2^e)| <= lim. 0 for xmax = 0.
+__device__ __forceinline__ int fixed_point_exp(double xmax, double lim)
+{
+    if (!(xmax > 0.0) || !(xmax < INFINITY)) return 0;
+    int e = ilogb(lim) - ilogb(xmax);
+    e = max(-200, min(200, e));
+    while (e < 200 && ldexp(xmax, e + 1) <= lim) ++e;
+    while (e > -200 && ldexp(xmax, e) > lim) --e;
+    return e;
+}
+
+// Pass 3: sigma = sqrt(sum (flux - f_ref)^2 / n), the smallest positive time step and the
+// fixed-point exponent per star: a chunk of min(chunk, n) samples then sums to at most
+// 2^31 - 1 in magnitude in any bin. grid = stars, 32 threads.
+__global__ void prep_sigma_kernel(const double *partial, const long long *pmin, int G, int nstars, int chunk,
                                   StarStats *stats)
 {
     const int s = blockIdx.x;
     if (threadIdx.x != 0) return;
-    double t = 0.0;
+    double t = 0.0, xm = 0.0;
     long long m = LLONG_MAX;
     for (int g = 0; g < G; ++g) {
         t += partial[(size_t)nstars * G + (size_t)s * G + g];
+        xm = fmax(xm, partial[(size_t)3 * nstars * G + (size_t)s * G + g]);
         const long long v = pmin[(size_t)s * G + g];
         m = v < m ? v : m;
     }
     stats[s].sigma = (float)sqrt(t / (double)stats[s].n);
     stats[s].dtau0 = m == LLONG_MAX ? 0 : m;
+    // a chunk holds at most min(chunk, n) samples of the star
+    const int lmax = min(chunk, max(1, stats[s].n));
+    stats[s].qexp = fixed_point_exp(xm, floor(2147483647.0 / (double)lmax));
+    stats[s].pad = 0;
 }
 
 // Pass 4: one flag byte per group of 16 samples: 1 if every step inside the group lies in
 // [dtau0, dtau0 + 2] (a regular cadence up to the 2^-24 d rounding of tau) and the high
 // word of tau is the same for all 16 (it changes every 2^32 units, ~256 d). The fold
 // skips its per-group bin-collision check on flagged groups when the period allows it,
-// and forms their phases with one th * F_lo product per group.
+// and forms their phases with one th * F_lo product per group. The same pass writes the
+// fixed-point flux xq = rint(x 2^qexp) when the scratch has room for it.
 // grid = (G, stars).
 __global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratch smp,
                                   const StarStats *stats)
@@ -227,12 +254,20 @@ __global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratc
             }
         }
         smp.flags[base / 16 + q] = reg ? 1 : 0;
+        if (smp.xq) {
+            // fixed-point flux (exact: scaling by a power of two, then rounding to nearest
+            // even); zero past the star's end
+            const double sc = ldexp(1.0, stats[s].qexp);
+            for (int k = 0; k < 16; ++k)
+                smp.xq[base + j0 + k] = j0 + k < len ? __double2int_rn((double)smp.x[base + j0 + k] * sc) : 0;
+        }
     }
 }
 
 cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
                         int nstars, int64_t max_len, const double *t0s, double t0, SampleScratch smp,
-                        double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st)
+                        double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st,
+                        int chunk)
 {
     (void)max_len;
     dim3 grid(G, nstars);
@@ -240,7 +275,7 @@ cudaError_t launch_prep(const double *times, const float *flux, const int64_t *l
     prep_sum_kernel<<<grid, 256, 0, st>>>(flux, lc_off, n, partial);
     prep_quant_kernel<<<grid, 256, 0, st>>>(times, flux, lc_off, n, t0s, t0, partial, pmin, smp, stats,
                                             status);
-    prep_sigma_kernel<<<nstars, 32, 0, st>>>(partial, pmin, G, nstars, stats);
+    prep_sigma_kernel<<<nstars, 32, 0, st>>>(partial, pmin, G, nstars, chunk < 16 ? 16 : chunk, stats);
     prep_flags_kernel<<<grid, 256, 0, st>>>(lc_off, n, smp, stats);
     return cudaGetLastError();
 }
@@ -305,6 +340,38 @@ struct StorePacked64 {
     }
     __device__ __forceinline__ float sum(uint32_t b) const { return __uint_as_float(lds_u32x2(v + (b << 8)).x); }
     __device__ __forceinline__ uint32_t count(uint32_t b) const { return lds_u32x2(v + (b << 8)).y; }
+};
+
+// Words accumulated by no-return shared reductions: 256 bytes per bin of a warp, the 32
+// lanes' sum words then their 32-bit count words ([bin][sum row, count row][lane]), so both
+// rows are free of bank conflicts and the count sits at a fixed offset (128) from the sum.
+// During the fold the sum word holds the fixed-point sum (two's complement, mod 2^32); one
+// update is two red.shared.add.u32 with no result to wait for. Reductions of one thread to
+// one address take effect in program order, so no check for two samples in one bin is
+// needed, and integer sums do not depend on the order anyway. After the last chunk's flush
+// the sum word holds the FP32 sum and the count word the exact count.
+struct StoreRed32 {
+    uint32_t v;  // shared address of this lane's bin-0 sum word
+    static constexpr bool kSaturates = false;
+    __device__ __forceinline__ void add(uint32_t b, int32_t xq) const
+    {
+        const uint32_t a = v + (b << 8);
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"((uint32_t)xq) : "memory");
+        asm volatile("red.shared.add.u32 [%0+128], %1;" ::"r"(a), "r"(1u) : "memory");
+    }
+    __device__ __forceinline__ void load(uint32_t b, float &s, uint32_t &c) const
+    {
+        s = lds_f32(v + (b << 8));
+        c = lds_u32(v + (b << 8) + 128u);
+    }
+    __device__ __forceinline__ void put(uint32_t b, float s, uint32_t c) const
+    {
+        sts_f32(v + (b << 8), s);
+        sts_u32(v + (b << 8) + 128u, c);
+    }
+    __device__ __forceinline__ float sum(uint32_t b) const { return lds_f32(v + (b << 8)); }
+    __device__ __forceinline__ uint32_t count(uint32_t b) const { return lds_u32(v + (b << 8) + 128u); }
+    __device__ __forceinline__ int32_t isum(uint32_t b) const { return (int32_t)lds_u32(v + (b << 8)); }
 };
 
 // Tile data of U consecutive samples, held in registers.
@@ -592,6 +659,63 @@ __device__ __forceinline__ void fold_segment(uint32_t stl, uint32_t sth, uint32_
                                nbins, shift);
 }
 
+// kLayoutRed32: fold this stream's share of nvalid samples (a segment starting on a
+// 16-sample boundary of the tile) by reductions: the 16-sample groups g with
+// g mod nstreams = stream, and the tail after the last whole group if its turn falls on this
+// stream. Groups flagged regular by the prep pass read one tau high word and form
+// th * F_lo once; the others read every sample's high word. sxq addresses the fixed-point
+// flux of the tile.
+template <bool POW2>
+__device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sth, uint32_t sxq, unsigned long long fmask,
+                                                 int nvalid, const StoreRed32 &st, uint32_t Fl, uint32_t Fh,
+                                                 uint32_t nbins, int shift, int stream, int nstreams)
+{
+    const int ng = nvalid >> 4;
+#pragma unroll 1
+    for (int g = stream; g < ng; g += nstreams) {
+        const uint32_t o = 64u * (uint32_t)g;
+        uint4 a[4], xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = lds_u32x4(stl + o + 16u * q);
+            xv[q] = lds_u32x4(sxq + o + 16u * q);
+        }
+        uint32_t b[16];
+        if ((fmask >> g) & 1ull) {
+            const uint32_t thF = lds_u32(sth + o) * Fl;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                b[4 * q + 0] = phase_bin_th<POW2>(a[q].x, thF, Fl, Fh, nbins, shift);
+                b[4 * q + 1] = phase_bin_th<POW2>(a[q].y, thF, Fl, Fh, nbins, shift);
+                b[4 * q + 2] = phase_bin_th<POW2>(a[q].z, thF, Fl, Fh, nbins, shift);
+                b[4 * q + 3] = phase_bin_th<POW2>(a[q].w, thF, Fl, Fh, nbins, shift);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 h = lds_u32x4(sth + o + 16u * q);
+                b[4 * q + 0] = phase_bin<POW2>(a[q].x, h.x, Fl, Fh, nbins, shift);
+                b[4 * q + 1] = phase_bin<POW2>(a[q].y, h.y, Fl, Fh, nbins, shift);
+                b[4 * q + 2] = phase_bin<POW2>(a[q].z, h.z, Fl, Fh, nbins, shift);
+                b[4 * q + 3] = phase_bin<POW2>(a[q].w, h.w, Fl, Fh, nbins, shift);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            st.add(b[4 * q + 0], (int32_t)xv[q].x);
+            st.add(b[4 * q + 1], (int32_t)xv[q].y);
+            st.add(b[4 * q + 2], (int32_t)xv[q].z);
+            st.add(b[4 * q + 3], (int32_t)xv[q].w);
+        }
+    }
+    if (ng % nstreams == stream) {
+        for (int i = 16 * ng; i < nvalid; ++i) {
+            const uint32_t bb = phase_bin<POW2>(lds_u32(stl + 4u * i), lds_u32(sth + 4u * i), Fl, Fh, nbins, shift);
+            st.add(bb, (int32_t)lds_u32(sxq + 4u * i));
+        }
+    }
+}
+
 // Fold this lane's chunk partials into the Kahan workspace (sum, compensation) and the
 // exact 32-bit counts. On the last chunk the finished sums (sum - compensation) go back
 // into the store with the counts (16-bit stores saturate at 65535; the exact totals stay
@@ -662,6 +786,49 @@ __device__ __forceinline__ bool flush_chunk(const St &st, float2 *wsc, uint32_t 
         flush_one(st, wsc, wcn, b0, idx, first, last, sc, cc, over);
     }
     return over;
+}
+
+// kLayoutRed32 flush: add each bin's chunk sum and count into the exact workspace (int64
+// fixed-point sum, 32-bit count). On the last chunk the bin gets its FP32 sum
+// tot 2^-qexp (one rounding) and its count; otherwise it is cleared. Workspace reads are
+// batched 16 bins at a time to overlap their latency.
+__device__ __forceinline__ void flush_one_red(const StoreRed32 &st, long long *wss, uint32_t *wcn, int b,
+                                              size_t idx, bool last, long long tot, uint32_t cc, double qscale)
+{
+    float unused;
+    uint32_t c;
+    st.load((uint32_t)b, unused, c);
+    tot += (long long)st.isum((uint32_t)b);
+    cc += c;
+    if (last) {
+        st.put((uint32_t)b, (float)((double)tot * qscale), cc);
+    } else {
+        wss[idx] = tot;
+        wcn[idx] = cc;
+        st.put((uint32_t)b, 0.f, 0u);
+    }
+}
+
+__device__ __forceinline__ void flush_chunk_red(const StoreRed32 &st, long long *wss, uint32_t *wcn, int blo,
+                                                int bhi, int ppc, bool first, bool last, double qscale)
+{
+    int b0 = blo;
+    for (; b0 + 16 <= bhi; b0 += 16) {
+        long long ts[16];
+        uint32_t cc[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            ts[u] = first ? 0ll : wss[(size_t)(b0 + u) * ppc];
+            cc[u] = first ? 0u : wcn[(size_t)(b0 + u) * ppc];
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            flush_one_red(st, wss, wcn, b0 + u, (size_t)(b0 + u) * ppc, last, ts[u], cc[u], qscale);
+    }
+    for (; b0 < bhi; ++b0) {
+        const size_t idx = (size_t)b0 * ppc;
+        flush_one_red(st, wss, wcn, b0, idx, last, first ? 0ll : wss[idx], first ? 0u : wcn[idx], qscale);
+    }
 }
 
 // Bins of one profile as seen by one lane: the fold's lane-private store.
@@ -1210,14 +1377,21 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort;
     __shared__ SearchShared sh;
+    constexpr bool kRed = LAYOUT == kLayoutRed32;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nbins = p.nbins;
     const int ppc = 32 * p.warps;
     const int tile = p.tile;
+    // fold warps: period group gw = warp % warps, sample stream sw = warp / warps (kLayoutRed32
+    // only; otherwise one stream). Stream sw finalises and writes out bins [blo, bhi).
+    const int nstreams = kRed ? p.streams : 1;
+    const int nfw = p.warps * nstreams;
+    const int gw = warp % p.warps, sw = warp / p.warps;
+    const int blo = (int)((int64_t)sw * nbins / nstreams), bhi = (int)((int64_t)(sw + 1) * nbins / nstreams);
     // block barrier of the fold warps (in kModeSearch the scorer warp is not among them)
     auto fold_sync = [&]() {
-        if (MODE == kModeSearch) named_bar_sync(1, 32 * p.warps);
+        if (MODE == kModeSearch) named_bar_sync(1, 32 * nfw);
         else __syncthreads();
     };
 
@@ -1226,11 +1400,15 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     uint32_t *th_buf = tl_buf + 2 * tile;
     float *x_buf = reinterpret_cast<float *>(th_buf + 2 * tile);
     uint8_t *f_buf = reinterpret_cast<uint8_t *>(x_buf + 2 * tile);  // [2][tile / 16]
-    using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64, StorePaired16>::type;
+    using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64,
+                                         typename std::conditional<kRed, StoreRed32, StorePaired16>::type>::type;
     St st;
     if constexpr (LAYOUT == kLayoutPacked64) {
         uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (tile / 16));
         st.v = smem_u32(v + (size_t)warp * nbins * 32 + lane);
+    } else if constexpr (kRed) {
+        uint32_t *v = reinterpret_cast<uint32_t *>(f_buf + 2 * (tile / 16));
+        st.v = smem_u32(v + (size_t)gw * nbins * 64 + lane);
     } else {
         float *acc = reinterpret_cast<float *>(f_buf + 2 * (tile / 16));
         const int nb2 = (nbins + 1) & ~1;
@@ -1250,8 +1428,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     }
     __syncthreads();
     uint32_t parity_bits = 0u;  // bit b: phase parity of buffer b
-    float2 *wsc_cta = p.ws_sc + (size_t)blockIdx.x * nbins * ppc + warp * 32 + lane;
-    uint32_t *wcn_cta = p.ws_cnt + (size_t)blockIdx.x * nbins * ppc + warp * 32 + lane;
+    float2 *wsc_cta = p.ws_sc + (size_t)blockIdx.x * nbins * ppc + gw * 32 + lane;
+    uint32_t *wcn_cta = p.ws_cnt + (size_t)blockIdx.x * nbins * ppc + gw * 32 + lane;
 
     int64_t task_end = p.ntasks;
     if (p.ntasks_dev) {
@@ -1261,10 +1439,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     // kModeSearch: this block's tasks, their rows as tickets, and the warps' scorer staging
     const int64_t first_task = p.task_begin + blockIdx.x;
     const int my_tasks = first_task < task_end ? (int)((task_end - first_task + gridDim.x - 1) / gridDim.x) : 0;
-    float2 *Bw = reinterpret_cast<float2 *>(smem + p.stage_off) + (size_t)warp * coop_pairs(nbins);
+    // scorer staging: one slot per warp of stream 0 (the fold warps that also score
+    // leftover rows) and one for the scorer warp
+    float2 *Bw = reinterpret_cast<float2 *>(smem + p.stage_off) + (size_t)(warp == nfw ? p.warps : gw) * coop_pairs(nbins);
     int cur_s = -1;
     unsigned long long cur_key = 0ull;
-    if (MODE == kModeSearch && warp == p.warps) {
+    if (MODE == kModeSearch && warp == nfw) {
         // the scorer warp: take tickets in order, wait for each one's task to be published
         for (;;) {
             int t = 0;
@@ -1301,7 +1481,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         // (more than 2^24 samples happens only for offsets the batch plan rejected)
         const int64_t nsamp = min(le - lb, (int64_t)1 << 24);
         const int64_t sbase = scratch_start(lb, s);
-        const int64_t k = gb + (task - tbase) * ppc + warp * 32 + lane;
+        const int64_t k = gb + (task - tbase) * ppc + gw * 32 + lane;
         const bool kvalid = k < ge;
 
         uint32_t Fl = 0u, Fh = 0u;
@@ -1321,7 +1501,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         }
         // one group size for the whole warp, so its lanes never diverge between paths
         const int wg = __all_sync(0xffffffffu, gsize >= 16) ? 16 : (__all_sync(0xffffffffu, gsize >= 8) ? 8 : 0);
-        for (int b = 0; b < nbins; ++b) st.put((uint32_t)b, 0.f, 0u);
+        const double qscale = kRed ? ldexp(1.0, -p.stats[s].qexp) : 1.0;  // fixed-point unit
+        for (int b = blo; b < bhi; ++b) st.put((uint32_t)b, 0.f, 0u);
         const int ntiles = (int)((nsamp + tile - 1) / tile);
         auto issue = [&](int t, int buf) {
             const int64_t i0 = (int64_t)t * tile;
@@ -1331,7 +1512,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             mbar_arrive_expect_tx(&bars[buf], 3u * bytes + fbytes);
             bulk_g2s(tl_buf + buf * tile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(th_buf + buf * tile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
+            if (kRed) bulk_g2s(x_buf + buf * tile, p.smp.xq + sbase + i0, bytes, &bars[buf]);
+            else bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
         fold_sync();  // previous task's readers are done with both buffers
@@ -1344,8 +1526,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         int chunk_left = p.chunk;
         for (int t = 0; t < ntiles; ++t) {
             const int buf = t & 1;
-            const bool ok = mbar_wait_bounded(&bars[buf], (parity_bits >> buf) & 1u);
+            bool ok = mbar_wait_bounded(&bars[buf], (parity_bits >> buf) & 1u);
             parity_bits ^= 1u << buf;
+            // with several streams the fold warps meet at chunk flushes inside the tile, so
+            // they all take the same branch
+            if (nstreams > 1) ok = !named_bar_or(1, 32 * nfw, !ok);
             if (!ok) {
                 s_abort = 1;
                 report_error(p.status, kErrTimeout);
@@ -1380,13 +1565,27 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     while (i < nvs) {
                         // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
                         const int seg = min(nvs - i, chunk_left);
-                        fold_segment<POW2, St, (MAXW <= 4)>(stl + 4u * i, sth + 4u * i, sx + 4u * i, fmask >> (i >> 4),
-                                                             seg, st, Fl, Fh, (uint32_t)nbins, p.shift, wg);
+                        if constexpr (kRed)
+                            fold_segment_red<POW2>(stl + 4u * i, sth + 4u * i, sx + 4u * i, fmask >> (i >> 4), seg, st,
+                                                   Fl, Fh, (uint32_t)nbins, p.shift, sw, nstreams);
+                        else
+                            fold_segment<POW2, St, (MAXW <= 4)>(stl + 4u * i, sth + 4u * i, sx + 4u * i,
+                                                                 fmask >> (i >> 4), seg, st, Fl, Fh, (uint32_t)nbins,
+                                                                 p.shift, wg);
                         i += seg;
                         chunk_left -= seg;
                         const bool last = (t == ntiles - 1) && (sub + i == nv);
                         if (chunk_left == 0 || last) {
-                            over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
+                            if constexpr (kRed) {
+                                // every stream's reductions of the chunk land before the flush
+                                // reads them, and the cleared bins before the next chunk's
+                                if (nstreams > 1) fold_sync();
+                                flush_chunk_red(st, reinterpret_cast<long long *>(wsc_cta), wcn_cta, blo, bhi, ppc,
+                                                first_flush, last, qscale);
+                                if (nstreams > 1) fold_sync();
+                            }
+                            else
+                                over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
                             first_flush = false;
                             chunk_left = p.chunk;
                         }
@@ -1405,14 +1604,15 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             if (threadIdx.x == 0 && t + 2 < ntiles) issue(t + 2, buf);
         }
 
-        // ---------------- epilogues (lane-private, no block barrier needed)
+        // ---------------- epilogues (lane-private; with several streams each writes its own
+        // bins, which it also clears for the next task)
         if (MODE == kModeFold) {
             // output row: the period, or the lane's chunk slot
-            const int64_t row = p.slot_k ? (task - p.task_begin) * ppc + warp * 32 + lane : k;
-            if (p.slot_k) p.slot_k[row] = kvalid ? k : -1;
+            const int64_t row = p.slot_k ? (task - p.task_begin) * ppc + gw * 32 + lane : k;
+            if (p.slot_k && sw == 0) p.slot_k[row] = kvalid ? k : -1;
             if (kvalid || p.slot_k) {
                 const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
-                for (int b = 0; b < nbins; ++b) {
+                for (int b = blo; b < bhi; ++b) {
                     float S;
                     uint32_t c;
                     st.load((uint32_t)b, S, c);
@@ -1427,9 +1627,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             const int b = iter & 1;
             const int need = (iter >> 1) * ppc;  // rows of slot b that must be scored first
             bool ok = true;
-            if (iter >= 2) {
+            if (iter >= 2 && sw == 0) {
                 // slot b still holds task iter - 2: score leftover rows of the published tasks
-                // (tickets below iter * ppc) until all of iter - 2's rows are done
+                // (tickets below iter * ppc) until all of iter - 2's rows are done (the
+                // warps of stream 0 only: they own the fold warps' scorer staging)
                 for (;;) {
                     int t = -1;
                     if (lane == 0) t = *reinterpret_cast<volatile int *>(&sh.done[b]) >= need
@@ -1445,10 +1646,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     }
                 }
             }
+            // the other streams write their bins of the slot once stream 0 has found it free
+            if (nstreams > 1) ok = !named_bar_or(1, 32 * nfw, !ok);
             if (ok) {
-                const size_t base = ((size_t)blockIdx.x * 2 + b) * ppc + warp * 32 + lane;
-                p.slot_k[base] = kvalid ? k : -1;
-                for (int bb = 0; bb < nbins; ++bb) {
+                const size_t base = ((size_t)blockIdx.x * 2 + b) * ppc + gw * 32 + lane;
+                if (sw == 0) p.slot_k[base] = kvalid ? k : -1;
+                for (int bb = blo; bb < bhi; ++bb) {
                     float S;
                     uint32_t c;
                     st.load((uint32_t)bb, S, c);
@@ -1459,7 +1662,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 }
             }
             // every row of the task is written; all fold warps leave together on a failure
-            if (named_bar_or(1, 32 * p.warps, !ok)) {
+            if (named_bar_or(1, 32 * nfw, !ok)) {
                 if (threadIdx.x == 0) *reinterpret_cast<volatile int *>(&s_abort) = 1;
                 return;
             }
@@ -1487,7 +1690,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             }
         }
     }
-    if (MODE == kModeSearch) {
+    if (MODE == kModeSearch && sw == 0) {
         // all tasks published: score whatever rows are left, then leave
         for (;;) {
             int t = 0;
@@ -1502,7 +1705,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     if (MODE == kModeFold && p.slot_k) {
         // slots of tasks in this launch's range that lie past the device task count
         const int64_t t0 = task_end > p.task_begin ? task_end : p.task_begin;
-        for (int64_t task = t0 + blockIdx.x; task < p.ntasks; task += gridDim.x)
+        for (int64_t task = t0 + blockIdx.x; task < p.ntasks && (int)threadIdx.x < ppc; task += gridDim.x)
             p.slot_k[(task - p.task_begin) * ppc + threadIdx.x] = -1;
     }
 }
@@ -1521,6 +1724,8 @@ static cudaError_t set_smem_attr_all()
     if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPaired16, kMaxFoldWarps>();
     if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPacked64, 4>();
     if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutPacked64, kMaxFoldWarps>();
+    if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutRed32, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<MODE, POW2, kLayoutRed32, kMaxRedWarps>();
     return e;
 }
 
@@ -1533,6 +1738,8 @@ int fold_register_kernels()
     if (e == cudaSuccess) e = set_smem_attr<kModeSearch, false, kLayoutPacked64, 4>();
     if (e == cudaSuccess) e = set_smem_attr<kModeSearch, true, kLayoutPaired16, 4>();
     if (e == cudaSuccess) e = set_smem_attr<kModeSearch, false, kLayoutPaired16, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, true, kLayoutRed32, kMaxRedWarps>();
+    if (e == cudaSuccess) e = set_smem_attr<kModeSearch, false, kLayoutRed32, kMaxRedWarps>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, true>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeFold, false>();
     if (e == cudaSuccess) e = set_smem_attr_all<kModeBox, true>();
@@ -1543,14 +1750,13 @@ int fold_register_kernels()
 size_t fold_smem_bytes(int nbins, int warps, int layout, int tile)
 {
     const size_t nb2 = (size_t)((nbins + 1) & ~1);
-    const size_t per_warp = layout == kLayoutPacked64 ? (size_t)32 * nbins * 8
-                                                      : (size_t)32 * (nbins * 4 + nb2 * 2);
+    const size_t per_warp = layout == kLayoutPaired16 ? (size_t)32 * (nbins * 4 + nb2 * 2) : (size_t)32 * nbins * 8;
     return 128 + (size_t)2 * tile * 12 + 2 * (tile / 16) + (size_t)warps * per_warp;
 }
 
 int fold_max_warps(int nbins, int layout, int tile)
 {
-    int w = kMaxFoldWarps;
+    int w = layout == kLayoutRed32 ? kMaxRedWarps : kMaxFoldWarps;
     while (w > 1 && fold_smem_bytes(nbins, w, layout, tile) > kSmemLimit - 1024) --w;
     return fold_smem_bytes(nbins, w, layout, tile) <= kSmemLimit - 1024 ? w : 0;
 }
@@ -1568,23 +1774,28 @@ static int occupancy_of(int threads, size_t smem)
     return n;
 }
 
-int search_blocks_per_sm(int nbins, int warps, int layout, int tile)
+int search_blocks_per_sm(int nbins, int warps, int layout, int tile, int streams)
 {
-    const size_t smem = search_smem_bytes(nbins, warps, layout, tile);
+    const size_t smem = search_smem_bytes(nbins, warps, layout, tile, streams);
     if (smem == 0) return 0;
-    const int threads = 32 * (warps + 1);
+    const int threads = 32 * (warps * streams + 1);
+    if (layout == kLayoutRed32) return occupancy_of<kModeSearch, true, kLayoutRed32, kMaxRedWarps>(threads, smem);
     return layout == kLayoutPacked64 ? occupancy_of<kModeSearch, true, kLayoutPacked64, 4>(threads, smem)
                                      : occupancy_of<kModeSearch, true, kLayoutPaired16, 4>(threads, smem);
 }
 
-int fold_blocks_per_sm(int nbins, int warps, int layout, int tile)
+int fold_blocks_per_sm(int nbins, int warps, int layout, int tile, int streams)
 {
     const size_t smem = fold_smem_bytes(nbins, warps, layout, tile);
     if (smem > kSmemLimit - 1024) return 0;
-    const int threads = 32 * warps;
+    if (streams > 1 && (layout != kLayoutRed32 || warps * streams > kMaxRedWarps)) return 0;
+    const int threads = 32 * warps * streams;
     if (layout == kLayoutPacked64)
         return warps <= 4 ? occupancy_of<kModeFold, true, kLayoutPacked64, 4>(threads, smem)
                           : occupancy_of<kModeFold, true, kLayoutPacked64, kMaxFoldWarps>(threads, smem);
+    if (layout == kLayoutRed32)
+        return warps * streams <= 4 ? occupancy_of<kModeFold, true, kLayoutRed32, 4>(threads, smem)
+                                    : occupancy_of<kModeFold, true, kLayoutRed32, kMaxRedWarps>(threads, smem);
     return warps <= 4 ? occupancy_of<kModeFold, true, kLayoutPaired16, 4>(threads, smem)
                       : occupancy_of<kModeFold, true, kLayoutPaired16, kMaxFoldWarps>(threads, smem);
 }
@@ -1597,35 +1808,44 @@ static void launch_variant(const FoldParams &p, int grid, int threads, size_t sm
     if (p.layout == kLayoutPacked64) {
         if (p.warps <= 4) fold_kernel<MODE, POW2, kLayoutPacked64, 4><<<grid, threads, smem, st>>>(p);
         else fold_kernel<MODE, POW2, kLayoutPacked64, kMaxFoldWarps><<<grid, threads, smem, st>>>(p);
+    } else if (p.layout == kLayoutRed32) {
+        if (threads <= 128) fold_kernel<MODE, POW2, kLayoutRed32, 4><<<grid, threads, smem, st>>>(p);
+        else fold_kernel<MODE, POW2, kLayoutRed32, kMaxRedWarps><<<grid, threads, smem, st>>>(p);
     } else {
         if (p.warps <= 4) fold_kernel<MODE, POW2, kLayoutPaired16, 4><<<grid, threads, smem, st>>>(p);
         else fold_kernel<MODE, POW2, kLayoutPaired16, kMaxFoldWarps><<<grid, threads, smem, st>>>(p);
     }
 }
 
-size_t search_smem_bytes(int nbins, int warps, int layout, int tile)
+size_t search_smem_bytes(int nbins, int warps, int layout, int tile, int streams)
 {
-    if (warps + 1 > 4) return 0;
+    if (streams < 1 || (streams > 1 && layout != kLayoutRed32)) return 0;
+    if (warps * streams + 1 > (layout == kLayoutRed32 ? kMaxRedWarps : 4)) return 0;
     const size_t off = (fold_smem_bytes(nbins, warps, layout, tile) + 15) & ~(size_t)15;
     const size_t bytes = off + (size_t)(warps + 1) * coop_pairs(nbins) * sizeof(float2);
     return bytes <= kSmemLimit - 1024 ? bytes : 0;
 }
 
-// One fold block of `warps` warps plus the scorer warp (the 128-thread instantiation).
+// One fold block of `warps` warps plus the scorer warp (the 128-thread instantiation, or
+// up to kMaxRedWarps warps for the reduction layout).
 template <bool POW2>
 static void launch_search_variant(const FoldParams &p, int grid, size_t smem, cudaStream_t st)
 {
-    const int threads = 32 * (p.warps + 1);
+    const int threads = 32 * (p.warps * p.streams + 1);
     if (p.layout == kLayoutPacked64) fold_kernel<kModeSearch, POW2, kLayoutPacked64, 4><<<grid, threads, smem, st>>>(p);
+    else if (p.layout == kLayoutRed32)
+        fold_kernel<kModeSearch, POW2, kLayoutRed32, kMaxRedWarps><<<grid, threads, smem, st>>>(p);
     else fold_kernel<kModeSearch, POW2, kLayoutPaired16, 4><<<grid, threads, smem, st>>>(p);
 }
 
 cudaError_t launch_fold(const FoldParams &p_in, int mode, int grid, cudaStream_t st)
 {
-    const FoldParams &p = p_in;
+    FoldParams p = p_in;
+    if (mode == kModeBox) p.streams = 1;  // the box epilogue reads a whole profile per warp
     if (p.tile != 512 && p.tile != 1024 && p.tile != 2048) return cudaErrorInvalidValue;
+    if (p.streams < 1 || (p.streams > 1 && p.layout != kLayoutRed32)) return cudaErrorInvalidValue;
     if (mode == kModeSearch) {
-        const size_t smem = search_smem_bytes(p.nbins, p.warps, p.layout, p.tile);
+        const size_t smem = search_smem_bytes(p.nbins, p.warps, p.layout, p.tile, p.streams);
         if (smem == 0 || !p.sums || !p.counts || !p.slot_k || !p.score) return cudaErrorInvalidValue;
         FoldParams q = p;
         q.stage_off = (fold_smem_bytes(p.nbins, p.warps, p.layout, p.tile) + 15) & ~(size_t)15;
@@ -1634,8 +1854,9 @@ cudaError_t launch_fold(const FoldParams &p_in, int mode, int grid, cudaStream_t
         return cudaGetLastError();
     }
     const size_t smem = fold_smem_bytes(p.nbins, p.warps, p.layout, p.tile);
-    if (smem > kSmemLimit - 1024) return cudaErrorInvalidValue;
-    const int threads = 32 * p.warps;
+    if (smem > kSmemLimit - 1024 || (p.layout == kLayoutRed32 && p.warps * p.streams > kMaxRedWarps))
+        return cudaErrorInvalidValue;
+    const int threads = 32 * p.warps * p.streams;
     const bool pow2 = p.shift >= 0;
     if (mode == kModeFold) {
         if (pow2) launch_variant<kModeFold, true>(p, grid, threads, smem, st);

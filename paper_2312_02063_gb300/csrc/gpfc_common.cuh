@@ -100,6 +100,7 @@ __device__ __forceinline__ float4 lds_f32x4(uint32_t a)
     return v;
 }
 __device__ __forceinline__ void sts_f32(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v)); }
 __device__ __forceinline__ void sts_u16(uint32_t a, uint32_t v)
 {
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v));

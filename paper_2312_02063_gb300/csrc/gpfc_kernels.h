@@ -18,6 +18,8 @@ constexpr int kTile = 1024;            // default light-curve samples per bulk-c
 constexpr int kMaxTile = 2048;         // tiles are 512, 1024 or 2048 samples
 constexpr int kMaxFoldWarps = 16;      // warps per fold block (32 periods each)
 constexpr int kMaxNbinsLane = 1024;    // largest nbins of the lane-private fold
+constexpr int kMaxRedWarps = 12;       // warps of a kLayoutRed32 block (fold warps of all
+                                       // streams, plus the scorer warp of a search block)
 constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block (227 KB); kernels ask
                                        // for at most kSmemLimit - 1024 dynamic bytes
 
@@ -29,6 +31,8 @@ struct StarStats {
     float sigma;    // population std of the flux (FP64 reduction, rounded)
     int32_t n;      // samples of the star
     long long dtau0;  // smallest positive step between consecutive quantised times (0: none)
+    int32_t qexp;     // fixed-point flux: xq = rint(x 2^qexp), |xq| <= (2^31 - 1) / chunk
+    int32_t pad;
 };
 
 // Samples of all stars, quantised, at 16-byte aligned per-star offsets.
@@ -36,6 +40,7 @@ struct SampleScratch {
     uint32_t *tau_lo;   // low 32 bits of tau
     int32_t *tau_hi;    // high 32 bits of tau
     float *x;           // flux - f_ref (FP32)
+    int32_t *xq;        // rint(x 2^qexp): the fixed-point flux of the reduction layout
     uint8_t *flags;     // one byte per 16 samples: regular-cadence group (see prep)
 };
 
@@ -45,7 +50,10 @@ struct SampleScratch {
 enum FoldMode : int { kModeFold = 0, kModeBox = 1, kModeSearch = 3 };
 
 // Shared-memory layout of the lane-private bins (see fold.cu).
-enum FoldLayout : int { kLayoutPaired16 = 1, kLayoutPacked64 = 2 };
+// kLayoutRed32: 8 bytes per bin (a 32-bit sum word and a 32-bit count word), accumulated
+// as fixed-point integer sums and counts by no-return shared reductions
+// (red.shared.add.u32).
+enum FoldLayout : int { kLayoutPaired16 = 1, kLayoutPacked64 = 2, kLayoutRed32 = 3 };
 
 struct FoldParams {
     SampleScratch smp;
@@ -62,11 +70,14 @@ struct FoldParams {
     const StarStats *stats;
     int nbins;
     int shift;                 // 32 - log2(nbins) if nbins is a power of two, else -1
-    int warps;                 // warps per block; periods per block = 32 * warps
+    int warps;                 // period groups per block; periods per block = 32 * warps
+    int streams;               // fold warps per period group (kLayoutRed32; else 1): warp
+                               // w folds group w % warps over every streams-th sample group
     int chunk;                 // samples per shared-memory chunk: multiple of 16, <= 65520
     int layout;                // FoldLayout
     int tile;                  // samples per bulk-copy tile: 512, 1024 or 2048
-    float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation)
+    float2 *ws_sc;             // [grid][nbins][32*warps] Kahan (sum, compensation), or
+                               // the int64 fixed-point sums of kLayoutRed32
     uint32_t *ws_cnt;          // [grid][nbins][32*warps] counts
     // kModeFold outputs ([global period][nbins], or [slot][nbins] when slot_k is set);
     // kModeSearch uses sums, counts and slot_k as its ring, [grid][2][32 * warps] rows
@@ -116,16 +127,17 @@ cudaError_t launch_box_coop(const BoxCoopParams &p, int num_sms, cudaStream_t st
 
 size_t fold_smem_bytes(int nbins, int warps, int layout, int tile = kTile);
 int fold_max_warps(int nbins, int layout, int tile = kTile);
-int fold_blocks_per_sm(int nbins, int warps, int layout, int tile);
+int fold_blocks_per_sm(int nbins, int warps, int layout, int tile, int streams = 1);
 int fold_register_kernels();
 
 cudaError_t launch_prep(const double *times, const float *flux, const int64_t *lc_off, int64_t n,
                         int nstars, int64_t max_len, const double *t0s, double t0, SampleScratch smp,
-                        double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st);
+                        double *partial, int G, StarStats *stats, uint32_t *status, cudaStream_t st,
+                        int chunk = 65520);
 cudaError_t launch_fold(const FoldParams &p, int mode, int grid, cudaStream_t st);
 // Shared memory of a kModeSearch block (0 if it does not fit or warps + 1 > 4).
-size_t search_smem_bytes(int nbins, int warps, int layout, int tile);
-int search_blocks_per_sm(int nbins, int warps, int layout, int tile);
+size_t search_smem_bytes(int nbins, int warps, int layout, int tile, int streams = 1);
+int search_blocks_per_sm(int nbins, int warps, int layout, int tile, int streams = 1);
 cudaError_t launch_argmax(const float *score, int64_t np, unsigned long long *key, cudaStream_t st);
 cudaError_t launch_batch_plan(const int64_t *lc_off, const int64_t *grid_off, int nstars, int64_t n_total,
                               int64_t np_total, int ppc, int64_t *lc_s, int64_t *grid_s, int64_t *task_off,

@@ -4,10 +4,12 @@ cache flush between calls), for profiling with external tools such as Nsight Com
   python -m paper_2312_02063_gb300.run_search --what box --n-periods 250000 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what cnn --n-periods 250000 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what cnn-score --n-profiles 16384 --repeat 5
+  python -m paper_2312_02063_gb300.run_search --what fold --n-periods 32768 --layout 3 --warps 4
 
 box: fold + box-SNR search (one kernel, widths 1..108); cnn: fold + CNN search; cnn-score:
-CNN scoring of device-generated profiles. Prints the mean CUDA-event time of the repeats
-after the first.
+CNN scoring of device-generated profiles; fold: the fold alone (means and counts of every
+period). --layout, --warps, --chunk and --tile set the fold's launch config (0: automatic).
+Prints the mean CUDA-event time of the repeats after the first.
 """
 from __future__ import annotations
 
@@ -16,20 +18,24 @@ import math
 
 import torch
 
-from . import (BOX_FUSED, SCORER_BOX, SCORER_CNN, Context, gpfc_score_cnn, gpfc_search, gpfc_synth_profiles)
+from . import (BOX_FUSED, SCORER_BOX, SCORER_CNN, Context, gpfc_fold, gpfc_score_cnn, gpfc_search,
+               gpfc_synth_profiles)
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["box", "cnn", "cnn-score"], default="box")
+    ap.add_argument("--what", choices=["box", "cnn", "cnn-score", "fold"], default="box")
     ap.add_argument("--n-periods", type=int, default=250_000)
     ap.add_argument("--n-profiles", type=int, default=16_384)
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--seed", type=int, default=20232204)
+    for k in ("layout", "warps", "chunk", "tile"):
+        ap.add_argument("--" + k, type=int, default=0)
     a = ap.parse_args()
     import lcsynth  # the synthetic-input generators
     from .train import init_weights
     ctx = Context(0)
+    ctx.set_fold_config(warps=a.warps, layout=a.layout, chunk=a.chunk, tile=a.tile)
     dev = ctx.device
     w = init_weights(dev, 1)
     if a.what == "cnn-score":
@@ -45,10 +51,14 @@ def main():
         f = torch.from_numpy(lc.flux).to(dev)
         p = torch.from_numpy(periods).to(dev)
         score = torch.empty(a.n_periods, dtype=torch.float32, device=dev)
+        folded = torch.empty(a.n_periods, 256, dtype=torch.float32, device=dev)
+        counts = torch.empty(a.n_periods, 256, dtype=torch.int32, device=dev)
         ctx.set_box_path(BOX_FUSED)
 
         def call():
-            if a.what == "box":
+            if a.what == "fold":
+                gpfc_fold(ctx, t, f, p, 256, lc.t0, folded=folded, counts=counts)
+            elif a.what == "box":
                 gpfc_search(ctx, t, f, p, 256, lc.t0, SCORER_BOX, 1, int(math.ceil(0.42 * 256)), 0.0, score)
             else:
                 gpfc_search(ctx, t, f, p, 256, lc.t0, SCORER_CNN, score=score, weights=w)
@@ -62,7 +72,8 @@ def main():
         e1.record()
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(f"{a.what}: {sum(ms) / len(ms):.3f} ms per call (mean of {len(ms)}, steady state)")
+    print(f"{a.what}: {sum(ms) / len(ms):.3f} ms per call (mean of {len(ms)}, steady state); "
+          f"plan {ctx.last_fold_plan()}")
     ctx.close()
 
 

@@ -240,7 +240,7 @@ def test_autotune_picks_a_valid_config_with_identical_results(ctx):
     ctx.sync()
     ctx.set_autotune(1)
     cfg = g.gpfc_autotune(ctx, t, f, p, 256, g.SCORER_BOX, 1, 108, 0.0)
-    assert cfg["tile"] in (512, 1024, 2048) and cfg["layout"] in (1, 2) and cfg["blocks_per_sm"] >= 1
+    assert cfg["tile"] in (512, 1024, 2048) and cfg["layout"] in (1, 2, 3) and cfg["blocks_per_sm"] >= 1
     assert 1 <= cfg["warps"] <= ctx.fold_max_warps(256, cfg["layout"]) or cfg["tile"] != 1024
     sc, _, _ = g.gpfc_search(ctx, t, f, p, 256, lc.t0, g.SCORER_BOX, 1, 108, 0.0)
     ctx.sync()

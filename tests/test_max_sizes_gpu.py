@@ -1,7 +1,8 @@
 """GPU parity at the boundary's largest sizes: a light curve of 2^24 samples (the most a
 star may have) and a search over 2^22 periods (4,194,304; scores only, so the outputs stay
 at 16 MB). Checked against the FP64 oracle on sampled periods, with the fold's and the
-box-SNR's tolerances (counts bit-exact, means 1e-6 relative, box-SNR 1e-5 relative).
+box-SNR's tolerances (counts bit-exact, means 1e-6 relative, box-SNR 1e-5 relative plus
+the fixed-point allowance of tolerances.py).
 """
 import numpy as np
 import pytest
@@ -9,6 +10,7 @@ import torch
 
 import lcsynth
 import oracle
+from tolerances import box_atol, fixed_point_unit
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +54,8 @@ def test_fold_and_search_of_2_pow_24_samples(ctx):
     sc = score.cpu().numpy().astype(np.float64)
     fin = np.isfinite(sc_o)
     np.testing.assert_array_equal(np.isfinite(sc), fin)
-    assert np.all(np.abs(sc[fin] - sc_o[fin]) <= BOX_RTOL * np.maximum(np.abs(sc_o[fin]), 1.0))
+    tol = BOX_RTOL * np.maximum(np.abs(sc_o[fin]), 1.0) + box_atol(fixed_point_unit(flux), 1e-3)
+    assert np.all(np.abs(sc[fin] - sc_o[fin]) <= tol)
     assert int(bi.item()) == oracle.argmax(score.cpu().numpy())
 
 

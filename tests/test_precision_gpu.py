@@ -1,7 +1,9 @@
-"""GPU parity where the FP32 partial sums of the fold face their worst cancellation
-(Sec. 2.3 step 3): a full-length light curve with white noise of 1e-2, red noise of 2e-3
-and a 1%-deep transit, so the centred sums swing far more than on the quiet Kepler-like
-star. Counts bit-exact, means within 1e-6 relative, box-SNR within 1e-5 relative, through
+"""GPU parity on a loud star (Sec. 2.3 step 3): a full-length light curve with white noise
+of 1e-2, red noise of 2e-3 and a 1%-deep transit. The centred sums swing far more than on
+the quiet Kepler-like star (the worst cancellation for FP32 partial sums), and the flux
+range makes the fixed-point unit of the default 256-bin fold coarser than the float32
+flux grid, so its rounding is real. Counts bit-exact, means within 1e-6 relative,
+box-SNR within 1e-5 relative plus the fixed-point allowance of tolerances.py, through
 gpfc_fold and through every box-search path at 256 bins.
 """
 import numpy as np
@@ -10,6 +12,7 @@ import torch
 
 import lcsynth
 import oracle
+from tolerances import box_atol, fixed_point_unit
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +73,9 @@ def test_loud_star_box_snr_matches_oracle(ctx, loud_star, path):
     finally:
         ctx.set_box_path(g.BOX_AUTO)
     sc = sc.cpu().numpy().astype(np.float64)
-    rel = np.abs(sc - sc_o) / np.maximum(np.abs(sc_o), 1.0)
-    print(f"loud star, {path} box search: max relative box-SNR error {rel.max():.3e}")
-    assert rel.max() <= BOX_RTOL
+    err = np.abs(sc - sc_o)
+    tol = BOX_RTOL * np.maximum(np.abs(sc_o), 1.0) + box_atol(fixed_point_unit(lc.flux), sigma)
+    print(f"loud star, {path} box search: max box-SNR error {err.max():.3e}, "
+          f"largest fraction of its tolerance {np.max(err / tol):.3f}")
+    assert np.all(err <= tol)
     assert int(bi.item()) == oracle.argmax(sc.astype(np.float32))
