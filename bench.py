@@ -35,11 +35,11 @@ UNIT = "sample·period folds/s"
 NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
-SM_FOLD_UPDATES_PER_CLK = 8           # the pipe model: 128 B/clk / (8 B read + 8 B written)
-# DRAM bytes (read + write) of one whole 250,000-period one-kernel search (fold + box-SNR) of
-# the same light curve in steady state (no cache flush, one ncu pass):
-# profiles/dram_traffic_steady_state_kepler62835.md
-SEARCH_DRAM_BYTES_PER_PERIOD = (219.01e6 + 960.84e6) / 250000
+SM_FOLD_UPDATES_PER_CLK = 16          # the pipe model: 128 B/clk / (4 B + 4 B of reductions)
+# DRAM bytes (read + write) of the fold kernel's launches of one 250,000-period search of the
+# same light curve in steady state (no cache flush, one ncu pass), per period; None until
+# taken for the current kernel
+SEARCH_DRAM_BYTES_PER_PERIOD = None
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -488,7 +488,9 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ctx.set_box_path(g.BOX_FUSED)  # fold and box-SNR in one kernel (the default for one star)
+    # the default path: from 256 bins the reduction fold (exact fixed-point sums, twelve
+    # warps per SM) pipelined with the warp-per-profile box-SNR scorer on two side streams
+    ctx.set_box_path(g.BOX_AUTO)
 
     def step():
         g.gpfc_search(ctx, t_d, f_d, p_d, NBINS, lc.t0, g.SCORER_BOX, 1, W_MAX, 0.0, score, bi, bs)
@@ -565,16 +567,19 @@ def run_gpu(args, rank, world, local_rank):
         smax = float(peaks.get("sm_max_mhz", 2070.0))
         sms = ctx.num_sms
         model_gups = sms * SM_FOLD_UPDATES_PER_CLK * smax * 1e6 / 1e9
-        # the fold's binding pipe, measured here: lane-private 8-byte shared-memory
-        # read-modify-writes (the fold's bin record) at full occupancy, and at the fold's own
-        # footprint (256 bins x 3 warps per SM)
+        # the fold's binding pipe, measured here: lane-private shared-memory updates of the
+        # fold's 8-byte bin record at full occupancy (16 warps x 32 bins per SM), as two
+        # no-return reductions (the default fold's record) and as a 64-bit read-modify-write
+        # (the FP32 layout's record), and both at the fold's own footprint (256 bins x 3
+        # period groups per SM)
         probe = {}
-        for key, cfg in (("rmw8_full", (8, 32, 16, 1)), ("rmw8_fold_footprint", (8, 256, 3, 1)),
-                         ("rmw4_full", (4, 32, 16, 1))):
-            ups, upc = g.gpfc_probe_smem_rmw(*cfg, iters=20000, op=0)
+        for key, cfg, op in (("red8_full", (8, 32, 16, 1), 1), ("red8_fold_footprint", (8, 256, 3, 1), 1),
+                             ("rmw8_full", (8, 32, 16, 1), 0), ("rmw8_fold_footprint", (8, 256, 3, 1), 0)):
+            ups, upc = g.gpfc_probe_smem_rmw(*cfg, iters=20000, op=op)
             probe[key] = {"gupdates_per_s": ups / 1e9, "updates_per_clk_sm": upc,
-                          "config": f"{cfg[0]}-byte words, {cfg[1]} bins x {cfg[2]} warps per SM"}
-        peak_gups = probe["rmw8_full"]["gupdates_per_s"]
+                          "config": f"{cfg[0]}-byte record, {'two 32-bit reductions' if op else 'load + store'}, "
+                                    f"{cfg[1]} bins x {cfg[2]} warps per SM"}
+        peak_gups = probe["red8_full"]["gupdates_per_s"]
         kmean = statistics.mean(kernel_ms)
         # the search kernel's own launch (fold + box-SNR): all n * N_PERIODS updates of a step
         # over its duration
@@ -596,7 +601,8 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
-            "roofline": {"bound": "smem", "kernel": "fold_kernel<search> (fold + box-SNR)", "achieved": achieved,
+            "roofline": {"bound": "smem", "kernel": "fold_kernel (reduction layout, 3 period groups x 4 streams)",
+                         "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                          "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None
                          else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS,
@@ -604,19 +610,19 @@ def run_gpu(args, rank, world, local_rank):
                                           "state (no cache flush), scaled by periods",
                          "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
                          "search_ms": kmean,
-                         "peak_basis": "measured in this run by gpfc_probe_smem_rmw: lane-private 8-byte "
-                                       "(FP32 sum + 32-bit count) shared-memory read-modify-writes, 16 warps x "
-                                       f"32 bins per SM, {probe['rmw8_full']['updates_per_clk_sm']:.2f} "
-                                       "updates/clk/SM",
+                         "peak_basis": "measured in this run by gpfc_probe_smem_rmw: lane-private updates of "
+                                       "the fold's 8-byte record (32-bit sum and count words) by two "
+                                       "red.shared.add.u32, 16 warps x 32 bins per SM, "
+                                       f"{probe['red8_full']['updates_per_clk_sm']:.2f} updates/clk/SM",
                          "peak_model": model_gups,
                          "peak_model_basis": f"{sms} SMs x {SM_FOLD_UPDATES_PER_CLK} updates/clk (128 B/clk over "
-                                             f"16 B per update) x {smax:.0f} MHz ({src} sm_max_mhz)",
+                                             f"8 B of reductions per update) x {smax:.0f} MHz ({src} sm_max_mhz)",
                          "probe": probe},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
-            # per step: 4 prep kernels, the search kernel, the argmax
-            "gpu_launches": (5 + launches) * args.steps,
+            # per step: 4 prep kernels, each fold launch and its box-SNR launch, the argmax
+            "gpu_launches": (5 + 2 * launches) * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }

@@ -553,8 +553,10 @@ int gpfc_set_graph(gpfc_ctx *ctx, int enable);
  * period; this call times a kernel that does only that, with each lane's records laid out
  * [bin][lane] as the fold keeps them, eight distinct bins updated per iteration, and
  * reports the rate.
- *  - word_bytes 8: FP32 sum + 32-bit count packed in 64 bits (op 0: one 64-bit load and
- *    store per update; op 1: one red.shared.add.u64); 6: FP32 sum word plus a 16-bit
+ *  - word_bytes 8: op 0: FP32 sum + 32-bit count packed in 64 bits, one 64-bit load and
+ *    store per update (fold layout 2); op 1: a 32-bit sum word and a 32-bit count word
+ *    128 bytes apart (256 bytes per bin of a warp), two red.shared.add.u32 per update
+ *    (fold layout 3); 6: FP32 sum word plus a 16-bit
  *    count, two counts per 32-bit word (op 0: 32-bit and 16-bit loads and stores; op 1:
  *    red.shared.add.f32 to the sum and red.shared.add.u32 to the paired count); 4: one
  *    32-bit word (op 0: load and store; op 1: red.shared.add.u32).

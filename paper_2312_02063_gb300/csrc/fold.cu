@@ -659,54 +659,93 @@ __device__ __forceinline__ void fold_segment(uint32_t stl, uint32_t sth, uint32_
                                nbins, shift);
 }
 
+// Tile data of one 16-sample group for the reduction fold: tau low words, fixed-point
+// flux, and the tau high word of the group's first sample.
+struct RedGroup {
+    uint4 a[4];
+    uint4 x[4];
+    uint32_t th;
+};
+
+__device__ __forceinline__ void load_red_group(uint32_t stl, uint32_t sth, uint32_t sxq, int g, RedGroup &G)
+{
+    const uint32_t o = 64u * (uint32_t)g;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        G.a[q] = lds_u32x4(stl + o + 16u * q);
+        G.x[q] = lds_u32x4(sxq + o + 16u * q);
+    }
+    G.th = lds_u32(sth + o);
+}
+
+// Bins of a group. A group flagged regular by the prep pass has one tau high word (th),
+// so th * F_lo is formed once; the others read every sample's high word.
+template <bool POW2>
+__device__ __forceinline__ void red_group_bins(const RedGroup &G, bool regular, uint32_t sth, int g, uint32_t Fl,
+                                               uint32_t Fh, uint32_t nbins, int shift, uint32_t (&b)[16])
+{
+    if (regular) {
+        const uint32_t thF = G.th * Fl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            b[4 * q + 0] = phase_bin_th<POW2>(G.a[q].x, thF, Fl, Fh, nbins, shift);
+            b[4 * q + 1] = phase_bin_th<POW2>(G.a[q].y, thF, Fl, Fh, nbins, shift);
+            b[4 * q + 2] = phase_bin_th<POW2>(G.a[q].z, thF, Fl, Fh, nbins, shift);
+            b[4 * q + 3] = phase_bin_th<POW2>(G.a[q].w, thF, Fl, Fh, nbins, shift);
+        }
+    } else {
+        const uint32_t o = 64u * (uint32_t)g;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 h = lds_u32x4(sth + o + 16u * q);
+            b[4 * q + 0] = phase_bin<POW2>(G.a[q].x, h.x, Fl, Fh, nbins, shift);
+            b[4 * q + 1] = phase_bin<POW2>(G.a[q].y, h.y, Fl, Fh, nbins, shift);
+            b[4 * q + 2] = phase_bin<POW2>(G.a[q].z, h.z, Fl, Fh, nbins, shift);
+            b[4 * q + 3] = phase_bin<POW2>(G.a[q].w, h.w, Fl, Fh, nbins, shift);
+        }
+    }
+}
+
+__device__ __forceinline__ void red_group_add(const StoreRed32 &st, const uint32_t (&b)[16], const RedGroup &G)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        st.add(b[4 * q + 0], (int32_t)G.x[q].x);
+        st.add(b[4 * q + 1], (int32_t)G.x[q].y);
+        st.add(b[4 * q + 2], (int32_t)G.x[q].z);
+        st.add(b[4 * q + 3], (int32_t)G.x[q].w);
+    }
+}
+
 // kLayoutRed32: fold this stream's share of nvalid samples (a segment starting on a
 // 16-sample boundary of the tile) by reductions: the 16-sample groups g with
 // g mod nstreams = stream, and the tail after the last whole group if its turn falls on this
-// stream. Groups flagged regular by the prep pass read one tau high word and form
-// th * F_lo once; the others read every sample's high word. sxq addresses the fixed-point
-// flux of the tile.
+// stream. Two-stage pipeline: the tile data of the stream's next group is loaded while
+// the current group's reductions issue (the loop body holds two stages with the register
+// roles swapped, so nothing is copied). sxq addresses the fixed-point flux of the tile.
 template <bool POW2>
 __device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sth, uint32_t sxq, unsigned long long fmask,
                                                  int nvalid, const StoreRed32 &st, uint32_t Fl, uint32_t Fh,
                                                  uint32_t nbins, int shift, int stream, int nstreams)
 {
     const int ng = nvalid >> 4;
-#pragma unroll 1
-    for (int g = stream; g < ng; g += nstreams) {
-        const uint32_t o = 64u * (uint32_t)g;
-        uint4 a[4], xv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a[q] = lds_u32x4(stl + o + 16u * q);
-            xv[q] = lds_u32x4(sxq + o + 16u * q);
-        }
+    // one stage: bins of group g (data in C), load group g + nstreams into N, add group g
+    auto stage = [&](const RedGroup &C, RedGroup &N, int g) {
         uint32_t b[16];
-        if ((fmask >> g) & 1ull) {
-            const uint32_t thF = lds_u32(sth + o) * Fl;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                b[4 * q + 0] = phase_bin_th<POW2>(a[q].x, thF, Fl, Fh, nbins, shift);
-                b[4 * q + 1] = phase_bin_th<POW2>(a[q].y, thF, Fl, Fh, nbins, shift);
-                b[4 * q + 2] = phase_bin_th<POW2>(a[q].z, thF, Fl, Fh, nbins, shift);
-                b[4 * q + 3] = phase_bin_th<POW2>(a[q].w, thF, Fl, Fh, nbins, shift);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 h = lds_u32x4(sth + o + 16u * q);
-                b[4 * q + 0] = phase_bin<POW2>(a[q].x, h.x, Fl, Fh, nbins, shift);
-                b[4 * q + 1] = phase_bin<POW2>(a[q].y, h.y, Fl, Fh, nbins, shift);
-                b[4 * q + 2] = phase_bin<POW2>(a[q].z, h.z, Fl, Fh, nbins, shift);
-                b[4 * q + 3] = phase_bin<POW2>(a[q].w, h.w, Fl, Fh, nbins, shift);
-            }
+        red_group_bins<POW2>(C, (fmask >> g) & 1ull, sth, g, Fl, Fh, nbins, shift, b);
+        if (g + nstreams < ng) load_red_group(stl, sth, sxq, g + nstreams, N);
+        red_group_add(st, b, C);
+    };
+    int g = stream;
+    if (g < ng) {
+        RedGroup G0, G1;
+        load_red_group(stl, sth, sxq, g, G0);
+#pragma unroll 1
+        for (; g + nstreams < ng; g += 2 * nstreams) {
+            stage(G0, G1, g);
+            stage(G1, G0, g + nstreams);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            st.add(b[4 * q + 0], (int32_t)xv[q].x);
-            st.add(b[4 * q + 1], (int32_t)xv[q].y);
-            st.add(b[4 * q + 2], (int32_t)xv[q].z);
-            st.add(b[4 * q + 3], (int32_t)xv[q].w);
-        }
+        if (g < ng) stage(G0, G1, g);
     }
     if (ng % nstreams == stream) {
         for (int i = 16 * ng; i < nvalid; ++i) {

@@ -21,8 +21,9 @@ namespace {
 // 16-bit count, two per 32-bit word [bin/2][lane] (load and store of each). LDST4: one
 // 32-bit word. RED6: the 6-byte record updated by no-return shared reductions
 // (red.shared.add.f32 to the sum, red.shared.add.u32 of 1 << 16 (bin & 1) to the paired
-// count). RED4: red.shared.add.u32 to a 32-bit word. RED8: red.shared.add.u64 to a 64-bit
-// word.
+// count). RED4: red.shared.add.u32 to a 32-bit word. RED8: the reduction fold's record,
+// 256 bytes per bin of a warp ([bin][sum row, count row][lane], 32-bit words), updated by
+// two red.shared.add.u32 (sum, and count at +128 bytes).
 enum ProbeKind { kLdSt8, kLdSt6, kLdSt4, kRed6, kRed4, kRed8 };
 
 __host__ __device__ constexpr uint32_t probe_bytes_x2(int k)  // twice the bytes per bin
@@ -36,12 +37,15 @@ __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *
     extern __shared__ __align__(16) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool kSix = KIND == kLdSt6 || KIND == kRed6;
-    constexpr uint32_t kW = kSix ? 4u : probe_bytes_x2(KIND) / 2u;  // bytes of the word addressed per bin
+    // bytes of the word addressed per bin and lane (the 8-byte reduction record is two
+    // 4-byte rows)
+    constexpr uint32_t kW = (kSix || KIND == kRed8) ? 4u : probe_bytes_x2(KIND) / 2u;
+    constexpr uint32_t kBinStride = KIND == kRed8 ? 256u : 32u * kW;  // bytes per bin of a warp
     const uint32_t wbase = smem_u32(sm) + (uint32_t)warp * (uint32_t)nbins * 32u * probe_bytes_x2(KIND) / 2u;
     const uint32_t base = wbase + (uint32_t)lane * kW;
     const uint32_t cbase = wbase + (uint32_t)nbins * 128u + (uint32_t)lane * 4u;  // 6-byte records: counts
     const uint32_t mask = (uint32_t)nbins - 1u;
-    const uint32_t words = kSix ? nbins + nbins / 2 : nbins;
+    const uint32_t words = kSix ? nbins + nbins / 2 : (KIND == kRed8 ? 2 * nbins : nbins);
     for (uint32_t b = 0; b < words; ++b) {
         if (kW == 8) asm volatile("st.shared.v2.u32 [%0], {%1, %1};" ::"r"(base + b * 256u), "r"(0u));
         else asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + b * 128u), "r"(0u));
@@ -55,7 +59,7 @@ __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             bb[u] = (b + 37u * (uint32_t)u) & mask;
-            a[u] = base + bb[u] * 32u * kW;
+            a[u] = base + bb[u] * kBinStride;
         }
         if (KIND == kRed6) {
 #pragma unroll
@@ -69,8 +73,10 @@ __global__ void smem_rmw_probe_kernel(int nbins, int iters, unsigned long long *
             for (int u = 0; u < 8; ++u) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a[u]), "r"(3u) : "memory");
         } else if (KIND == kRed8) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a[u]), "l"(0x0000010000000003ull) : "memory");
+            for (int u = 0; u < 8; ++u) {
+                asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a[u]), "r"(3u) : "memory");
+                asm volatile("red.shared.add.u32 [%0+128], %1;" ::"r"(a[u]), "r"(1u) : "memory");
+            }
         } else if (KIND == kLdSt8) {
             uint32_t s[8], c[8];
 #pragma unroll

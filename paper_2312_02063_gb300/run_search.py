@@ -4,9 +4,9 @@ cache flush between calls), for profiling with external tools such as Nsight Com
   python -m paper_2312_02063_gb300.run_search --what box --n-periods 250000 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what cnn --n-periods 250000 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what cnn-score --n-profiles 16384 --repeat 5
-  python -m paper_2312_02063_gb300.run_search --what fold --n-periods 32768 --layout 3 --warps 4
+  python -m paper_2312_02063_gb300.run_search --what fold --n-periods 32768 --layout 2 --warps 3
 
-box: fold + box-SNR search (one kernel, widths 1..108); cnn: fold + CNN search; cnn-score:
+box: fold + box-SNR search (the default path, widths 1..108); cnn: fold + CNN search; cnn-score:
 CNN scoring of device-generated profiles; fold: the fold alone (means and counts of every
 period). --layout, --warps, --chunk and --tile set the fold's launch config (0: automatic).
 Prints the mean CUDA-event time of the repeats after the first.
@@ -18,7 +18,7 @@ import math
 
 import torch
 
-from . import (BOX_FUSED, SCORER_BOX, SCORER_CNN, Context, gpfc_fold, gpfc_score_cnn, gpfc_search,
+from . import (SCORER_BOX, SCORER_CNN, Context, gpfc_fold, gpfc_score_cnn, gpfc_search,
                gpfc_synth_profiles)
 
 
@@ -53,7 +53,6 @@ def main():
         score = torch.empty(a.n_periods, dtype=torch.float32, device=dev)
         folded = torch.empty(a.n_periods, 256, dtype=torch.float32, device=dev)
         counts = torch.empty(a.n_periods, 256, dtype=torch.int32, device=dev)
-        ctx.set_box_path(BOX_FUSED)
 
         def call():
             if a.what == "fold":
