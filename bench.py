@@ -36,10 +36,10 @@ NBINS = 256
 N_PERIODS = 250_000  # default; --n-periods changes it (small cases for profiling)
 W_MAX = int(math.ceil(0.42 * NBINS))  # 108: widths up to the longest injected duty cycle
 SM_FOLD_UPDATES_PER_CLK = 16          # the pipe model: 128 B/clk / (4 B + 4 B of reductions)
-# DRAM bytes (read + write) of the fold kernel's launches of one 250,000-period search of the
-# same light curve in steady state (no cache flush, one ncu pass), per period; None until
-# taken for the current kernel
-SEARCH_DRAM_BYTES_PER_PERIOD = None
+# DRAM bytes (read + write) of the fold kernel's 18 launches of one 250,000-period search of
+# the same light curve in steady state (no cache flush, one ncu pass), per period:
+# profiles/dram_traffic_steady_state_kepler62835.md
+SEARCH_DRAM_BYTES_PER_PERIOD = (0.09088e6 + 174.462208e6) / 250000
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -605,9 +605,10 @@ def run_gpu(args, rank, world, local_rank):
                          "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                          "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None
-                         else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS,
-                         "traffic_basis": "ncu dram__bytes_read+write of one 250,000-period search in steady "
-                                          "state (no cache flush), scaled by periods",
+                         else SEARCH_DRAM_BYTES_PER_PERIOD * N_PERIODS / launches,
+                         "traffic_basis": "per fold launch: ncu dram__bytes_read+write of the fold launches of "
+                                          "one 250,000-period search in steady state (no cache flush), scaled "
+                                          "by periods and divided by the launches of a step",
                          "kernel_ms": fold_step_ms / launches, "launches_per_step": launches,
                          "search_ms": kmean,
                          "peak_basis": "measured in this run by gpfc_probe_smem_rmw: lane-private updates of "

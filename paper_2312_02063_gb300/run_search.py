@@ -5,10 +5,12 @@ cache flush between calls), for profiling with external tools such as Nsight Com
   python -m paper_2312_02063_gb300.run_search --what cnn --n-periods 250000 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what cnn-score --n-profiles 16384 --repeat 5
   python -m paper_2312_02063_gb300.run_search --what fold --n-periods 32768 --layout 2 --warps 3
+  python -m paper_2312_02063_gb300.run_search --what probe
 
 box: fold + box-SNR search (the default path, widths 1..108); cnn: fold + CNN search; cnn-score:
 CNN scoring of device-generated profiles; fold: the fold alone (means and counts of every
-period). --layout, --warps, --chunk and --tile set the fold's launch config (0: automatic).
+period); probe: the shared-memory bin-update rates of every record kind (gpfc_probe_smem_rmw)
+at full occupancy and at the fold's 256-bin footprints. --layout, --warps, --chunk and --tile set the fold's launch config (0: automatic).
 Prints the mean CUDA-event time of the repeats after the first.
 """
 from __future__ import annotations
@@ -18,13 +20,25 @@ import math
 
 import torch
 
-from . import (SCORER_BOX, SCORER_CNN, Context, gpfc_fold, gpfc_score_cnn, gpfc_search,
+from . import (SCORER_BOX, SCORER_CNN, Context, gpfc_fold, gpfc_probe_smem_rmw, gpfc_score_cnn, gpfc_search,
                gpfc_synth_profiles)
+
+
+def probe_sweep():
+    names = {(8, 0): "8 B packed, ld/st", (8, 1): "8 B two rows, 2 x red.u32", (6, 0): "6 B paired, ld/st",
+             (6, 1): "6 B paired, red.f32 + red.u32", (4, 0): "4 B, ld/st", (4, 1): "4 B, red.u32"}
+    print("record | op | bins x warps per SM | updates/clk/SM | G updates/s")
+    for (word, op), name in names.items():
+        for nbins, warps in ((32, 16), (256, 3), (256, 4)):
+            if word * nbins * 32 * warps > 227 * 1024:
+                continue
+            ups, upc = gpfc_probe_smem_rmw(word, nbins, warps, 1, 20000, op=op)
+            print(f"{name} | {nbins} x {warps} | {upc:.2f} | {ups / 1e9:.1f}")
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["box", "cnn", "cnn-score", "fold"], default="box")
+    ap.add_argument("--what", choices=["box", "cnn", "cnn-score", "fold", "probe"], default="box")
     ap.add_argument("--n-periods", type=int, default=250_000)
     ap.add_argument("--n-profiles", type=int, default=16_384)
     ap.add_argument("--repeat", type=int, default=5)
@@ -34,6 +48,9 @@ def main():
     a = ap.parse_args()
     import lcsynth  # the synthetic-input generators
     from .train import init_weights
+    if a.what == "probe":
+        probe_sweep()
+        return
     ctx = Context(0)
     ctx.set_fold_config(warps=a.warps, layout=a.layout, chunk=a.chunk, tile=a.tile)
     dev = ctx.device
