@@ -340,6 +340,7 @@ EqParams eq_params(gpfc_ctx *ctx, const WideBuffers &w, int64_t n, const double 
     p.fshift = shift_of(nfine);
     p.ppb = eq_periods_per_block(nfine);
     p.kscale = w.kscale;
+    p.red32 = eq_red32(n) ? 1 : 0;
     p.stats = w.stats;
     p.status = ctx->status_dev;
     return p;

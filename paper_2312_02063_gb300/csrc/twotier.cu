@@ -17,7 +17,11 @@
 // signed fixed point with a per-star quantum 2^-k, chosen so that n max|x| 2^k < 2^38:
 // no sum, prefix sum or count can overflow its field, every addition is exact, and the
 // fold is a single 64-bit shared-memory atomic add per sample and period, deterministic
-// whatever the order. A block folds up to kEqMaxPeriods periods at a time (4096 fine
+// whatever the order. Up to 65,536 samples the fold is instead two 32-bit shared-memory
+// reductions per sample and period (several times the 64-bit atomics' rate), into a row of
+// 32-bit sums and a row of counts per period, with k the largest such that
+// |rint(x 2^k)| <= floor((2^31 - 1) / n): still exact, at 2^31 / n levels of max|x| instead
+// of 2^38 / n; the rows are then packed into the same 64-bit words. A block folds up to kEqMaxPeriods periods at a time (4096 fine
 // bins x 6 periods = 192 KB of shared memory), scans each period's fine bins (exact
 // integer prefix sums), and evaluates G at the boundaries by binary search on the
 // cumulative counts.
@@ -57,11 +61,21 @@ __global__ void eq_absmax_kernel(const float *__restrict__ x, int64_t n, unsigne
     if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, m);
 }
 
-// Quantum exponent k with n max|x| 2^k < 2^38, and q_i = rint(x_i 2^k).
+// Quantum exponent k, and q_i = rint(x_i 2^k). 64-bit words: n max|x| 2^k < 2^38. 32-bit
+// reductions (eq_red32(n)): the largest k with max|x| 2^k <= floor((2^31 - 1) / n), so every
+// |q_i| is at most that bound and no bin sum of n samples leaves 32 bits.
 __device__ __forceinline__ int eq_scale(unsigned int maxbits, int64_t n)
 {
     const float m = __uint_as_float(maxbits);
     if (!(m > 0.f) || !isfinite(m)) return 0;
+    if (eq_red32(n)) {
+        const double lim = floor(2147483647.0 / (double)n), xm = (double)m;
+        int k = ilogb(lim) - ilogb(xm);
+        k = max(-200, min(200, k));
+        while (k < 200 && ldexp(xm, k + 1) <= lim) ++k;
+        while (k > -200 && ldexp(xm, k) > lim) --k;
+        return k;
+    }
     int e = 0;
     frexp((double)m * (double)n, &e);  // m n < 2^e
     const int k = 38 - e;
@@ -101,7 +115,7 @@ __device__ __forceinline__ unsigned long long eq_block_scan(unsigned long long v
     return v + before;
 }
 
-template <bool POW2>
+template <bool POW2, bool RED32>
 __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p)
 {
     extern __shared__ __align__(16) unsigned long long bins[];  // [ppb][nfine]
@@ -136,7 +150,9 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
             Fl[pp] = pp < nper ? sF[2 * pp] : 0u;
             Fh[pp] = pp < nper ? sF[2 * pp + 1] : 0u;
         }
-        // steps 1-3: fine bins, one 64-bit atomic add per sample and period
+        // steps 1-3: fine bins, one 64-bit atomic add per sample and period, or (RED32) two
+        // 32-bit reductions into the period's sum row and count row (2 nfine words)
+        const uint32_t rows = smem_u32(bins);
         for (int64_t i = threadIdx.x; i < n; i += kEqThreads) {
             const uint32_t tl = p.tau_lo[i];
             const uint32_t th = (uint32_t)p.tau_hi[i];
@@ -153,11 +169,41 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
                         f = (uint32_t)(((unsigned long long)hi * (uint32_t)nfine +
                                         (unsigned long long)__umulhi(lo, (uint32_t)nfine)) >> 32);
                     }
-                    atomicAdd(&bins[pp * nfine + eq_word((int)f, swz)], v);
+                    if (RED32) {
+                        const uint32_t a = rows + 4u * (uint32_t)(2 * pp * nfine + eq_word((int)f, swz));
+                        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"((uint32_t)v) : "memory");
+                        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a + 4u * (uint32_t)nfine), "r"(1u) : "memory");
+                    } else {
+                        atomicAdd(&bins[pp * nfine + eq_word((int)f, swz)], v);
+                    }
                 }
             }
         }
         __syncthreads();
+        if (RED32) {
+            // each period's rows (32-bit sums, then counts) become its 64-bit words
+            // count << 40 plus the sum, in place: all of a period's reads come before a
+            // barrier and its writes after it
+            constexpr int kPer = kEqMaxFine / kEqThreads;
+            for (int pp = 0; pp < nper; ++pp) {
+                const uint32_t *R = reinterpret_cast<const uint32_t *>(bins + (size_t)pp * nfine);
+                unsigned long long w[kPer];
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const int f = threadIdx.x + u * kEqThreads;
+                    w[u] = f < nfine ? ((unsigned long long)R[nfine + f] << kCountShift) +
+                                           (unsigned long long)(long long)(int32_t)R[f]
+                                     : 0ull;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const int f = threadIdx.x + u * kEqThreads;
+                    if (f < nfine) bins[(size_t)pp * nfine + f] = w[u];
+                }
+            }
+            __syncthreads();
+        }
         if (p.width_only) {
             // the fine bins are the result: counts, exact sums rounded once, means
             for (int idx = threadIdx.x; idx < nper * nfine; idx += kEqThreads) {
@@ -244,11 +290,14 @@ cudaError_t launch_eq_fold(const EqParams &p, int num_sms, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(eq_fold_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kSmemLimit - 4096));
+        const int lim = (int)(kSmemLimit - 4096);
+        cudaError_t e = cudaFuncSetAttribute(eq_fold_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(eq_fold_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kSmemLimit - 4096));
+            e = cudaFuncSetAttribute(eq_fold_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(eq_fold_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(eq_fold_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -256,8 +305,14 @@ cudaError_t launch_eq_fold(const EqParams &p, int num_sms, cudaStream_t st)
     if (p.ppb < 1 || p.ppb > kEqMaxPeriods || smem > kSmemLimit - 4096) return cudaErrorInvalidValue;
     const int64_t ngroups = (p.np + p.ppb - 1) / p.ppb;
     const int grid = (int)(ngroups < (int64_t)num_sms ? ngroups : (int64_t)num_sms);
-    if (p.fshift >= 0) eq_fold_kernel<true><<<grid, kEqThreads, smem, st>>>(p);
-    else eq_fold_kernel<false><<<grid, kEqThreads, smem, st>>>(p);
+    if (p.red32 != (int)eq_red32(p.n)) return cudaErrorInvalidValue;  // must match the quantum of the prep
+    if (p.red32) {
+        if (p.fshift >= 0) eq_fold_kernel<true, true><<<grid, kEqThreads, smem, st>>>(p);
+        else eq_fold_kernel<false, true><<<grid, kEqThreads, smem, st>>>(p);
+    } else {
+        if (p.fshift >= 0) eq_fold_kernel<true, false><<<grid, kEqThreads, smem, st>>>(p);
+        else eq_fold_kernel<false, false><<<grid, kEqThreads, smem, st>>>(p);
+    }
     return cudaGetLastError();
 }
 
