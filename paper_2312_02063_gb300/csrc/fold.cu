@@ -830,9 +830,13 @@ __device__ __forceinline__ bool flush_chunk(const St &st, float2 *wsc, uint32_t 
 // kLayoutRed32 flush: add each bin's chunk sum and count into the exact workspace (int64
 // fixed-point sum, 32-bit count). On the last chunk the bin gets its FP32 sum
 // tot 2^-qexp (one rounding) and its count; otherwise it is cleared. Workspace reads are
-// batched 16 bins at a time to overlap their latency.
+// batched 16 bins at a time to overlap their latency. qscale_f (nonzero when
+// |qexp| <= 100) is 2^-qexp as an FP32 number: then tot is rounded to FP32 and scaled
+// exactly (no result of a bin sum comes near the FP32 range's ends), the same single
+// rounding as in FP64 without the FP64 pipe.
 __device__ __forceinline__ void flush_one_red(const StoreRed32 &st, long long *wss, uint32_t *wcn, int b,
-                                              size_t idx, bool last, long long tot, uint32_t cc, double qscale)
+                                              size_t idx, bool last, long long tot, uint32_t cc, double qscale,
+                                              float qscale_f)
 {
     float unused;
     uint32_t c;
@@ -840,7 +844,7 @@ __device__ __forceinline__ void flush_one_red(const StoreRed32 &st, long long *w
     tot += (long long)st.isum((uint32_t)b);
     cc += c;
     if (last) {
-        st.put((uint32_t)b, (float)((double)tot * qscale), cc);
+        st.put((uint32_t)b, qscale_f != 0.f ? __ll2float_rn(tot) * qscale_f : (float)((double)tot * qscale), cc);
     } else {
         wss[idx] = tot;
         wcn[idx] = cc;
@@ -851,6 +855,8 @@ __device__ __forceinline__ void flush_one_red(const StoreRed32 &st, long long *w
 __device__ __forceinline__ void flush_chunk_red(const StoreRed32 &st, long long *wss, uint32_t *wcn, int blo,
                                                 int bhi, int ppc, bool first, bool last, double qscale)
 {
+    const int qexp = -ilogb(qscale);
+    const float qscale_f = (qexp >= -100 && qexp <= 100) ? __int_as_float((127 - qexp) << 23) : 0.f;
     int b0 = blo;
     for (; b0 + 16 <= bhi; b0 += 16) {
         long long ts[16];
@@ -862,11 +868,71 @@ __device__ __forceinline__ void flush_chunk_red(const StoreRed32 &st, long long 
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-            flush_one_red(st, wss, wcn, b0 + u, (size_t)(b0 + u) * ppc, last, ts[u], cc[u], qscale);
+            flush_one_red(st, wss, wcn, b0 + u, (size_t)(b0 + u) * ppc, last, ts[u], cc[u], qscale, qscale_f);
     }
     for (; b0 < bhi; ++b0) {
         const size_t idx = (size_t)b0 * ppc;
-        flush_one_red(st, wss, wcn, b0, idx, last, first ? 0ll : wss[idx], first ? 0u : wcn[idx], qscale);
+        flush_one_red(st, wss, wcn, b0, idx, last, first ? 0ll : wss[idx], first ? 0u : wcn[idx], qscale, qscale_f);
+    }
+}
+
+// kLayoutRed32, kModeFold: the last chunk's flush and the epilogue in one pass. Each bin's
+// exact total (the chunk's sum and count plus, unless this is the first chunk, the
+// workspace's) goes straight to the output row as in write_profile_bins, with the same
+// single FP32 rounding of the sum as flush_one_red; four bins at a time, so the loads,
+// conversions and divisions of four bins overlap.
+__device__ __forceinline__ void finish_red_rows(const StoreRed32 &st, int blo, int bhi, const long long *wss,
+                                                const uint32_t *wcn, size_t ppc, bool first, double qscale,
+                                                bool kvalid, size_t rowoff, float fh, float fl, float *folded,
+                                                float *sums, int32_t *counts, bool vec)
+{
+    const int qexp = -ilogb(qscale);
+    const float qscale_f = (qexp >= -100 && qexp <= 100) ? __int_as_float((127 - qexp) << 23) : 0.f;
+    auto bin = [&](int b, long long tot, uint32_t c, float &m, float &sv, int32_t &cv) {
+        const float S = qscale_f != 0.f ? __ll2float_rn(tot) * qscale_f : (float)((double)tot * qscale);
+        if (!kvalid) c = 0u;
+        m = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
+        sv = c ? S : 0.f;
+        cv = (int32_t)c;
+        (void)b;
+    };
+    auto total = [&](int b, long long &tot, uint32_t &c) {
+        float unused;
+        st.load((uint32_t)b, unused, c);
+        tot = (long long)st.isum((uint32_t)b);
+        if (!first) {
+            tot += wss[(size_t)b * ppc];
+            c += wcn[(size_t)b * ppc];
+        }
+    };
+    int b = blo;
+    if (vec) {
+        for (; b + 4 <= bhi; b += 4) {
+            long long t[4];
+            uint32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) total(b + u, t[u], c[u]);
+            float4 m, sv;
+            int4 cv;
+            bin(b, t[0], c[0], m.x, sv.x, cv.x);
+            bin(b + 1, t[1], c[1], m.y, sv.y, cv.y);
+            bin(b + 2, t[2], c[2], m.z, sv.z, cv.z);
+            bin(b + 3, t[3], c[3], m.w, sv.w, cv.w);
+            if (folded) *reinterpret_cast<float4 *>(folded + rowoff + b) = m;
+            if (sums) *reinterpret_cast<float4 *>(sums + rowoff + b) = sv;
+            if (counts) *reinterpret_cast<int4 *>(counts + rowoff + b) = cv;
+        }
+    }
+    for (; b < bhi; ++b) {
+        long long t;
+        uint32_t c;
+        total(b, t, c);
+        float m, sv;
+        int32_t cv;
+        bin(b, t, c, m, sv, cv);
+        if (folded) folded[rowoff + b] = m;
+        if (sums) sums[rowoff + b] = sv;
+        if (counts) counts[rowoff + b] = cv;
     }
 }
 
@@ -1410,6 +1476,50 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int want, const int *
     return true;
 }
 
+// Write bins [blo, bhi) of this lane's profile to its output row (row offset rowoff):
+// means fh + (fl + S / c) (NaN for an empty bin), sums (0 for an empty bin) and counts;
+// each output may be NULL. The lanes of a warp write 32 different rows, so every store
+// touches 32 sectors: with vec (16-byte aligned outputs, nbins and blo multiples of 4) a
+// lane writes four bins per store.
+template <class St>
+__device__ __forceinline__ void write_profile_bins(const St &st, int blo, int bhi, size_t rowoff, bool kvalid,
+                                                   bool over, const uint32_t *wcn, size_t ppc, float fh, float fl,
+                                                   float *folded, float *sums, int32_t *counts, bool vec)
+{
+    auto bin = [&](int b, float &m, float &sv, int32_t &cv) {
+        float S;
+        uint32_t c;
+        st.load((uint32_t)b, S, c);
+        if (over) c = wcn[(size_t)b * ppc];
+        if (!kvalid) c = 0u;
+        m = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
+        sv = c ? S : 0.f;
+        cv = (int32_t)c;
+    };
+    int b = blo;
+    if (vec) {
+        for (; b + 4 <= bhi; b += 4) {
+            float4 m, sv;
+            int4 cv;
+            bin(b, m.x, sv.x, cv.x);
+            bin(b + 1, m.y, sv.y, cv.y);
+            bin(b + 2, m.z, sv.z, cv.z);
+            bin(b + 3, m.w, sv.w, cv.w);
+            if (folded) *reinterpret_cast<float4 *>(folded + rowoff + b) = m;
+            if (sums) *reinterpret_cast<float4 *>(sums + rowoff + b) = sv;
+            if (counts) *reinterpret_cast<int4 *>(counts + rowoff + b) = cv;
+        }
+    }
+    for (; b < bhi; ++b) {
+        float m, sv;
+        int32_t cv;
+        bin(b, m, sv, cv);
+        if (folded) folded[rowoff + b] = m;
+        if (sums) sums[rowoff + b] = sv;
+        if (counts) counts[rowoff + b] = cv;
+    }
+}
+
 template <int MODE, bool POW2, int LAYOUT, int MAXW>
 __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
 {
@@ -1467,6 +1577,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     }
     __syncthreads();
     uint32_t parity_bits = 0u;  // bit b: phase parity of buffer b
+    // profile rows written four bins per store when the outputs allow it
+    const bool vec_out = (nbins & 3) == 0 && (blo & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(p.folded) | reinterpret_cast<uintptr_t>(p.sums) |
+                           reinterpret_cast<uintptr_t>(p.counts)) & 15) == 0;
     float2 *wsc_cta = p.ws_sc + (size_t)blockIdx.x * nbins * ppc + gw * 32 + lane;
     uint32_t *wcn_cta = p.ws_cnt + (size_t)blockIdx.x * nbins * ppc + gw * 32 + lane;
 
@@ -1562,6 +1676,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
         }
         bool over = false;
         bool first_flush = true;
+        bool last_first = true;  // kLayoutRed32 fold: whether the last chunk was also the first
         int chunk_left = p.chunk;
         for (int t = 0; t < ntiles; ++t) {
             const int buf = t & 1;
@@ -1617,11 +1732,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                         if (chunk_left == 0 || last) {
                             if constexpr (kRed) {
                                 // every stream's reductions of the chunk land before the flush
-                                // reads them, and the cleared bins before the next chunk's
-                                if (nstreams > 1) fold_sync();
-                                flush_chunk_red(st, reinterpret_cast<long long *>(wsc_cta), wcn_cta, blo, bhi, ppc,
-                                                first_flush, last, qscale);
-                                if (nstreams > 1) fold_sync();
+                                // reads them, and the cleared bins before the next chunk's. The
+                                // fold's last chunk is finished in the epilogue (after the tile
+                                // loop's barrier), straight into the output rows.
+                                if (!(MODE == kModeFold && last)) {
+                                    if (nstreams > 1) fold_sync();
+                                    flush_chunk_red(st, reinterpret_cast<long long *>(wsc_cta), wcn_cta, blo, bhi,
+                                                    ppc, first_flush, last, qscale);
+                                    if (nstreams > 1) fold_sync();
+                                } else {
+                                    last_first = first_flush;
+                                }
                             }
                             else
                                 over = flush_chunk(st, wsc_cta, wcn_cta, nbins, ppc, first_flush, last);
@@ -1649,18 +1770,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             // output row: the period, or the lane's chunk slot
             const int64_t row = p.slot_k ? (task - p.task_begin) * ppc + gw * 32 + lane : k;
             if (p.slot_k && sw == 0) p.slot_k[row] = kvalid ? k : -1;
-            if (kvalid || p.slot_k) {
-                const float fh = p.stats[s].f_hi, fl = p.stats[s].f_lo;
-                for (int b = blo; b < bhi; ++b) {
-                    float S;
-                    uint32_t c;
-                    st.load((uint32_t)b, S, c);
-                    if (over) c = wcn_cta[(size_t)b * ppc];
-                    if (!kvalid) c = 0u;
-                    if (p.folded) p.folded[(size_t)row * nbins + b] = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
-                    if (p.sums) p.sums[(size_t)row * nbins + b] = c ? S : 0.f;
-                    if (p.counts) p.counts[(size_t)row * nbins + b] = (int32_t)c;
-                }
+            if constexpr (kRed) {
+                if ((kvalid || p.slot_k) && ntiles > 0)
+                    finish_red_rows(st, blo, bhi, reinterpret_cast<const long long *>(wsc_cta), wcn_cta, (size_t)ppc,
+                                    last_first, qscale, kvalid, (size_t)row * nbins, p.stats[s].f_hi,
+                                    p.stats[s].f_lo, p.folded, p.sums, p.counts, vec_out);
+                else if (kvalid || p.slot_k)
+                    write_profile_bins(st, blo, bhi, (size_t)row * nbins, kvalid, false, wcn_cta, (size_t)ppc,
+                                       p.stats[s].f_hi, p.stats[s].f_lo, p.folded, p.sums, p.counts, vec_out);
+            } else if (kvalid || p.slot_k) {
+                write_profile_bins(st, blo, bhi, (size_t)row * nbins, kvalid, over, wcn_cta, (size_t)ppc,
+                                   p.stats[s].f_hi, p.stats[s].f_lo, p.folded, p.sums, p.counts, vec_out);
             }
         } else if (MODE == kModeSearch) {
             const int b = iter & 1;
@@ -1690,15 +1810,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             if (ok) {
                 const size_t base = ((size_t)blockIdx.x * 2 + b) * ppc + gw * 32 + lane;
                 if (sw == 0) p.slot_k[base] = kvalid ? k : -1;
-                for (int bb = blo; bb < bhi; ++bb) {
-                    float S;
-                    uint32_t c;
-                    st.load((uint32_t)bb, S, c);
-                    if (over) c = wcn_cta[(size_t)bb * ppc];
-                    if (!kvalid) c = 0u;
-                    p.sums[base * nbins + bb] = c ? S : 0.f;
-                    p.counts[base * nbins + bb] = (int32_t)c;
-                }
+                write_profile_bins(st, blo, bhi, base * nbins, kvalid, over, wcn_cta, (size_t)ppc, 0.f, 0.f, nullptr,
+                                   p.sums, p.counts, vec_out);
             }
             // every row of the task is written; all fold warps leave together on a failure
             if (named_bar_or(1, 32 * nfw, !ok)) {

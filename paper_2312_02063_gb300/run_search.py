@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--n-profiles", type=int, default=16_384)
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--seed", type=int, default=20232204)
+    ap.add_argument("--n-samples", type=int, default=0, help="keep only the first N samples of the star (0: all)")
     for k in ("layout", "warps", "chunk", "tile"):
         ap.add_argument("--" + k, type=int, default=0)
     a = ap.parse_args()
@@ -64,8 +65,9 @@ def main():
     else:
         lc = lcsynth.light_curve_kepler(seed=a.seed)
         periods = lcsynth.freq_grid(a.n_periods)
-        t = torch.from_numpy(lc.times).to(dev)
-        f = torch.from_numpy(lc.flux).to(dev)
+        ns = a.n_samples if a.n_samples > 0 else lc.times.shape[0]
+        t = torch.from_numpy(lc.times[:ns].copy()).to(dev)
+        f = torch.from_numpy(lc.flux[:ns].copy()).to(dev)
         p = torch.from_numpy(periods).to(dev)
         score = torch.empty(a.n_periods, dtype=torch.float32, device=dev)
         folded = torch.empty(a.n_periods, 256, dtype=torch.float32, device=dev)
