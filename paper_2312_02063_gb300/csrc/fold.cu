@@ -838,13 +838,13 @@ __device__ __forceinline__ void flush_one_red(const StoreRed32 &st, long long *w
                                               size_t idx, bool last, long long tot, uint32_t cc, double qscale,
                                               float qscale_f)
 {
-    float unused;
-    uint32_t c;
-    st.load((uint32_t)b, unused, c);
     tot += (long long)st.isum((uint32_t)b);
-    cc += c;
+    cc += st.count((uint32_t)b);
     if (last) {
-        st.put((uint32_t)b, qscale_f != 0.f ? __ll2float_rn(tot) * qscale_f : (float)((double)tot * qscale), cc);
+        float S;
+        if (qscale_f != 0.f) S = __ll2float_rn(tot) * qscale_f;
+        else S = (float)((double)tot * qscale);
+        st.put((uint32_t)b, S, cc);
     } else {
         wss[idx] = tot;
         wcn[idx] = cc;
@@ -888,8 +888,14 @@ __device__ __forceinline__ void finish_red_rows(const StoreRed32 &st, int blo, i
 {
     const int qexp = -ilogb(qscale);
     const float qscale_f = (qexp >= -100 && qexp <= 100) ? __int_as_float((127 - qexp) << 23) : 0.f;
+    // warp-uniform choice of the conversion: a single chunk's total is a 32-bit integer
+    // (converted on the FP32 side); longer stars and extreme units go through FP64
+    const int conv = qscale_f == 0.f ? 2 : (first ? 0 : 1);
     auto bin = [&](int b, long long tot, uint32_t c, float &m, float &sv, int32_t &cv) {
-        const float S = qscale_f != 0.f ? __ll2float_rn(tot) * qscale_f : (float)((double)tot * qscale);
+        float S;
+        if (conv == 0) S = __int2float_rn((int)tot) * qscale_f;
+        else if (conv == 1) S = __ll2float_rn(tot) * qscale_f;
+        else S = (float)((double)tot * qscale);
         if (!kvalid) c = 0u;
         m = c ? fh + (fl + S / (float)c) : __int_as_float(0x7fc00000);
         sv = c ? S : 0.f;
@@ -897,8 +903,7 @@ __device__ __forceinline__ void finish_red_rows(const StoreRed32 &st, int blo, i
         (void)b;
     };
     auto total = [&](int b, long long &tot, uint32_t &c) {
-        float unused;
-        st.load((uint32_t)b, unused, c);
+        c = st.count((uint32_t)b);
         tot = (long long)st.isum((uint32_t)b);
         if (!first) {
             tot += wss[(size_t)b * ppc];
@@ -1646,7 +1651,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 const unsigned long long F = (unsigned long long)__double2ll_rn(q);
                 Fl = (uint32_t)F;
                 Fh = (uint32_t)(F >> 32);
-                gsize = regular_group_size(F, p.stats[s].dtau0, (uint32_t)nbins);
+                // (the reduction layout needs no collision-free group size)
+                if (!kRed) gsize = regular_group_size(F, p.stats[s].dtau0, (uint32_t)nbins);
             } else {
                 gsize = 0;
                 report_error(p.status, kErrRange);
