@@ -153,10 +153,24 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_fold_kernel(const EqParams p
         // steps 1-3: fine bins, one 64-bit atomic add per sample and period, or (RED32) two
         // 32-bit reductions into the period's sum row and count row (2 nfine words)
         const uint32_t rows = smem_u32(bins);
+        // each thread's next sample is loaded while the current one is folded (the loads
+        // come from L2; their latency would otherwise stall every iteration)
+        uint32_t ntl = 0u, nth = 0u;
+        long long nq = 0;
+        if (threadIdx.x < n) {
+            ntl = p.tau_lo[threadIdx.x];
+            nth = (uint32_t)p.tau_hi[threadIdx.x];
+            nq = p.q[threadIdx.x];
+        }
         for (int64_t i = threadIdx.x; i < n; i += kEqThreads) {
-            const uint32_t tl = p.tau_lo[i];
-            const uint32_t th = (uint32_t)p.tau_hi[i];
-            const unsigned long long v = (1ull << kCountShift) + (unsigned long long)p.q[i];
+            const uint32_t tl = ntl;
+            const uint32_t th = nth;
+            const unsigned long long v = (1ull << kCountShift) + (unsigned long long)nq;
+            if (i + kEqThreads < n) {
+                ntl = p.tau_lo[i + kEqThreads];
+                nth = (uint32_t)p.tau_hi[i + kEqThreads];
+                nq = p.q[i + kEqThreads];
+            }
 #pragma unroll
             for (int pp = 0; pp < kEqMaxPeriods; ++pp) {
                 if (pp < nper) {
