@@ -284,7 +284,7 @@ def test_argument_errors_are_synchronous(ctx):
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("layout,chunk", [(1, 1000), (2, 1000), (1, 0), (2, 0)])
+@pytest.mark.parametrize("layout,chunk", [(1, 1000), (2, 1000), (1, 0), (2, 0), (3, 1000), (3, 0)])
 def test_fold_and_search_every_kernel_variant(ctx, layout, chunk):
     import paper_2312_02063_gb300 as g
     rng = np.random.default_rng(layout * 10 + chunk)
@@ -324,3 +324,38 @@ def test_bounded_wait_gives_up_reports_timeout_and_context_recovers(ctx):
     fo, co = gpu_fold(ctx, lc.times, lc.flux, periods, 64, lc.t0)
     mean_o, cnt_o, _ = oracle.fold(lc.times, lc.flux, periods, 64, lc.t0)
     check_fold(fo, co, mean_o, cnt_o)
+
+
+def test_reduction_fold_is_identical_for_any_launch_shape(ctx):
+    """Layout 3 sums integers exactly, so its outputs must not depend on how the work is
+    spread: warps (period groups), sample streams per group, tile size and blocks per SM give
+    bit-identical means, counts and box scores, on one chunk (the default) and on several
+    (chunk 992: exact int64 flushes)."""
+    import paper_2312_02063_gb300 as g
+    rng = np.random.default_rng(33)
+    n = 20011
+    times = np.sort(rng.uniform(0.0, 600.0, n))
+    times[500:509] = times[500]
+    flux = (1.0 + rng.normal(0, 5e-3, n)).astype(np.float32)
+    periods = rng.uniform(0.2, 1.0, 700)
+    t_d, f_d, p_d = _dev(ctx, times), _dev(ctx, flux), _dev(ctx, periods)
+    try:
+        for chunk in (0, 992):
+            ref = None
+            for warps, streams, tile in ((1, 1, 1024), (3, 4, 1024), (2, 6, 2048), (3, 2, 512), (1, 12, 1024)):
+                ctx.set_fold_config(warps=warps, layout=3, chunk=chunk, tile=tile, streams=streams)
+                fo, co = g.gpfc_fold(ctx, t_d, f_d, p_d, 256, 0.0)
+                sc, _, _ = g.gpfc_search(ctx, t_d, f_d, p_d, 256, 0.0, g.SCORER_BOX, 1, 108, 5e-3)
+                ctx.sync()
+                got = (fo.cpu().numpy(), co.cpu().numpy(), sc.cpu().numpy())
+                plan = ctx.last_fold_plan()
+                assert plan["layout"] == 3 and plan["streams"] == streams
+                if ref is None:
+                    ref = got
+                else:
+                    np.testing.assert_array_equal(got[0], ref[0])
+                    np.testing.assert_array_equal(got[1], ref[1])
+                    np.testing.assert_array_equal(got[2], ref[2])
+    finally:
+        ctx.reset_fold_config()
+
