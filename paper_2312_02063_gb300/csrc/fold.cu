@@ -4,21 +4,30 @@
 //   tau_i = rint((t_i - t0) 2^24), F_k = rint(2^40 / P_k), phase = (tau F mod 2^64) / 2^64,
 //   bin = floor(phase * nbins), then per-bin count and flux sum, mean = sum / count.
 //
-// Design. One lane owns one trial period for the whole light curve, so no two threads
-// ever update the same bin and no atomics are needed. Each warp keeps the bins of its
-// 32 periods in shared memory laid out [bin][lane], so a warp's 32 read-modify-writes never
-// conflict whatever bins the lanes hit: either 8-byte words (FP32 partial sum, 32-bit
-// count; the default from 256 bins) or FP32 sums with paired 16-bit counts (6 bytes a
-// bin, four warps' worth at 256 bins). Light-curve tiles (tau split in two 32-bit words,
-// flux - f_ref, one regular-cadence flag byte per 16 samples) are staged into shared
-// memory by the bulk-copy (TMA) engine, double-buffered behind an mbarrier, and every lane
-// reads the same sample (a broadcast). Groups of 16 (or 8) regular samples that can never
-// put two samples into one bin at the warp's periods go through a software-pipelined loop
-// without collision checks; other groups take a checked path.
+// Design. One lane owns one trial period for the whole light curve; the bins of a warp's
+// (or period group's) 32 periods sit in shared memory laid out [bin][lane], so the 32
+// updates of one instruction never conflict whatever bins the lanes hit. Light-curve tiles
+// (tau split in two 32-bit words, the flux, one regular-cadence flag byte per 16 samples)
+// are staged into shared memory by the bulk-copy (TMA) engine, double-buffered behind an
+// mbarrier, and every lane reads the same sample (a broadcast). Three bin layouts:
 //
-// The partial sums cover a chunk of 128 * nbins samples; at the end of each chunk they
-// are added into a per-block workspace with Kahan compensation (sum, compensation) and
-// exact 32-bit counts, which stays resident in L2.
+// * kLayoutRed32 (the default from 256 bins): per bin a row of the 32 lanes' 32-bit
+//   fixed-point sums and a row of their 32-bit counts; an update is two no-return
+//   red.shared.add.u32. The flux is pre-quantised per star (x_q = rint(x 2^e), e from the
+//   largest |x| and the chunk length, so a chunk's bin sum fits in 32 bits), the sums are
+//   exact and independent of the order of the additions, and so several warps (sample
+//   streams) fold disjoint 16-sample groups of every tile into the same period group's
+//   bins: three 64 KB period groups per block at 256 bins, four streams each, twelve warps.
+//   Chunk sums go exactly into an int64 workspace; each bin is rounded once to FP32.
+// * kLayoutPacked64: FP32 partial sum and 32-bit count in one 8-byte word, a 64-bit load
+//   and store per update; one warp per 32 periods.
+// * kLayoutPaired16: FP32 sums with paired 16-bit counts (6 bytes a bin), the default below
+//   256 bins.
+// The FP32 layouts apply a group of 16 (or 8) regular samples that can never put two
+// samples into one bin at the warp's periods through a software-pipelined loop without
+// collision checks, other groups through a checked path; their partial sums cover a chunk
+// of 128 * nbins samples and are then added into the workspace with Kahan compensation
+// (sum, compensation) and exact 32-bit counts. The workspace stays resident in L2.
 //
 // Epilogues (kernel modes): write means and counts (gpfc_fold) or centred sums and counts
 // (the separate box scorer); run the box-SNR search over each lane's finished profile
