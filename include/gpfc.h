@@ -171,11 +171,16 @@ int gpfc_workspace_size(gpfc_ctx *ctx, int64_t n, int64_t n_periods, int32_t nbi
  * folded  [n_periods][nbins] float32 row-major, per-bin mean flux, NaN for an empty bin;
  *                        may be NULL (not written)
  * counts  [n_periods][nbins] int32 row-major, samples per bin; may be NULL
- * Sums are accumulated as (flux - mean flux) in FP32 with Kahan compensation (chunk
- * partials in shared memory, compensated across chunks); counts are exact integers.
- * Above 1024 bins (more than a lane's shared-memory share) the fold adds each sample
- * with one 64-bit shared-memory atomic per period into count << 40 plus the flux sum in
- * fixed point (quantum 2^-k with n max|flux - mean| 2^k < 2^38): exact sums, rounded once.
+ * Sums are of x = float32(flux - mean flux); counts are exact integers. From 256 bins (fold
+ * layout 3, the default) x is rounded to a multiple of 2^-e, e per star the largest with
+ * max|x| 2^e <= floor((2^31 - 1) / min(chunk, n)), and the multiples are summed exactly
+ * (shared-memory integer reductions, int64 across chunks), each bin rounded once to FP32:
+ * a bin mean is within 2^-e / 2 of the exact mean of the x. Below 256 bins (layouts 1 and 2)
+ * they are accumulated in FP32 with Kahan compensation (chunk partials in shared memory,
+ * compensated across chunks). Above 1024 bins (more than a lane's shared-memory share) the
+ * fold adds each sample with shared-memory atomics per period into count << 40 plus the
+ * flux sum in fixed point (quantum 2^-k with n max|x| 2^k < 2^38, or up to 65,536 samples
+ * two 32-bit reductions with n max|x| 2^k < 2^31): exact sums, rounded once.
  * Limits: 1 <= n <= 2^24 (n < 2^24 above 1024 bins), 1 <= n_periods <= 2^31 - 1,
  * |tau| < 2^62, F < 2^63. */
 int gpfc_fold(gpfc_ctx *ctx, const double *times, const float *flux, int64_t n,
