@@ -191,6 +191,11 @@ FoldPlan plan_with(const gpfc_ctx *ctx, int64_t n, int64_t np, int nbins, const 
     pl.layout = cfg.layout ? cfg.layout : default_layout(nbins);
     if (fold_max_warps(nbins, pl.layout, pl.tile) < 1) pl.layout = kLayoutPaired16;
     if (fold_max_warps(nbins, pl.layout, pl.tile) < 1) pl.tile = 512;
+    // the reduction layout's tiles are 8 bytes a sample: 2048-sample tiles (half the
+    // per-tile work) where they cost no period group
+    if (!cfg.tile && pl.layout == kLayoutRed32 &&
+        fold_max_warps(nbins, pl.layout, kMaxTile) >= fold_max_warps(nbins, pl.layout, pl.tile))
+        pl.tile = kMaxTile;
     const int maxw = fold_max_warps(nbins, pl.layout, pl.tile);
     // enough blocks to cover the SMs when the grid is short, else the widest block
     int64_t per_sm = (np + (int64_t)32 * ctx->num_sms - 1) / ((int64_t)32 * ctx->num_sms);
@@ -254,6 +259,7 @@ size_t carve_fold(void *base, const FoldPlan &pl, int64_t n_total, int nstars, i
     fb.smp.tau_hi = c.take<int32_t>(se);
     fb.smp.x = c.take<float>(se);
     fb.smp.xq = c.take<int32_t>(se);
+    fb.smp.thg = c.take<int32_t>(se / 16 + 64);
     fb.smp.flags = c.take<uint8_t>(se / 16 + 64);
     fb.ws_sc = c.take<float2>((size_t)pl.grid * nbins * pl.ppc);
     fb.ws_cnt = c.take<uint32_t>((size_t)pl.grid * nbins * pl.ppc);
@@ -309,6 +315,7 @@ size_t carve_wide(void *base, int64_t n, WideBuffers &w)
     w.smp.tau_hi = c.take<int32_t>(se);
     w.smp.x = c.take<float>(se);
     w.smp.xq = nullptr;  // the two-tier fold quantises on its own
+    w.smp.thg = nullptr;
     w.smp.flags = c.take<uint8_t>(se / 16 + 64);
     w.q = c.take<long long>(n);
     w.maxbits = c.take<unsigned int>(1);

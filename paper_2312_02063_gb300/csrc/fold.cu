@@ -230,6 +230,8 @@ __global__ void prep_sigma_kernel(const double *partial, const long long *pmin, 
     stats[s].pad = 0;
 }
 
+constexpr int32_t kThMixed = INT32_MIN;  // per-group high word marker: the samples differ
+
 // Pass 4: one flag byte per group of 16 samples: 1 if every step inside the group lies in
 // [dtau0, dtau0 + 2] (a regular cadence up to the 2^-24 d rounding of tau) and the high
 // word of tau is the same for all 16 (it changes every 2^32 units, ~256 d). The fold
@@ -263,6 +265,18 @@ __global__ void prep_flags_kernel(const int64_t *lc_off, int64_t n, SampleScratc
             }
         }
         smp.flags[base / 16 + q] = reg ? 1 : 0;
+        if (smp.thg) {
+            // the group's common tau high word, or kThMixed if its samples differ in it (a
+            // valid high word is below 2^30 in magnitude: |tau| < 2^62)
+            int32_t th0 = 0;
+            bool same = true;
+            for (int k = 0; k < 16 && j0 + k < len; ++k) {
+                const int32_t th = smp.tau_hi[base + j0 + k];
+                if (k == 0) th0 = th;
+                same &= th == th0;
+            }
+            smp.thg[base / 16 + q] = same ? th0 : kThMixed;
+        }
         if (smp.xq) {
             // fixed-point flux (exact: scaling by a power of two, then rounding to nearest
             // even); zero past the star's end
@@ -669,14 +683,15 @@ __device__ __forceinline__ void fold_segment(uint32_t stl, uint32_t sth, uint32_
 }
 
 // Tile data of one 16-sample group for the reduction fold: tau low words, fixed-point
-// flux, and the tau high word of the group's first sample.
+// flux and the tau high word of the group's first sample (all from the tile).
 struct RedGroup {
     uint4 a[4];
     uint4 x[4];
     uint32_t th;
 };
 
-__device__ __forceinline__ void load_red_group(uint32_t stl, uint32_t sth, uint32_t sxq, int g, RedGroup &G)
+// sthg: shared address of the segment's per-group high words
+__device__ __forceinline__ void load_red_group(uint32_t stl, uint32_t sthg, uint32_t sxq, int g, RedGroup &G)
 {
     const uint32_t o = 64u * (uint32_t)g;
 #pragma unroll
@@ -684,16 +699,18 @@ __device__ __forceinline__ void load_red_group(uint32_t stl, uint32_t sth, uint3
         G.a[q] = lds_u32x4(stl + o + 16u * q);
         G.x[q] = lds_u32x4(sxq + o + 16u * q);
     }
-    G.th = lds_u32(sth + o);
+    G.th = lds_u32(sthg + 4u * (uint32_t)g);
 }
 
-// Bins of a group. A group flagged regular by the prep pass has one tau high word (th),
-// so th * F_lo is formed once; the others read every sample's high word.
+// Bins of a group. A group whose samples share one tau high word (th) forms th * F_lo
+// once; the others (marked kThMixed by the prep pass: the few that straddle a change of the
+// high word, every ~256 days, or unsorted times) read every sample's high word from global
+// memory.
 template <bool POW2>
-__device__ __forceinline__ void red_group_bins(const RedGroup &G, bool regular, uint32_t sth, int g, uint32_t Fl,
+__device__ __forceinline__ void red_group_bins(const RedGroup &G, const int32_t *gth, int g, uint32_t Fl,
                                                uint32_t Fh, uint32_t nbins, int shift, uint32_t (&b)[16])
 {
-    if (regular) {
+    if (G.th != (uint32_t)kThMixed) {
         const uint32_t thF = G.th * Fl;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -703,10 +720,10 @@ __device__ __forceinline__ void red_group_bins(const RedGroup &G, bool regular, 
             b[4 * q + 3] = phase_bin_th<POW2>(G.a[q].w, thF, Fl, Fh, nbins, shift);
         }
     } else {
-        const uint32_t o = 64u * (uint32_t)g;
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(gth + 16 * g);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint4 h = lds_u32x4(sth + o + 16u * q);
+            const uint4 h = __ldg(h4 + q);
             b[4 * q + 0] = phase_bin<POW2>(G.a[q].x, h.x, Fl, Fh, nbins, shift);
             b[4 * q + 1] = phase_bin<POW2>(G.a[q].y, h.y, Fl, Fh, nbins, shift);
             b[4 * q + 2] = phase_bin<POW2>(G.a[q].z, h.z, Fl, Fh, nbins, shift);
@@ -731,24 +748,27 @@ __device__ __forceinline__ void red_group_add(const StoreRed32 &st, const uint32
 // g mod nstreams = stream, and the tail after the last whole group if its turn falls on this
 // stream. Two-stage pipeline: the tile data of the stream's next group is loaded while
 // the current group's reductions issue (the loop body holds two stages with the register
-// roles swapped, so nothing is copied). sxq addresses the fixed-point flux of the tile.
+// roles swapped, so nothing is copied). stl, sthg and sxq address the tile's tau low
+// words, per-group high words and fixed-point flux; gth the segment's per-sample high words
+// in global memory.
 template <bool POW2>
-__device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sth, uint32_t sxq, unsigned long long fmask,
-                                                 int nvalid, const StoreRed32 &st, uint32_t Fl, uint32_t Fh,
-                                                 uint32_t nbins, int shift, int stream, int nstreams)
+__device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sthg, const int32_t *gth, uint32_t sxq,
+                                                 int nvalid, const StoreRed32 &st,
+                                                 uint32_t Fl, uint32_t Fh, uint32_t nbins, int shift, int stream,
+                                                 int nstreams)
 {
     const int ng = nvalid >> 4;
     // one stage: bins of group g (data in C), load group g + nstreams into N, add group g
     auto stage = [&](const RedGroup &C, RedGroup &N, int g) {
         uint32_t b[16];
-        red_group_bins<POW2>(C, (fmask >> g) & 1ull, sth, g, Fl, Fh, nbins, shift, b);
-        if (g + nstreams < ng) load_red_group(stl, sth, sxq, g + nstreams, N);
+        red_group_bins<POW2>(C, gth, g, Fl, Fh, nbins, shift, b);
+        if (g + nstreams < ng) load_red_group(stl, sthg, sxq, g + nstreams, N);
         red_group_add(st, b, C);
     };
     int g = stream;
     if (g < ng) {
         RedGroup G0, G1;
-        load_red_group(stl, sth, sxq, g, G0);
+        load_red_group(stl, sthg, sxq, g, G0);
 #pragma unroll 1
         for (; g + nstreams < ng; g += 2 * nstreams) {
             stage(G0, G1, g);
@@ -758,7 +778,7 @@ __device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sth, uin
     }
     if (ng % nstreams == stream) {
         for (int i = 16 * ng; i < nvalid; ++i) {
-            const uint32_t bb = phase_bin<POW2>(lds_u32(stl + 4u * i), lds_u32(sth + 4u * i), Fl, Fh, nbins, shift);
+            const uint32_t bb = phase_bin<POW2>(lds_u32(stl + 4u * i), (uint32_t)__ldg(gth + i), Fl, Fh, nbins, shift);
             st.add(bb, (int32_t)lds_u32(sxq + 4u * i));
         }
     }
@@ -1560,9 +1580,14 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     uint32_t *tl_buf = reinterpret_cast<uint32_t *>(smem + 128);
+    // the reduction layout's tiles hold the low words, the fixed-point flux, one high word
+    // per 16-sample group and the flags (the few groups whose samples differ in their high
+    // word read them from global memory)
     uint32_t *th_buf = tl_buf + 2 * tile;
-    float *x_buf = reinterpret_cast<float *>(th_buf + 2 * tile);
-    uint8_t *f_buf = reinterpret_cast<uint8_t *>(x_buf + 2 * tile);  // [2][tile / 16]
+    float *x_buf = reinterpret_cast<float *>(kRed ? th_buf : th_buf + 2 * tile);
+    uint32_t *thg_buf = reinterpret_cast<uint32_t *>(x_buf + 2 * tile);     // kRed: [2][tile / 16]
+    uint8_t *f_buf = reinterpret_cast<uint8_t *>(kRed ? thg_buf + 2 * (tile / 16)
+                                                      : reinterpret_cast<uint32_t *>(x_buf + 2 * tile));  // [2][tile / 16]
     using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64,
                                          typename std::conditional<kRed, StoreRed32, StorePaired16>::type>::type;
     St st;
@@ -1677,9 +1702,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             const int nv = (int)min((int64_t)tile, nsamp - i0);
             const uint32_t bytes = (uint32_t)(((nv + 3) & ~3) * 4);
             const uint32_t fbytes = (uint32_t)((((nv + 15) >> 4) + 15) & ~15);
-            mbar_arrive_expect_tx(&bars[buf], 3u * bytes + fbytes);
+            const uint32_t gbytes = kRed ? (uint32_t)((((nv + 15) >> 4) * 4 + 15) & ~15) : 0u;
+            mbar_arrive_expect_tx(&bars[buf], (kRed ? 2u : 3u) * bytes + fbytes + gbytes);
             bulk_g2s(tl_buf + buf * tile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(th_buf + buf * tile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
+            if (!kRed) bulk_g2s(th_buf + buf * tile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
+            else bulk_g2s(thg_buf + buf * (tile / 16), p.smp.thg + (sbase + i0) / 16, gbytes, &bars[buf]);
             if (kRed) bulk_g2s(x_buf + buf * tile, p.smp.xq + sbase + i0, bytes, &bars[buf]);
             else bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
             bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
@@ -1713,7 +1740,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     const uint32_t sth = smem_u32(th_buf + buf * tile + sub);
                     const uint32_t sx = smem_u32(x_buf + buf * tile + sub);
                     unsigned long long fmask = 0ull;
-                    {
+                    if (!kRed) {  // the reduction layout takes no collision-free runs
                         const uint4 *fw = reinterpret_cast<const uint4 *>(f_buf + buf * (tile / 16) + sub / 16);
                         const int nq = (nvs + 255) >> 8;  // 16-byte words holding the sub-tile's flags
 #pragma unroll
@@ -1735,8 +1762,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                         // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
                         const int seg = min(nvs - i, chunk_left);
                         if constexpr (kRed)
-                            fold_segment_red<POW2>(stl + 4u * i, sth + 4u * i, sx + 4u * i, fmask >> (i >> 4), seg, st,
-                                                   Fl, Fh, (uint32_t)nbins, p.shift, sw, nstreams);
+                            fold_segment_red<POW2>(stl + 4u * i,
+                                                   smem_u32(thg_buf + buf * (tile / 16) + (sub + i) / 16),
+                                                   p.smp.tau_hi + sbase + (int64_t)t * tile + sub + i,
+                                                   sx + 4u * i, seg, st, Fl, Fh, (uint32_t)nbins, p.shift, sw,
+                                                   nstreams);
                         else
                             fold_segment<POW2, St, (MAXW <= 4)>(stl + 4u * i, sth + 4u * i, sx + 4u * i,
                                                                  fmask >> (i >> 4), seg, st, Fl, Fh, (uint32_t)nbins,
@@ -1918,7 +1948,10 @@ size_t fold_smem_bytes(int nbins, int warps, int layout, int tile)
 {
     const size_t nb2 = (size_t)((nbins + 1) & ~1);
     const size_t per_warp = layout == kLayoutPaired16 ? (size_t)32 * (nbins * 4 + nb2 * 2) : (size_t)32 * nbins * 8;
-    return 128 + (size_t)2 * tile * 12 + 2 * (tile / 16) + (size_t)warps * per_warp;
+    // tile bytes per sample (and the reduction layout's high word per 16 samples)
+    const size_t per_sample = layout == kLayoutRed32 ? 8 : 12;
+    const size_t per_group = layout == kLayoutRed32 ? 4 : 0;
+    return 128 + (size_t)2 * tile * per_sample + 2 * (tile / 16) * (1 + per_group) + (size_t)warps * per_warp;
 }
 
 int fold_max_warps(int nbins, int layout, int tile)

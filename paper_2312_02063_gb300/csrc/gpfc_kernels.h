@@ -41,6 +41,7 @@ struct SampleScratch {
     int32_t *tau_hi;    // high 32 bits of tau
     float *x;           // flux - f_ref (FP32)
     int32_t *xq;        // rint(x 2^qexp): the fixed-point flux of the reduction layout
+    int32_t *thg;       // one word per 16 samples: tau_hi of the group's first sample
     uint8_t *flags;     // one byte per 16 samples: regular-cadence group (see prep)
 };
 
