@@ -1724,9 +1724,16 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             const int buf = t & 1;
             bool ok = mbar_wait_bounded(&bars[buf], (parity_bits >> buf) & 1u);
             parity_bits ^= 1u << buf;
-            // with several streams the fold warps meet at chunk flushes inside the tile, so
-            // they all take the same branch
-            if (nstreams > 1) ok = !named_bar_or(1, 32 * nfw, !ok);
+            // with several streams the fold warps meet at the chunk flushes inside a tile, so
+            // before a tile that holds one they all take the same branch (every warp knows
+            // whether it does: chunk boundaries and the tile count are the same for all)
+            const int nv_t = (int)min((int64_t)tile, nsamp - (int64_t)t * tile);
+            // (the fold mode finishes its last chunk after the tile loop; the others flush it
+            // inside the last tile)
+            const bool last_tile = t == ntiles - 1;
+            const bool flush_inside = (chunk_left <= nv_t && !(MODE == kModeFold && chunk_left == nv_t && last_tile)) ||
+                                      (last_tile && MODE != kModeFold);
+            if (nstreams > 1 && flush_inside) ok = !named_bar_or(1, 32 * nfw, !ok);
             if (!ok) {
                 s_abort = 1;
                 report_error(p.status, kErrTimeout);
