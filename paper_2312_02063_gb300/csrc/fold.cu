@@ -1702,14 +1702,15 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             const int nv = (int)min((int64_t)tile, nsamp - i0);
             const uint32_t bytes = (uint32_t)(((nv + 3) & ~3) * 4);
             const uint32_t fbytes = (uint32_t)((((nv + 15) >> 4) + 15) & ~15);
+            // (the reduction layout needs no cadence flags: its groups carry their high word)
             const uint32_t gbytes = kRed ? (uint32_t)((((nv + 15) >> 4) * 4 + 15) & ~15) : 0u;
-            mbar_arrive_expect_tx(&bars[buf], (kRed ? 2u : 3u) * bytes + fbytes + gbytes);
+            mbar_arrive_expect_tx(&bars[buf], kRed ? 2u * bytes + gbytes : 3u * bytes + fbytes);
             bulk_g2s(tl_buf + buf * tile, p.smp.tau_lo + sbase + i0, bytes, &bars[buf]);
             if (!kRed) bulk_g2s(th_buf + buf * tile, p.smp.tau_hi + sbase + i0, bytes, &bars[buf]);
             else bulk_g2s(thg_buf + buf * (tile / 16), p.smp.thg + (sbase + i0) / 16, gbytes, &bars[buf]);
             if (kRed) bulk_g2s(x_buf + buf * tile, p.smp.xq + sbase + i0, bytes, &bars[buf]);
             else bulk_g2s(x_buf + buf * tile, p.smp.x + sbase + i0, bytes, &bars[buf]);
-            bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
+            if (!kRed) bulk_g2s(f_buf + buf * (tile / 16), p.smp.flags + (sbase + i0) / 16, fbytes, &bars[buf]);
         };
         fold_sync();  // previous task's readers are done with both buffers
         if (threadIdx.x == 0 && ntiles > 0) {  // a star without samples issues nothing
