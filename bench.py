@@ -39,7 +39,7 @@ SM_FOLD_UPDATES_PER_CLK = 16          # the pipe model: 128 B/clk / (4 B + 4 B o
 # DRAM bytes (read + write) of the fold kernel's 18 launches of one 250,000-period search of
 # the same light curve in steady state (no cache flush, one ncu pass), per period:
 # profiles/dram_traffic_steady_state_kepler62835.md
-SEARCH_DRAM_BYTES_PER_PERIOD = (0.123392e6 + 129.42208e6) / 250000
+SEARCH_DRAM_BYTES_PER_PERIOD = (0.144128e6 + 122.268416e6) / 250000
 L2_FLUSH_BYTES = 256 << 20
 
 
