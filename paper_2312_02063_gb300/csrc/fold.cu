@@ -1233,9 +1233,11 @@ __device__ __forceinline__ float box_reeval(const Bins &B, int nbins, int bs, in
 }
 
 // Box-SNR of one profile held by one thread: every start, then the winner re-evaluated.
+// The walk over the blocks of R starts s0_first, s0_first + s0_stride, ... of one profile:
+// its best (v, key = w << 12 | s), by the walk's rule.
 template <int R, class Bins>
-__device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
-                                           float &score, int &best_s, int &best_w)
+__device__ __forceinline__ void box_search_part(const Bins &B, int nbins, int w_min, int w_max, int s0_first,
+                                                int s0_stride, float &bv, int &bkey)
 {
     float Stot = 0.f, Ntot = 0.f;
     int nnz = 0;
@@ -1245,10 +1247,19 @@ __device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, 
         Ntot += c;
         nnz += c > 0.f;
     }
-    float bv = -INFINITY;
-    int bkey = 0x7fffffff;
-    if (w_max < nnz) box_walk<R, false>(B, nbins, w_min, w_max, Stot, Ntot, 0, R, bv, bkey);
-    else box_walk<R, true>(B, nbins, w_min, w_max, Stot, Ntot, 0, R, bv, bkey);
+    bv = -INFINITY;
+    bkey = 0x7fffffff;
+    if (w_max < nnz) box_walk<R, false>(B, nbins, w_min, w_max, Stot, Ntot, s0_first, s0_stride, bv, bkey);
+    else box_walk<R, true>(B, nbins, w_min, w_max, Stot, Ntot, s0_first, s0_stride, bv, bkey);
+}
+
+template <int R, class Bins>
+__device__ __forceinline__ void box_search(const Bins &B, int nbins, int w_min, int w_max, float sigma,
+                                           float &score, int &best_s, int &best_w)
+{
+    float bv;
+    int bkey;
+    box_search_part<R>(B, nbins, w_min, w_max, 0, R, bv, bkey);
     if (bkey == 0x7fffffff) {
         score = -INFINITY;
         best_s = -1;
@@ -1876,22 +1887,52 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 *reinterpret_cast<volatile int *>(&sh.pub[b]) = iter;
             }
         } else if (MODE == kModeBox) {
+            constexpr int kR = MAXW <= 4 ? 16 : 8;
             float sc = -INFINITY;
             int bs = -1, bw = -1;
-            if (kvalid) {
-                float sig = p.sigma_user;
-                if (!(sig > 0.f)) sig = p.stats[s].sigma;
-                if (!(sig > 0.f)) sig = 1.f;
-                const LaneBins<St> B{st, wcn_cta, (size_t)ppc, over};
-                box_search<(MAXW <= 4 ? 16 : 8)>(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
-                p.score[k] = sc;
-                if (p.best_s) p.best_s[k] = bs;
-                if (p.best_w) p.best_w[k] = bw;
+            float sig = p.sigma_user;
+            if (!(sig > 0.f)) sig = p.stats[s].sigma;
+            if (!(sig > 0.f)) sig = 1.f;
+            const LaneBins<St> B{st, wcn_cta, (size_t)ppc, over};
+            if (nstreams == 1) {
+                if (kvalid) box_search<kR>(B, nbins, p.w_min, p.w_max, sig, sc, bs, bw);
+            } else {
+                // the streams of a period group walk every nstreams-th block of starts of the
+                // lanes' profiles; their winners meet in the idle tile buffer, and stream 0
+                // keeps the best by the walk's rule and re-evaluates it
+                float bv = -INFINITY;
+                int bkey = 0x7fffffff;
+                if (kvalid) box_search_part<kR>(B, nbins, p.w_min, p.w_max, sw * kR, nstreams * kR, bv, bkey);
+                float2 *M = reinterpret_cast<float2 *>(tl_buf);  // [nstreams][ppc]
+                M[sw * ppc + gw * 32 + lane] = make_float2(bv, __int_as_float(bkey));
+                fold_sync();
+                if (sw == 0) {
+                    for (int r = 1; r < nstreams; ++r) {
+                        const float2 m = M[r * ppc + gw * 32 + lane];
+                        const int key = __float_as_int(m.y);
+                        const bool take = (m.x > bv) | ((m.x == bv) & (key < bkey));
+                        bv = take ? m.x : bv;
+                        bkey = take ? key : bkey;
+                    }
+                    if (kvalid && bkey != 0x7fffffff) {
+                        bw = bkey >> 12;
+                        bs = bkey & 4095;
+                        sc = box_reeval(B, nbins, bs, bw, sig);
+                    }
+                }
+                fold_sync();  // the merge area is free before the next task's tiles
             }
-            if (p.best_key) {
-                unsigned long long key = kvalid ? argmax_key(sc, k - gb) : 0ull;
-                key = warp_max_u64(key);
-                if (lane == 0 && key) atomicMax(&p.best_key[s], key);
+            if (sw == 0) {
+                if (kvalid) {
+                    p.score[k] = sc;
+                    if (p.best_s) p.best_s[k] = bs;
+                    if (p.best_w) p.best_w[k] = bw;
+                }
+                if (p.best_key) {
+                    unsigned long long key = kvalid ? argmax_key(sc, k - gb) : 0ull;
+                    key = warp_max_u64(key);
+                    if (lane == 0 && key) atomicMax(&p.best_key[s], key);
+                }
             }
         }
     }
@@ -2049,7 +2090,9 @@ static void launch_search_variant(const FoldParams &p, int grid, size_t smem, cu
 cudaError_t launch_fold(const FoldParams &p_in, int mode, int grid, cudaStream_t st)
 {
     FoldParams p = p_in;
-    if (mode == kModeBox) p.streams = 1;  // the box epilogue reads a whole profile per warp
+    // the epilogue search of several streams merges through the tile buffer: it needs
+    // nstreams x periods-per-block (v, key) pairs there
+    if (mode == kModeBox && (size_t)p.streams * 32 * p.warps * 8 > (size_t)p.tile * 8) p.streams = 1;
     if (p.tile != 512 && p.tile != 1024 && p.tile != 2048) return cudaErrorInvalidValue;
     if (p.streams < 1 || (p.streams > 1 && p.layout != kLayoutRed32)) return cudaErrorInvalidValue;
     if (mode == kModeSearch) {
