@@ -784,6 +784,59 @@ __device__ __forceinline__ void fold_segment_red(uint32_t stl, uint32_t sthg, co
     }
 }
 
+// Most period groups a block may hold for the cross-group reduction fold below.
+constexpr int kRedCross = 3;
+
+// kLayoutRed32 with every fold warp a sample stream of all the block's period groups: the
+// stream's 16-sample groups (g mod nstreams = stream, as above) go into the bins of each of
+// the G period groups (lane l: period l of each group, bin records gstride bytes apart), so
+// each sample is read from the tile once per block rather than once per period group.
+template <bool POW2>
+__device__ __forceinline__ void fold_segment_red_x(uint32_t stl, uint32_t sthg, const int32_t *gth, uint32_t sxq,
+                                                   int nvalid, const StoreRed32 &st, uint32_t gstride,
+                                                   const uint32_t (&Fl)[kRedCross], const uint32_t (&Fh)[kRedCross],
+                                                   int G, uint32_t nbins, int shift, int stream, int nstreams)
+{
+    const int ng = nvalid >> 4;
+    auto one = [&](const RedGroup &C, int g, int j) {
+        uint32_t b[16];
+        red_group_bins<POW2>(C, gth, g, Fl[j], Fh[j], nbins, shift, b);
+        red_group_add(StoreRed32{st.v + (uint32_t)j * gstride}, b, C);
+    };
+    // one stage: group g (data in C) into every period group, group g + nstreams loaded into N
+    auto stage = [&](const RedGroup &C, RedGroup &N, int g) {
+        uint32_t b[16];
+        red_group_bins<POW2>(C, gth, g, Fl[0], Fh[0], nbins, shift, b);
+        if (g + nstreams < ng) load_red_group(stl, sthg, sxq, g + nstreams, N);
+        red_group_add(st, b, C);
+#pragma unroll
+        for (int j = 1; j < kRedCross; ++j)
+            if (j < G) one(C, g, j);
+    };
+    int g = stream;
+    if (g < ng) {
+        RedGroup G0, G1;
+        load_red_group(stl, sthg, sxq, g, G0);
+#pragma unroll 1
+        for (; g + nstreams < ng; g += 2 * nstreams) {
+            stage(G0, G1, g);
+            stage(G1, G0, g + nstreams);
+        }
+        if (g < ng) stage(G0, G1, g);
+    }
+    if (ng % nstreams == stream) {
+        for (int i = 16 * ng; i < nvalid; ++i) {
+            const uint32_t tl = lds_u32(stl + 4u * i), th = (uint32_t)__ldg(gth + i);
+            const int32_t xq = (int32_t)lds_u32(sxq + 4u * i);
+#pragma unroll
+            for (int j = 0; j < kRedCross; ++j)
+                if (j < G)
+                    StoreRed32{st.v + (uint32_t)j * gstride}.add(phase_bin<POW2>(tl, th, Fl[j], Fh[j], nbins, shift),
+                                                                 xq);
+        }
+    }
+}
+
 // Fold this lane's chunk partials into the Kahan workspace (sum, compensation) and the
 // exact 32-bit counts. On the last chunk the finished sums (sum - compensation) go back
 // into the store with the counts (16-bit stores saturate at 65535; the exact totals stay
@@ -1583,6 +1636,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     const int nfw = p.warps * nstreams;
     const int gw = warp % p.warps, sw = warp / p.warps;
     const int blo = (int)((int64_t)sw * nbins / nstreams), bhi = (int)((int64_t)(sw + 1) * nbins / nstreams);
+    // kLayoutRed32 with at most kRedCross period groups: fold warp w is sample stream w of nfw
+    // and folds into every group (the flushes and epilogues keep the (gw, sw) split above)
+    const bool cross = kRed && p.warps <= kRedCross;
+    // whether several warps add into one period group's bins (then they meet at the flushes)
+    const bool shared_bins = cross ? nfw > 1 : nstreams > 1;
     // block barrier of the fold warps (in kModeSearch the scorer warp is not among them)
     auto fold_sync = [&]() {
         if (MODE == kModeSearch) named_bar_sync(1, 32 * nfw);
@@ -1602,12 +1660,15 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
     using St = typename std::conditional<LAYOUT == kLayoutPacked64, StorePacked64,
                                          typename std::conditional<kRed, StoreRed32, StorePaired16>::type>::type;
     St st;
+    StoreRed32 st0{0u};  // kLayoutRed32: this lane's records of period group 0
+    const uint32_t gstride = (uint32_t)nbins * 256u;  // bytes between period groups' records
     if constexpr (LAYOUT == kLayoutPacked64) {
         uint2 *v = reinterpret_cast<uint2 *>(f_buf + 2 * (tile / 16));
         st.v = smem_u32(v + (size_t)warp * nbins * 32 + lane);
     } else if constexpr (kRed) {
         uint32_t *v = reinterpret_cast<uint32_t *>(f_buf + 2 * (tile / 16));
         st.v = smem_u32(v + (size_t)gw * nbins * 64 + lane);
+        st0.v = smem_u32(v + lane);
     } else {
         float *acc = reinterpret_cast<float *>(f_buf + 2 * (tile / 16));
         const int nb2 = (nbins + 1) & ~1;
@@ -1703,6 +1764,21 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                 report_error(p.status, kErrRange);
             }
         }
+        // the cross-group fold: this lane's period in each of the block's period groups
+        uint32_t FlX[kRedCross], FhX[kRedCross];
+#pragma unroll
+        for (int j = 0; j < kRedCross; ++j) {
+            FlX[j] = FhX[j] = 0u;
+            const int64_t kj = gb + (task - tbase) * ppc + j * 32 + lane;
+            if (cross && j < p.warps && kj < ge) {
+                const double q = kTwo40 / p.periods[kj];
+                if (q > 0.0 && q < kTwo63) {  // (a period outside (0, inf) is reported above)
+                    const unsigned long long F = (unsigned long long)__double2ll_rn(q);
+                    FlX[j] = (uint32_t)F;
+                    FhX[j] = (uint32_t)(F >> 32);
+                }
+            }
+        }
         // one group size for the whole warp, so its lanes never diverge between paths
         const int wg = __all_sync(0xffffffffu, gsize >= 16) ? 16 : (__all_sync(0xffffffffu, gsize >= 8) ? 8 : 0);
         const double qscale = kRed ? ldexp(1.0, -p.stats[s].qexp) : 1.0;  // fixed-point unit
@@ -1745,7 +1821,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
             const bool last_tile = t == ntiles - 1;
             const bool flush_inside = (chunk_left <= nv_t && !(MODE == kModeFold && chunk_left == nv_t && last_tile)) ||
                                       (last_tile && MODE != kModeFold);
-            if (nstreams > 1 && flush_inside) ok = !named_bar_or(1, 32 * nfw, !ok);
+            if (shared_bins && flush_inside) ok = !named_bar_or(1, 32 * nfw, !ok);
             if (!ok) {
                 s_abort = 1;
                 report_error(p.status, kErrTimeout);
@@ -1780,13 +1856,23 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                     while (i < nvs) {
                         // segments end at chunk boundaries (multiples of 4 samples) or the sub-tile end
                         const int seg = min(nvs - i, chunk_left);
-                        if constexpr (kRed)
+                        if constexpr (kRed) {
+                            if (cross) {
+                                // the streams' turns rotate with the segment's first group, so
+                                // segments of any length share their groups out evenly
+                                const int g0 = (int)((((int64_t)t * tile + sub + i) >> 4) % nfw);
+                                fold_segment_red_x<POW2>(stl + 4u * i,
+                                                         smem_u32(thg_buf + buf * (tile / 16) + (sub + i) / 16),
+                                                         p.smp.tau_hi + sbase + (int64_t)t * tile + sub + i,
+                                                         sx + 4u * i, seg, st0, gstride, FlX, FhX, p.warps,
+                                                         (uint32_t)nbins, p.shift, (warp - g0 + nfw) % nfw, nfw);
+                            } else
                             fold_segment_red<POW2>(stl + 4u * i,
                                                    smem_u32(thg_buf + buf * (tile / 16) + (sub + i) / 16),
                                                    p.smp.tau_hi + sbase + (int64_t)t * tile + sub + i,
                                                    sx + 4u * i, seg, st, Fl, Fh, (uint32_t)nbins, p.shift, sw,
                                                    nstreams);
-                        else
+                        } else
                             fold_segment<POW2, St, (MAXW <= 4)>(stl + 4u * i, sth + 4u * i, sx + 4u * i,
                                                                  fmask >> (i >> 4), seg, st, Fl, Fh, (uint32_t)nbins,
                                                                  p.shift, wg);
@@ -1800,10 +1886,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) fold_kernel(const FoldParams p)
                                 // fold's last chunk is finished in the epilogue (after the tile
                                 // loop's barrier), straight into the output rows.
                                 if (!(MODE == kModeFold && last)) {
-                                    if (nstreams > 1) fold_sync();
+                                    if (shared_bins) fold_sync();
                                     flush_chunk_red(st, reinterpret_cast<long long *>(wsc_cta), wcn_cta, blo, bhi,
                                                     ppc, first_flush, last, qscale);
-                                    if (nstreams > 1) fold_sync();
+                                    if (shared_bins) fold_sync();
                                 } else {
                                     last_first = first_flush;
                                 }
