@@ -39,7 +39,7 @@ SM_FOLD_UPDATES_PER_CLK = 16          # the pipe model: 128 B/clk / (4 B + 4 B o
 # DRAM bytes (read + write) of the fold kernel's 18 launches of one 250,000-period search of
 # the same light curve in steady state (no cache flush, one ncu pass), per period:
 # profiles/dram_traffic_steady_state_kepler62835.md
-SEARCH_DRAM_BYTES_PER_PERIOD = (0.144128e6 + 122.268416e6) / 250000
+SEARCH_DRAM_BYTES_PER_PERIOD = (0.403456e6 + 206.749696e6) / 250000
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -601,7 +601,7 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "periods_scored_per_s": world * N_PERIODS / (ms_per_step * 1e-3),
-            "roofline": {"bound": "smem", "kernel": "fold_kernel (reduction layout, 3 period groups x 4 streams)",
+            "roofline": {"bound": "smem", "kernel": "fold_kernel (reduction layout, 3 period groups, 12 sample streams across them)",
                          "achieved": achieved,
                          "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                          "traffic": None if SEARCH_DRAM_BYTES_PER_PERIOD is None

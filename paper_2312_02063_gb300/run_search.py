@@ -44,7 +44,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--seed", type=int, default=20232204)
     ap.add_argument("--n-samples", type=int, default=0, help="keep only the first N samples of the star (0: all)")
-    for k in ("layout", "warps", "chunk", "tile"):
+    for k in ("layout", "warps", "chunk", "tile", "streams"):
         ap.add_argument("--" + k, type=int, default=0)
     a = ap.parse_args()
     import lcsynth  # the synthetic-input generators
@@ -53,7 +53,7 @@ def main():
         probe_sweep()
         return
     ctx = Context(0)
-    ctx.set_fold_config(warps=a.warps, layout=a.layout, chunk=a.chunk, tile=a.tile)
+    ctx.set_fold_config(warps=a.warps, layout=a.layout, chunk=a.chunk, tile=a.tile, streams=a.streams)
     dev = ctx.device
     w = init_weights(dev, 1)
     if a.what == "cnn-score":
