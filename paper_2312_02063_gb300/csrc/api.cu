@@ -644,6 +644,28 @@ int run_search_box_fused(gpfc_ctx *ctx, const double *times, const float *flux, 
     return GPFC_OK;
 }
 
+// Period groups and sample streams of the fold launch of a chunk of nk periods, and its
+// grid. A chunk too short to give every SM a block of pl.warps period groups (the last chunk
+// of a search) takes fewer groups per block, each with more sample streams, so that more SMs
+// share it: layout 3 only, whose results do not depend on the launch shape, and only where
+// the block shape was not fixed by gpfc_set_fold_config. The launch fits the workspace
+// carved for pl (no more blocks, no more periods per block).
+static int chunk_shape(const gpfc_ctx *ctx, const FoldPlan &pl, int64_t nk, FoldParams &p)
+{
+    p.warps = pl.warps;
+    p.streams = pl.streams;
+    if (pl.layout == kLayoutRed32 && ctx->fold_cfg.warps == 0 && ctx->fold_cfg.streams == 0) {
+        const int64_t per_sm = (nk + (int64_t)32 * ctx->num_sms - 1) / ((int64_t)32 * ctx->num_sms);
+        const int w = (int)std::max<int64_t>(1, std::min<int64_t>(pl.warps, per_sm));
+        if (w < pl.warps) {
+            p.warps = w;
+            p.streams = std::max(1, std::min(kMaxRedWarps / w, pl.warps * pl.streams / w));
+        }
+    }
+    p.ntasks = (nk + 32 * p.warps - 1) / (32 * p.warps);
+    return (int)std::min<int64_t>(p.ntasks, pl.grid);
+}
+
 // Workspace of run_search_box_warp: the fold buffers, two chunks of sums and counts.
 size_t box_warp_bytes(const FoldPlan &pl, int64_t n, int64_t np, int nbins)
 {
@@ -692,22 +714,20 @@ int run_search_box_warp(gpfc_ctx *ctx, const double *times, const float *flux, i
         p.n = n;
         p.periods = periods + k0;
         p.np = nk;
-        p.ntasks = (nk + pl.ppc - 1) / pl.ppc;
         p.nstars = 1;
         p.stats = fb.stats;
         p.nbins = nbins;
         p.shift = shift_of(nbins);
-        p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
-        p.streams = pl.streams;
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
         p.sums = cs[b];
         p.counts = cc[b];
         p.status = ctx->status_dev;
-        return timed_fold(ctx, sf, [&] { return launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), sf); });
+        const int grid = chunk_shape(ctx, pl, nk, p);
+        return timed_fold(ctx, sf, [&] { return launch_fold(p, kModeFold, grid, sf); });
     };
     auto box = [&](int64_t i, int b, cudaStream_t sb) {
         const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);
@@ -803,22 +823,19 @@ int run_search_cnn(gpfc_ctx *ctx, const double *times, const float *flux, int64_
         p.n = n;
         p.periods = periods + k0;
         p.np = nk;
-        p.ntasks = (nk + pl.ppc - 1) / pl.ppc;
         p.nstars = 1;
         p.stats = fb.stats;
         p.nbins = nbins;
         p.shift = shift_of(nbins);
-        p.warps = pl.warps;
         p.chunk = pl.chunk;
         p.layout = pl.layout;
-        p.streams = pl.streams;
         p.tile = pl.tile;
         p.ws_sc = fb.ws_sc;
         p.ws_cnt = fb.ws_cnt;
         p.folded = cf[b];
         p.counts = cc[b];
         p.status = ctx->status_dev;
-        return launch_fold(p, kModeFold, (int)std::min<int64_t>(p.ntasks, pl.grid), sf);
+        return launch_fold(p, kModeFold, chunk_shape(ctx, pl, nk, p), sf);
     };
     auto cnn = [&](int64_t i, int b, cudaStream_t sb) {
         const int64_t k0 = i * chunk, nk = std::min<int64_t>(chunk, np - k0);

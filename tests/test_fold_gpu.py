@@ -359,3 +359,39 @@ def test_reduction_fold_is_identical_for_any_launch_shape(ctx):
     finally:
         ctx.reset_fold_config()
 
+
+
+@pytest.mark.parametrize("tail_per_sm", [40, 10])
+def test_short_last_chunk_scores_equal_a_fixed_block_shape(ctx, tail_per_sm):
+    """The searches fold a last chunk of periods too short to give every SM a block of three
+    period groups with narrower blocks (two groups for 40 periods per SM, one for 10; layout
+    3 only, whose sums are exact). Box and CNN scores must equal those of the same search with
+    the block shape fixed at three groups, which folds every chunk alike."""
+    import paper_2312_02063_gb300 as g
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rng = np.random.default_rng(41)
+    n = 6000
+    times = np.sort(rng.uniform(0.0, 400.0, n))
+    flux = (1.0 + rng.normal(0, 2e-3, n)).astype(np.float32)
+    periods = rng.uniform(0.2, 1.0, 96 * nsm + tail_per_sm * nsm)  # one full chunk and a short one
+    w = lcsynth.cnn_init(5, bias_scale=0.05)
+    w["fc2.w"] = lcsynth.round_to_bf16(w["fc2.w"] * 0.25)
+    wd = {k: _dev(ctx, v.astype(np.float32)) for k, v in w.items()}
+    t_d, f_d, p_d = _dev(ctx, times), _dev(ctx, flux), _dev(ctx, periods)
+
+    def both():
+        box = g.gpfc_search(ctx, t_d, f_d, p_d, 256, 0.0, g.SCORER_BOX, 1, 108, 2e-3)
+        cnn = g.gpfc_search(ctx, t_d, f_d, p_d, 256, 0.0, g.SCORER_CNN, weights=wd)
+        ctx.sync()
+        assert ctx.last_fold_plan()["layout"] == 3
+        return [[t.cpu().numpy() for t in r] for r in (box, cnn)]
+
+    auto = both()
+    try:
+        ctx.set_fold_config(warps=3, layout=3)
+        fixed = both()
+    finally:
+        ctx.reset_fold_config()
+    for a, f in zip(auto, fixed):
+        for x, y in zip(a, f):
+            np.testing.assert_array_equal(x, y)
