@@ -16,8 +16,11 @@
 //   red.shared.add.u32. The flux is pre-quantised per star (x_q = rint(x 2^e), e from the
 //   largest |x| and the chunk length, so a chunk's bin sum fits in 32 bits), the sums are
 //   exact and independent of the order of the additions, and so several warps (sample
-//   streams) fold disjoint 16-sample groups of every tile into the same period group's
-//   bins: three 64 KB period groups per block at 256 bins, four streams each, twelve warps.
+//   streams) fold disjoint 16-sample groups of every tile into the same bins: three 64 KB
+//   period groups per block at 256 bins and twelve warps, each warp one of twelve streams
+//   that adds its samples into all three groups (lane l: period l of each), so a sample is
+//   read from the tile once per block. (Blocks of more than three period groups give each
+//   group its own streams.) Flushes and epilogues split each group's bins over its warps.
 //   Chunk sums go exactly into an int64 workspace; each bin is rounded once to FP32.
 // * kLayoutPacked64: FP32 partial sum and 32-bit count in one 8-byte word, a 64-bit load
 //   and store per update; one warp per 32 periods.
