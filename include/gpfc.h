@@ -96,9 +96,11 @@ int gpfc_fold_launch_times(gpfc_ctx *ctx, float *total_ms, int32_t *launches);
  *   tile           light-curve samples per bulk copy into shared memory: 512, 1024 or 2048
  *   blocks_per_sm  resident blocks per multiprocessor of the persistent grid (capped by
  *                  what fits)
- *   streams        layout 3 only: warps that fold disjoint samples of each warp's 32 periods
- *                  into the same bins (1..12 with warps x streams <= 12; the box epilogue of
- *                  gpfc_search below 256 bins always uses 1) */
+ *   streams        layout 3 only: fold warps per period group (1..12 with warps x streams
+ *                  <= 12). With up to three period groups the block's warps x streams warps
+ *                  each fold a disjoint share of the samples into the bins of every group;
+ *                  with more, each group's streams fold into that group. The box epilogue
+ *                  of gpfc_search uses 1 where its streams' merge does not fit in a tile. */
 typedef struct {
     int32_t warps;
     int32_t layout;
